@@ -1,0 +1,145 @@
+/*
+ * ed.h -- C ABI of libed, a GB300 (sm_103a) exact-diagonalization impurity solver.
+ *
+ * The solver follows Sec. 4 of "Pyqcm: An open-source Python library for quantum cluster
+ * methods" (arXiv:2305.18643): a Hubbard-like cluster with optional bath orbitals
+ * (Eq. Hubbard, Eq. cdmft1) is diagonalized in a fixed (N_up, N_dn) sector with a
+ * matrix-free factorized Hamiltonian (Eq. factorized), the Lanczos ground state (Sec. 4.2)
+ * and the Lanczos / band-Lanczos Green function (Secs. 4.3, 4.4), evaluated on a frequency
+ * grid (Eq. jacobi, Eq. spectral1).
+ *
+ * Conventions shared by every call:
+ *  - Orbitals: cluster sites 0 .. n_sites-1 first, then bath orbitals n_sites .. L-1,
+ *    L = n_sites + n_bath <= 32.  Bit a of a spin's bit string is the occupation of orbital a
+ *    (Sec. 4.1, Eq. basis); each spin's states are labelled by ascending integer value, which
+ *    is the combinatorial-number-system rank.
+ *  - Hamiltonian: H = sum_{ab,s} h_ab c+_{as} c_{bs} + sum_{i<n_sites} U_i n_{i up} n_{i dn} with
+ *    h_ij = t_ij (sites), h_ii = t_ii - mu (sites), h_{i,ns+a} = theta_ia, h_{ns+a,ns+a} = eps_a.
+ *  - State vectors are row-major psi[u][d]: u = up label (slow), d = down label (fast); a
+ *    leading dimension ld >= d_dn may pad rows.
+ *  - Every call returns an ed_status: 0 = ok, > 0 = pending / warning, < 0 = error.  On error
+ *    ed_last_error() returns a message (thread-local, valid until the next call on that thread).
+ *  - Host arrays passed in are copied before the call returns; the caller keeps ownership.
+ *  - Device pointers are CUDA device addresses on the current device.
+ */
+#ifndef ED_H
+#define ED_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int ed_status;
+
+enum {
+  ED_OK = 0,
+  ED_PENDING = 1,             /* request still running (ed_poll) */
+  ED_WARN_DEGENERATE = 2,     /* ground state converged but a second Ritz value lies within
+                                 1e-8 max(1,|E0|): G is not unique (Sec. 4.2) */
+  ED_WARN_NOT_CONVERGED = 3,  /* max_iter reached; results written are the last iterate */
+  ED_ERR_INVALID = -1,        /* bad argument (NaN, non-symmetric t, bad sector, size limits) */
+  ED_ERR_OOM = -2,            /* device allocation failed */
+  ED_ERR_CUDA = -3,           /* a CUDA call failed */
+  ED_ERR_TOO_LARGE = -5,      /* request exceeds the memory budget of a server */
+  ED_ERR_TIMEOUT = -6,        /* a bounded device-side wait gave up */
+  ED_ERR_STATE = -7,          /* call out of order (e.g. no ground state yet) */
+  ED_ERR_NOT_FOUND = -8,      /* unknown request id */
+  ED_ERR_CANCELLED = -9
+};
+
+enum { ED_FP64 = 0, ED_FP32 = 1 };             /* precision of stored vectors */
+enum { ED_GF_CF = 0, ED_GF_BAND = 1 };         /* Green-function method: Sec. 4.3 / Sec. 4.4 */
+enum { ED_AXIS_REAL = 0, ED_AXIS_MATSUBARA = 1 };
+
+/* Cluster description (Eq. cdmft1).  All arrays are host arrays, copied at create. */
+typedef struct ed_cluster_desc {
+  int n_sites;          /* cluster sites, >= 1 */
+  int n_bath;           /* bath orbitals, >= 0; n_sites + n_bath <= 32 */
+  const double* t;      /* n_sites x n_sites row-major, symmetric; diagonal = on-site energies */
+  const double* U;      /* n_sites on-site interactions */
+  double mu;            /* chemical potential, acts on cluster sites only */
+  const double* eps;    /* n_bath bath energies (absolute); may be NULL if n_bath == 0 */
+  const double* theta;  /* n_sites x n_bath row-major hybridizations; may be NULL if n_bath == 0 */
+  int n_up, n_dn;       /* sector; 0 <= N_s <= L */
+  int precision;        /* ED_FP64 or ED_FP32 (FP32 vectors, FP64 reductions and recurrence,
+                           FP64 polish of the ground state) */
+  int gf_method;        /* ED_GF_CF or ED_GF_BAND */
+  uint64_t seed;        /* Lanczos start vector: v0[u][d] = splitmix64(seed ^ (u * d_dn + d)) */
+  double tol;           /* ground-state residual target ||H W - E0 W|| <= tol max(1,|E0|);
+                           <= 0 selects 1e-12 */
+  int max_iter;         /* Lanczos iterations per ground-state pass; <= 0 selects 600 */
+} ed_cluster_desc;
+
+typedef struct ed_cluster ed_cluster;
+
+/* Message of the last error on the calling thread (empty if none).  The string is owned by the
+ * library and stays valid until the next libed call on the same thread. */
+const char* ed_last_error(void);
+
+/* Validates and copies desc, builds the ground-state sector's basis and hopping tables on the
+ * device.  Errors: ED_ERR_INVALID (L > 32, a NaN, t not symmetric, N_s outside [0, L],
+ * d_s >= 2^24, more than 128 distinct off-diagonal h values), ED_ERR_OOM, ED_ERR_CUDA.
+ * On success *out owns device memory until ed_cluster_destroy. */
+ed_status ed_cluster_create(const ed_cluster_desc* desc, ed_cluster** out);
+
+/* Frees every device buffer of the cluster.  NULL is ignored. */
+void ed_cluster_destroy(ed_cluster* c);
+
+/* Lanczos ground state (Sec. 4.2): three-term recursion with FP64 reductions, lowest Ritz pair
+ * of the tridiagonal matrix, reconstruction of the ground state by retracing the recursion,
+ * then an explicit FP64 residual.  Synchronous.  Writes E0 (FP64), the residual
+ * ||H W - E0 W|| / max(1,|E0|) with ||W|| = 1, and the number of Lanczos iterations; any output
+ * pointer may be NULL.  The ground state stays on the device in the handle.
+ * Returns ED_OK, ED_WARN_DEGENERATE or ED_WARN_NOT_CONVERGED (results still written). */
+ed_status ed_ground_state(ed_cluster* c, double* E0, double* residual, int* iters);
+
+/* Copies the ground state psi[u][d] (d_up x d_dn, contiguous, FP64) to out (host or device).
+ * ED_ERR_STATE if ed_ground_state has not run. */
+ed_status ed_ground_vector(ed_cluster* c, double* out, int out_is_device);
+
+/* Cluster Green function G_ij(z), i, j over cluster sites only (Eq. green), for one spin
+ * (0 = up, 1 = down), on z_k = omega[k] + i eta (ED_AXIS_REAL) or z_k = i omega[k]
+ * (ED_AXIS_MATSUBARA).  Method from desc.gf_method.  Runs ed_ground_state first if needed.
+ * G_out: interleaved complex128 [n_freq][n_sites][n_sites] (2 doubles per element), host or
+ * device memory as out_is_device says; owned by the caller. */
+ed_status ed_green(ed_cluster* c, const double* omega, int n_freq, double eta, int axis, int spin,
+                   double* G_out, int out_is_device);
+
+/* Statistics of the last ed_green: total Lanczos (or band) steps over all starting vectors and
+ * the longest run.  Any pointer may be NULL. */
+ed_status ed_green_stats(const ed_cluster* c, int64_t* total_steps, int* max_steps);
+
+/* ---- lower-level calls (parity tests and benchmarks) ------------------------------------- */
+
+/* Sector dimensions d_up = C(L, n_up), d_dn = C(L, n_dn) of any sector of this cluster. */
+ed_status ed_sector_dims(const ed_cluster* c, int n_up, int n_dn, int64_t* d_up, int64_t* d_dn);
+
+/* Basis of one spin with N particles on L orbitals (Sec. 4.1), computed on the device by
+ * unranking the combinatorial number system; copied to the host array out[capacity].
+ * *dim receives C(L, N).  ED_ERR_INVALID if capacity < C(L, N). */
+ed_status ed_basis(int L, int N, uint32_t* out, int64_t capacity, int64_t* dim);
+
+/* Hopping table of one spin with N particles (Sec. 4.1, element (-1)^{M_ab} h_ab), built on
+ * the device, copied to host arrays: row_ptr[d + 1] (CSR, pull form: y[r] += K[r, c] x[c]),
+ * entries[n] packed as (c << 8) | (sign_bit << 7) | value_index, values[<= 128] the distinct
+ * off-diagonal h_ab.  K[r, c] = (sign_bit ? -1 : 1) * values[value_index].  The diagonal
+ * h_aa n_a is not in the table.  *n_entries and *n_values receive the counts; ED_ERR_INVALID if
+ * cap_entries is too small. */
+ed_status ed_hop_table(ed_cluster* c, int N, int32_t* row_ptr, uint32_t* entries, double* values,
+                       int64_t cap_entries, int64_t* n_entries, int* n_values);
+
+/* y = H x in sector (n_up, n_dn) on device arrays of d_up rows, leading dimension ld >= d_dn
+ * (elements; ld <= 0 means d_dn); dtype ED_FP64 (double) or ED_FP32 (float; products and sums in FP32).  x and y
+ * must not overlap.  stream: a cudaStream_t or NULL for the cluster's own stream.  Asynchronous
+ * on that stream. */
+ed_status ed_hpsi(ed_cluster* c, int n_up, int n_dn, int dtype, const void* x, void* y, int64_t ld,
+                  void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ED_H */

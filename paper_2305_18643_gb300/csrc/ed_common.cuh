@@ -1,0 +1,201 @@
+// Internal declarations shared by the libed translation units (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "ed.h"
+
+namespace ed {
+
+constexpr int kMaxOrb = 32;      // one 32-bit word per spin
+constexpr int kMaxVals = 128;    // distinct off-diagonal h values (7-bit index in a table entry)
+constexpr int kMaxHops = 256;    // hops per basis state: N (L - N) <= 16 * 16
+constexpr int kMaxPairs = kMaxOrb * (kMaxOrb - 1);
+
+// Packed hopping-table entry: source label << 8 | fermion-sign bit << 7 | value index.
+__host__ __device__ inline uint32_t ent_col(uint32_t e) { return e >> 8; }
+__host__ __device__ inline uint32_t ent_neg(uint32_t e) { return (e >> 7) & 1u; }
+__host__ __device__ inline uint32_t ent_vidx(uint32_t e) { return e & 127u; }
+
+struct Error : public std::runtime_error {
+  ed_status code;
+  Error(ed_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+void set_last_error(const std::string& msg);
+[[noreturn]] void throw_cuda(cudaError_t e, const char* what, const char* file, int line);
+
+#define ED_CUDA(call)                                                  \
+  do {                                                                 \
+    cudaError_t e_ = (call);                                           \
+    if (e_ != cudaSuccess) ::ed::throw_cuda(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define ED_CHECK_LAUNCH() ED_CUDA(cudaGetLastError())
+
+// Device buffer with RAII ownership (cudaMalloc / cudaFree).
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  explicit DevBuf(size_t count) { alloc(count); }
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  void alloc(size_t count) {
+    release();
+    if (count == 0) return;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      throw Error(ED_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
+    }
+    n = count;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+// Host-side model after validation: one-body matrix h over L orbitals and per-orbital U.
+struct ModelHost {
+  int ns = 0, nb = 0, L = 0;
+  std::vector<double> h;        // L x L
+  std::vector<double> U;        // L (0 on bath)
+  std::vector<double> vals;     // distinct off-diagonal h values
+  std::vector<int> pair_a, pair_b, pair_vidx;  // ordered pairs with h[a][b] != 0, a != b
+};
+
+// Parameters passed to kernels by value.
+struct HopParams {
+  double val[kMaxVals];
+  float valf[kMaxVals];
+  double U[kMaxOrb];
+  float Uf[kMaxOrb];
+  uint32_t umask;   // orbitals with U != 0
+  int nvals;
+};
+
+// One spin's sector with N particles: basis, two-level rank tables, hopping table, diagonal.
+struct SpinTables {
+  int L = 0, N = 0, split = 0;
+  int64_t dim = 0, nnz = 0;
+  DevBuf<uint32_t> basis;      // [dim] bit strings, ascending
+  DevBuf<int32_t> rank_lo;     // [2^split]       rank(b) = rank_lo[b & lomask] + rank_hi[b >> split]
+  DevBuf<int32_t> rank_hi;     // [2^(L-split)]
+  DevBuf<int32_t> ptr;         // [dim + 1]
+  DevBuf<uint32_t> ent;        // [nnz]
+  DevBuf<double> ediag;        // [dim] sum_a h_aa n_a
+  DevBuf<float> ediag32;       // [dim]
+};
+
+// Read-only device view of a two-spin sector for the H.psi kernels.
+struct SectorView {
+  int64_t d_up, d_dn, ld;
+  const uint32_t* B_up;
+  const uint32_t* B_dn;
+  const int32_t* ptr_up;
+  const uint32_t* ent_up;
+  const int32_t* ptr_dn;
+  const uint32_t* ent_dn;
+  const double* e_up;
+  const double* e_dn;
+  const float* e_up32;
+  const float* e_dn32;
+};
+
+struct RankView {
+  const int32_t* lo;
+  const int32_t* hi;
+  int split;
+  uint32_t lomask;
+};
+
+__device__ __forceinline__ int32_t rank_of(const RankView& r, uint32_t b) {
+  return r.lo[b & r.lomask] + r.hi[b >> r.split];
+}
+
+// sector.cu
+std::unique_ptr<SpinTables> build_spin_tables(const ModelHost& m, int N, cudaStream_t s);
+void basis_to_host(int L, int N, uint32_t* out, int64_t dim);
+uint64_t binomial(int n, int k);
+
+// hpsi.cu : y = H x (optionally fused Lanczos epilogue), batched over runs via blockIdx.z.
+struct LanczosScalars {
+  double* alpha;      // [runs][mstride]
+  double* beta;       // [runs][mstride + 1], beta[r][n] = b_n (norm); beta[r][0] = 0
+  double* beta0;      // [runs] initial norm b_0 (of the unnormalized start vector)
+  int* active;        // [runs] 1 while the run continues
+  double* partial;    // [runs][nblk][3] block partial sums
+  unsigned* counter;  // [runs] blocks finished (reset by the last block)
+  int mstride;
+  double btol;        // run stops when b_{n+1} < btol * b_0
+  int* nsteps;        // [runs] levels completed (alpha_0 .. alpha_{nsteps-1}); may be NULL
+};
+
+void launch_hpsi(const SectorView& sv, const HopParams& hp, int dtype, const void* x, void* y,
+                 cudaStream_t s);
+// One fused Lanczos step for `runs` vectors stored at X + r * vstride (and XP likewise):
+// W = H X - b_n XP written over XP; per-run reductions finish alpha_n, b_{n+1}.
+void launch_lanczos_step(const SectorView& sv, const HopParams& hp, int dtype, const void* X,
+                         void* XP, int64_t vstride, int runs, int n, const LanczosScalars& ls,
+                         int nblk_cap, cudaStream_t s);
+int lanczos_blocks(const SectorView& sv);   // blocks per run of the fused step
+
+// lanczos.cu
+void launch_lanczos_next(int dtype, void* W, const void* X, int64_t d_up, int64_t d_dn, int64_t ld,
+                         int64_t vstride, int runs, int n, const LanczosScalars& ls,
+                         void* omega, const double* coef, cudaStream_t s);
+void launch_start_vector(int dtype, void* v, int64_t d_up, int64_t d_dn, int64_t ld, uint64_t seed,
+                         cudaStream_t s);
+// Reductions into a device double: out = <a, b> over d_up x d_dn (two-stage, fixed order).
+void launch_dot(int dtype_a, const void* a, int dtype_b, const void* b, int64_t d_up, int64_t d_dn,
+                int64_t ld, double* partial, int nblk, double* out, cudaStream_t s);
+// y = ca * a + cb * b (elementwise, any dtype combination via conversion); scalars on device
+void launch_axpby(int dtype_y, void* y, int dtype_a, const void* a, const double* ca, int dtype_b,
+                  const void* b, const double* cb, int64_t d_up, int64_t d_dn, int64_t ld,
+                  cudaStream_t s);
+void launch_tridiag_lowest(const double* alpha, const double* beta, int n, double* out_eval,
+                           double* out_vec, cudaStream_t s);
+
+struct GroundResult {
+  double E0 = 0, residual = 0, gap = 0;
+  int iters = 0;
+  bool converged = false, degenerate = false;
+};
+
+}  // namespace ed
+
+// The opaque cluster handle.
+struct ed_cluster {
+  ed::ModelHost model;
+  ed::HopParams hp;
+  ed_cluster_desc desc;  // array pointers inside are cleared
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::map<int, std::unique_ptr<ed::SpinTables>> spins;  // by particle number
+  // ground state (FP64, contiguous d_up x d_dn)
+  ed::DevBuf<double> omega;
+  bool have_gs = false;
+  ed::GroundResult gs;
+  int64_t gf_total_steps = 0;
+  int gf_max_steps = 0;
+  ed::SpinTables& tables(int N);
+  ed::SectorView view(int n_up, int n_dn, int64_t ld);
+};

@@ -1,0 +1,209 @@
+// Ground-state driver (Sec. 4.2): host orchestration of the device kernels.  The recursion
+// coefficients stay on the device; the host only reads the tridiagonal eigen-summary every
+// `kCheck` steps to decide convergence.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "ed_common.cuh"
+
+namespace ed {
+
+constexpr int kCheck = 10;
+
+__global__ void k_scale_inv_sqrt(int dt, void* v, const double* nrm2, int64_t du, int64_t dd, int64_t ld) {
+  double f = *nrm2 > 0.0 ? 1.0 / sqrt(*nrm2) : 0.0;
+  const int64_t dim = du * dd;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < dim; idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t u = idx / dd, d = idx - u * dd;
+    int64_t o = u * ld + d;
+    if (dt == ED_FP64)
+      ((double*)v)[o] *= f;
+    else
+      ((float*)v)[o] = (float)((double)((float*)v)[o] * f);
+  }
+}
+
+void axpby_inv_sqrt(int dt, void* v, const double* nrm2, int64_t du, int64_t dd, int64_t ld, cudaStream_t s) {
+  int64_t b = (du * dd + 255) / 256;
+  int g = (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 8));
+  k_scale_inv_sqrt<<<g, 256, 0, s>>>(dt, v, nrm2, du, dd, ld);
+  ED_CHECK_LAUNCH();
+}
+
+__global__ void k_axpy_neg(double* y, const double* a, const double* x, int64_t n) {
+  double f = *a;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] -= f * x[i];
+}
+
+void axpy_neg(double* y, const double* a, const double* x, int64_t n, cudaStream_t s) {
+  int64_t b = (n + 255) / 256;
+  int g = (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 8));
+  k_axpy_neg<<<g, 256, 0, s>>>(y, a, x, n);
+  ED_CHECK_LAUNCH();
+}
+
+
+struct PinnedScalars {
+  double* p = nullptr;
+  PinnedScalars() { ED_CUDA(cudaMallocHost(&p, 16 * sizeof(double))); }
+  ~PinnedScalars() { if (p) cudaFreeHost(p); }
+};
+
+// One Lanczos pass set (first pass + retrace) from start vector `v0` (dtype, normalized in
+// place).  Writes the normalized-by-construction sum_n s_n v_n into omega (FP64).
+struct LanczosRun {
+  int M;
+  DevBuf<double> alpha, beta, beta0, partial, evals, svec, scal;
+  DevBuf<int> active, nsteps;
+  DevBuf<unsigned> counter;
+  LanczosScalars ls;
+  int nblk;
+  LanczosRun(int M_, int nblk_) : M(M_), nblk(nblk_) {
+    alpha.alloc(M + 1);
+    beta.alloc(M + 2);
+    beta0.alloc(1);
+    partial.alloc(std::max(nblk, 1) * 3 + 8);
+    evals.alloc(4);
+    svec.alloc(2 * (M + 2));
+    scal.alloc(8);
+    active.alloc(1);
+    nsteps.alloc(1);
+    counter.alloc(1);
+    ls = LanczosScalars{alpha.p, beta.p, beta0.p, active.p, partial.p, counter.p, M, 1e-13, nsteps.p};
+  }
+  void reset(cudaStream_t s) {
+    const double one = 1.0;
+    const int on = 1;
+    ED_CUDA(cudaMemsetAsync(beta.p, 0, (M + 2) * sizeof(double), s));
+    ED_CUDA(cudaMemcpyAsync(beta0.p, &one, sizeof(double), cudaMemcpyHostToDevice, s));
+    ED_CUDA(cudaMemcpyAsync(active.p, &on, sizeof(int), cudaMemcpyHostToDevice, s));
+    ED_CUDA(cudaMemsetAsync(counter.p, 0, sizeof(unsigned), s));
+  }
+};
+
+static size_t esize(int dtype) { return dtype == ED_FP64 ? sizeof(double) : sizeof(float); }
+
+// Runs pass 1 (until the Ritz estimate < tol_ritz) and the retrace; returns levels used.
+static int lanczos_pass(ed_cluster& c, const SectorView& sv, int dtype, LanczosRun& L, char* V0, char* V1, char* Vstart,
+                        double* omega, double tol_ritz, double* host, bool* breakdown, cudaStream_t s) {
+  const int64_t du = sv.d_up, dd = sv.d_dn, ld = sv.ld, dim = du * dd;
+  const size_t bytes = (size_t)dim * esize(dtype);
+  char* V[2] = {V0, V1};
+  int m = 0;
+  *breakdown = false;
+  for (int pass = 0; pass < 2; ++pass) {
+    L.reset(s);
+    ED_CUDA(cudaMemcpyAsync(V[0], Vstart, bytes, cudaMemcpyDeviceToDevice, s));
+    ED_CUDA(cudaMemsetAsync(V[1], 0, bytes, s));
+    if (pass == 1) launch_axpby(ED_FP64, omega, dtype, V[0], L.svec.p, dtype, nullptr, nullptr, du, dd, ld, s);
+    int cur = 0;
+    const int nmax = pass == 0 ? L.M : m - 1;
+    for (int n = 0; n < nmax; ++n) {
+      launch_lanczos_step(sv, c.hp, dtype, V[cur], V[cur ^ 1], 0, 1, n, L.ls, L.nblk, s);
+      launch_lanczos_next(dtype, V[cur ^ 1], V[cur], du, dd, ld, 0, 1, n, L.ls, pass == 1 ? omega : nullptr, L.svec.p, s);
+      cur ^= 1;
+      if (pass == 0 && ((n + 1) % kCheck == 0 || n + 1 == L.M)) {
+        ED_CUDA(cudaMemcpyAsync(host + 8, L.active.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        ED_CUDA(cudaStreamSynchronize(s));
+        int act = *(int*)(host + 8);
+        int levels = n + 1;
+        if (!act) {
+          // the run stopped at the first level whose b_{n+1} vanished: find it on the host
+          std::vector<double> b(n + 2);
+          ED_CUDA(cudaMemcpy(b.data(), L.beta.p, (n + 2) * sizeof(double), cudaMemcpyDeviceToHost));
+          levels = 1;
+          while (levels < n + 1 && b[levels] > L.ls.btol) ++levels;
+          *breakdown = levels < L.M;
+        }
+        launch_tridiag_lowest(L.alpha.p, L.beta.p, levels, L.evals.p, L.svec.p, s);
+        ED_CUDA(cudaMemcpyAsync(host, L.evals.p, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        ED_CUDA(cudaStreamSynchronize(s));
+        m = levels;
+        if (!act || host[2] < tol_ritz * std::max(1.0, std::fabs(host[0]))) break;
+      }
+    }
+  }
+  return m;
+}
+
+GroundResult run_ground_state(ed_cluster& c, int dtype, double tol, int max_iter, uint64_t seed) {
+  cudaStream_t s = c.stream;
+  const int nu = c.desc.n_up, nd = c.desc.n_dn;
+  SpinTables& tu = c.tables(nu);
+  SpinTables& td = c.tables(nd);
+  (void)tu;
+  (void)td;
+  SectorView sv = c.view(nu, nd, 0);
+  const int64_t du = sv.d_up, dd = sv.d_dn, dim = du * dd;
+  GroundResult R;
+  c.omega.alloc(std::max<int64_t>(dim, 1));
+  PinnedScalars hs;
+  double* host = hs.p;
+  if (dim == 0) throw Error(ED_ERR_INVALID, "empty sector");
+
+  const int nblk = lanczos_blocks(sv);
+  DevBuf<double> y64(dim);  // FP64 work vector for the polish
+  DevBuf<double> scal(8);
+  DevBuf<double> part(nblk + 8);
+  int dt = dtype;
+  int total_iters = 0;
+  bool have_start = false;
+  for (int attempt = 0; attempt < 6; ++attempt) {
+    const size_t bytes = (size_t)dim * esize(dt);
+    DevBuf<char> V0(bytes), V1(bytes), Vs(bytes);
+    if (!have_start) {
+      launch_start_vector(dt, Vs.p, du, dd, dd, seed, s);
+    } else {
+      launch_axpby(dt, Vs.p, ED_FP64, c.omega.p, scal.p + 7, ED_FP64, nullptr, nullptr, du, dd, dd, s);
+    }
+    // normalize the start vector
+    launch_dot(dt, Vs.p, dt, Vs.p, du, dd, dd, part.p, nblk + 8, scal.p + 0, s);
+    axpby_inv_sqrt(dt, Vs.p, scal.p + 0, du, dd, dd, s);  // Vs <- Vs / sqrt(<Vs,Vs>)
+    LanczosRun L(std::max(2, max_iter), nblk);
+    const double tol_ritz = dt == ED_FP64 ? std::min(1e-2, 0.1 * tol) : 1e-7;
+    bool breakdown = false;
+    int m = lanczos_pass(c, sv, dt, L, V0.p, V1.p, Vs.p, c.omega.p, tol_ritz, host, &breakdown, s);
+    total_iters += m;
+    const double lam0 = host[0], lam1 = host[1], ritz = host[2];
+    // FP64 polish: normalize omega, Rayleigh quotient and explicit residual.
+    launch_dot(ED_FP64, c.omega.p, ED_FP64, c.omega.p, du, dd, dd, part.p, nblk + 8, scal.p + 1, s);
+    axpby_inv_sqrt(ED_FP64, c.omega.p, scal.p + 1, du, dd, dd, s);
+    launch_hpsi(sv, c.hp, ED_FP64, c.omega.p, y64.p, s);
+    launch_dot(ED_FP64, c.omega.p, ED_FP64, y64.p, du, dd, dd, part.p, nblk + 8, scal.p + 2, s);
+    axpy_neg(y64.p, scal.p + 2, c.omega.p, dim, s);  // y <- y - E omega
+    launch_dot(ED_FP64, y64.p, ED_FP64, y64.p, du, dd, dd, part.p, nblk + 8, scal.p + 3, s);
+    ED_CUDA(cudaMemcpyAsync(host + 4, scal.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    ED_CUDA(cudaStreamSynchronize(s));
+    const double E = host[6];
+    const double res_abs = std::sqrt(std::max(0.0, host[7]));
+    const double scale = std::max(1.0, std::fabs(E));
+    R.E0 = E;
+    R.residual = res_abs / scale;
+    R.iters = total_iters;
+    R.gap = lam1 - lam0;
+    (void)ritz;
+    bool ok;
+    if (dtype == ED_FP64 || dt == ED_FP64) {
+      ok = R.residual <= tol || breakdown;
+    } else {
+      // FP32 storage: accept when the Kato-Temple bound on the Rayleigh quotient meets 1e-10.
+      double gap = lam1 - E;
+      ok = gap > 0.0 && res_abs * res_abs / gap <= 1e-10 * scale * 0.1;
+    }
+    R.degenerate = (lam1 - lam0) < 1e-8 * std::max(1.0, std::fabs(lam0));
+    if (ok) {
+      R.converged = true;
+      break;
+    }
+    // restart from the current ground-state estimate (FP64 refinement for the FP32 form)
+    const double one = 1.0;
+    ED_CUDA(cudaMemcpyAsync(scal.p + 7, &one, sizeof(double), cudaMemcpyHostToDevice, s));
+    have_start = true;
+    if (dt == ED_FP32) dt = ED_FP64;
+  }
+  return R;
+}
+
+}  // namespace ed

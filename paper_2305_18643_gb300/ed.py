@@ -1,0 +1,221 @@
+"""Thin ctypes binding of libed (include/ed.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls.  All computation happens in
+libed.so's CUDA kernels; there is no CPU path.  If the library has not been built the first
+call raises ``RuntimeError`` (build it with ``python -m paper_2305_18643_gb300.build``).
+Device arrays are passed as integer device pointers (e.g. ``torch.Tensor.data_ptr()``).
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+ED_OK, ED_PENDING, ED_WARN_DEGENERATE, ED_WARN_NOT_CONVERGED = 0, 1, 2, 3
+ED_ERR_INVALID, ED_ERR_OOM, ED_ERR_CUDA, ED_ERR_TOO_LARGE = -1, -2, -3, -5
+ED_ERR_TIMEOUT, ED_ERR_STATE, ED_ERR_NOT_FOUND, ED_ERR_CANCELLED = -6, -7, -8, -9
+ED_FP64, ED_FP32 = 0, 1
+ED_GF_CF, ED_GF_BAND = 0, 1
+ED_AXIS_REAL, ED_AXIS_MATSUBARA = 0, 1
+
+_dp = C.POINTER(C.c_double)
+
+
+class ed_cluster_desc(C.Structure):
+    _fields_ = [("n_sites", C.c_int), ("n_bath", C.c_int), ("t", _dp), ("U", _dp), ("mu", C.c_double),
+                ("eps", _dp), ("theta", _dp), ("n_up", C.c_int), ("n_dn", C.c_int), ("precision", C.c_int),
+                ("gf_method", C.c_int), ("seed", C.c_uint64), ("tol", C.c_double), ("max_iter", C.c_int)]
+
+
+class EDError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("libed status %d: %s" % (status, msg))
+        self.status = status
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """The loaded libed.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError("libed.so not found at %s; build it with `python -m paper_2305_18643_gb300.build`" % path)
+        L = C.CDLL(path)
+        vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int
+        sig = {
+            "ed_cluster_create": (i32, [C.POINTER(ed_cluster_desc), C.POINTER(vp)]),
+            "ed_cluster_destroy": (None, [vp]),
+            "ed_ground_state": (i32, [vp, _dp, _dp, C.POINTER(i32)]),
+            "ed_ground_vector": (i32, [vp, vp, i32]),
+            "ed_green": (i32, [vp, _dp, i32, C.c_double, i32, i32, vp, i32]),
+            "ed_green_stats": (i32, [vp, C.POINTER(i64), C.POINTER(i32)]),
+            "ed_sector_dims": (i32, [vp, i32, i32, C.POINTER(i64), C.POINTER(i64)]),
+            "ed_basis": (i32, [i32, i32, vp, i64, C.POINTER(i64)]),
+            "ed_hop_table": (i32, [vp, i32, vp, vp, vp, i64, C.POINTER(i64), C.POINTER(i32)]),
+            "ed_hpsi": (i32, [vp, i32, i32, i32, vp, vp, i64, vp]),
+            "ed_last_error": (C.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def ed_last_error():
+    return lib().ed_last_error().decode()
+
+
+def _check(st):
+    if st < 0:
+        raise EDError(st, ed_last_error())
+    return st
+
+
+def _arr(a, n):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64).ravel())
+    if a.size != n:
+        raise ValueError("expected %d values, got %d" % (n, a.size))
+    return a
+
+
+def ed_cluster_create(cluster, precision=ED_FP64, gf_method=ED_GF_CF, seed=0, tol=0.0, max_iter=0):
+    """Create a cluster handle from a dict with t, U, mu, eps, theta, n_up, n_dn."""
+    ns = int(np.asarray(cluster["t"]).shape[0])
+    eps = np.asarray(cluster.get("eps", np.zeros(0)), dtype=np.float64).ravel()
+    nb = int(eps.size)
+    keep = [_arr(cluster["t"], ns * ns), _arr(np.broadcast_to(np.asarray(cluster["U"], float), (ns,)), ns),
+            _arr(eps, nb) if nb else None,
+            _arr(cluster.get("theta", np.zeros((ns, 0))), ns * nb) if nb else None]
+    ptr = [k.ctypes.data_as(_dp) if k is not None else None for k in keep]
+    d = ed_cluster_desc(ns, nb, ptr[0], ptr[1], float(cluster["mu"]), ptr[2], ptr[3], int(cluster["n_up"]),
+                        int(cluster["n_dn"]), int(precision), int(gf_method), int(seed) & (2 ** 64 - 1),
+                        float(tol), int(max_iter))
+    h = C.c_void_p()
+    _check(lib().ed_cluster_create(C.byref(d), C.byref(h)))
+    return h
+
+
+def ed_cluster_destroy(h):
+    if h:
+        lib().ed_cluster_destroy(h)
+
+
+def ed_ground_state(h):
+    """Returns (status, E0, residual, iters)."""
+    E0, res, it = C.c_double(), C.c_double(), C.c_int()
+    st = _check(lib().ed_ground_state(h, C.byref(E0), C.byref(res), C.byref(it)))
+    return st, E0.value, res.value, it.value
+
+
+def ed_sector_dims(h, n_up, n_dn):
+    du, dd = C.c_int64(), C.c_int64()
+    _check(lib().ed_sector_dims(h, int(n_up), int(n_dn), C.byref(du), C.byref(dd)))
+    return du.value, dd.value
+
+
+def ed_ground_vector(h, n_up, n_dn, out_ptr=None):
+    """Ground state psi[u, d] (FP64).  With out_ptr (device pointer) it is copied there."""
+    if out_ptr is not None:
+        _check(lib().ed_ground_vector(h, C.c_void_p(out_ptr), 1))
+        return None
+    du, dd = ed_sector_dims(h, n_up, n_dn)
+    out = np.empty((du, dd))
+    _check(lib().ed_ground_vector(h, out.ctypes.data_as(C.c_void_p), 0))
+    return out
+
+
+def ed_green(h, omega, eta, n_sites, axis=ED_AXIS_REAL, spin=0, out_ptr=None):
+    """G[nz, n_sites, n_sites] complex128 (host), or written to device pointer out_ptr.
+    Returns (status, G or None)."""
+    om = _arr(omega, np.asarray(omega).size)
+    if out_ptr is not None:
+        st = _check(lib().ed_green(h, om.ctypes.data_as(_dp), om.size, float(eta), int(axis), int(spin),
+                                   C.c_void_p(out_ptr), 1))
+        return st, None
+    G = np.empty((om.size, n_sites, n_sites), dtype=np.complex128)
+    st = _check(lib().ed_green(h, om.ctypes.data_as(_dp), om.size, float(eta), int(axis), int(spin),
+                               G.ctypes.data_as(C.c_void_p), 0))
+    return st, G
+
+
+def ed_green_stats(h):
+    tot, mx = C.c_int64(), C.c_int()
+    _check(lib().ed_green_stats(h, C.byref(tot), C.byref(mx)))
+    return tot.value, mx.value
+
+
+def ed_basis(L, N):
+    dim = C.c_int64()
+    lib().ed_basis(int(L), int(N), None, 0, C.byref(dim))
+    out = np.empty(max(dim.value, 1), dtype=np.uint32)
+    _check(lib().ed_basis(int(L), int(N), out.ctypes.data_as(C.c_void_p), out.size, C.byref(dim)))
+    return out[: dim.value]
+
+
+def ed_hop_table(h, N, L):
+    """(row_ptr int32[d+1], entries uint32[nnz], values float64[nvals]) of one spin with N particles."""
+    nnz, nv = C.c_int64(), C.c_int()
+    lib().ed_hop_table(h, int(N), None, None, None, 0, C.byref(nnz), C.byref(nv))
+    import math
+    d = math.comb(L, N)
+    ptr = np.empty(d + 1, dtype=np.int32)
+    ent = np.empty(max(nnz.value, 1), dtype=np.uint32)
+    vals = np.empty(128, dtype=np.float64)
+    _check(lib().ed_hop_table(h, int(N), ptr.ctypes.data_as(C.c_void_p), ent.ctypes.data_as(C.c_void_p),
+                              vals.ctypes.data_as(C.c_void_p), ent.size, C.byref(nnz), C.byref(nv)))
+    return ptr, ent[: nnz.value], vals[: nv.value]
+
+
+def ed_hpsi(h, n_up, n_dn, dtype, x_ptr, y_ptr, ld=0, stream=0):
+    """y = H x on device pointers (FP64 or FP32), asynchronous on `stream` (0 = the cluster's)."""
+    _check(lib().ed_hpsi(h, int(n_up), int(n_dn), int(dtype), C.c_void_p(x_ptr), C.c_void_p(y_ptr), int(ld),
+                         C.c_void_p(stream) if stream else None))
+
+
+class Cluster:
+    """Owning wrapper of a cluster handle (context manager)."""
+
+    def __init__(self, cluster, **kw):
+        self.desc = cluster
+        self.h = ed_cluster_create(cluster, **kw)
+        self.ns = int(np.asarray(cluster["t"]).shape[0])
+        self.n_up, self.n_dn = int(cluster["n_up"]), int(cluster["n_dn"])
+
+    def close(self):
+        if self.h:
+            ed_cluster_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def ground_state(self):
+        return ed_ground_state(self.h)
+
+    def ground_vector(self):
+        return ed_ground_vector(self.h, self.n_up, self.n_dn)
+
+    def green(self, omega, eta, axis=ED_AXIS_REAL, spin=0):
+        return ed_green(self.h, omega, eta, self.ns, axis, spin)[1]
