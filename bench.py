@@ -1,0 +1,317 @@
+#!/usr/bin/env python3
+"""Benchmark of the exact-diagonalization solver: solves/s on one synthetic cluster workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload 4x4|cdmft|2x4] [--precision fp32|fp64] [--gf band|cf|none]
+
+A step is one whole solve through the C ABI: ed_cluster_create (basis and hopping tables),
+ed_ground_state (Lanczos, retrace, FP64 polish) and ed_green (starting vectors, Lanczos /
+band Lanczos, G on the frequency grid), then ed_cluster_destroy.  Under torchrun every rank
+solves its own seeded instance of the workload (independent problems, no data exchange):
+weak scaling, value = solves of all ranks / max-over-ranks time.
+
+The JSON line carries the kernel roofline of the fused Lanczos step (the dominant kernel),
+measured with CUDA events on the library's stream over the timed region, and a CPU baseline:
+the oracle timed on a bounded sample of the same workload.  ``--impl reference`` times that
+oracle instead of the GPU path.
+"""
+
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2305_18643_gb300 import workloads as W  # noqa: E402
+
+WORKLOADS = {
+    # name: (generator(instance), label, default precision, default gf, frequencies)
+    "4x4": (W.periodic_4x4, "4x4 periodic Hubbard, t=-1, t'=0.3 seeded sign, U=8, mu=4, N_up=N_dn=8 (d=12870^2)",
+            "fp32", "band", 1000),
+    "cdmft": (W.cdmft_2x2_bath, "2x2 plaquette + 8 bath, U=8, mu=4, N_up=N_dn=6 (d=924^2)", "fp32", "cf", 1000),
+    "2x4": (lambda instance=0: W.plain_2x4(), "2x4 open Hubbard, U=4, mu=2, N_up=N_dn=4 (d=70^2)", "fp64", "cf", 1000),
+}
+ETA = 0.05
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="4x4")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default=None)
+    ap.add_argument("--gf", choices=["band", "cf", "none"], default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ----------------------------------------------------------------------------- measurement helpers
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=10)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for r in csv.reader(io.StringIO(out)):
+            if len(r) >= 9:
+                self.rows.append([x.strip() for x in r])
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in self.rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        load = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": float(np.median(load)) if load else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def measured_peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(p))["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel_file, summary_file):
+    """Per-launch DRAM bytes from a committed ncu summary, if it was taken on this kernel source."""
+    p = os.path.join(ROOT, "profiles", summary_file)
+    src = os.path.join(ROOT, "paper_2305_18643_gb300", "csrc", kernel_file)
+    try:
+        txt = open(p).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+        t = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", txt)
+        if m and t and m.group(1) == sha:
+            return float(t.group(1))
+    except OSError:
+        pass
+    return None
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_2305_18643_gb300 import build, ed
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    build.build()
+    ed.lib()
+    gen, label, prec_d, gf_d, nfreq = WORKLOADS[args.workload]
+    prec = args.precision or prec_d
+    gf = args.gf or gf_d
+    c = gen(instance=rank)
+    ns = c["t"].shape[0]
+    omega = W.real_grid(nfreq)
+    precision = ed.ED_FP32 if prec == "fp32" else ed.ED_FP64
+    gf_method = ed.ED_GF_BAND if gf == "band" else ed.ED_GF_CF
+    G_dev = torch.empty((nfreq, ns, ns, 2), dtype=torch.float64, device="cuda")
+    G_host = torch.empty((nfreq, ns, ns, 2), dtype=torch.float64).pin_memory()
+    info = {}
+
+    def solve(to_host):
+        h = ed.ed_cluster_create(c, precision=precision, gf_method=gf_method, seed=1234 + rank)
+        try:
+            st, E0, res, it = ed.ed_ground_state(h)
+            info.update(E0=E0, residual=res, gs_iters=it, gs_status=st)
+            if gf != "none":
+                if to_host:
+                    st, _ = ed.ed_green(h, omega, ETA, ns, out_ptr=G_dev.data_ptr())
+                    G_host.copy_(G_dev)
+                else:
+                    ed.ed_green(h, omega, ETA, ns, out_ptr=G_dev.data_ptr())
+                info["gf_steps"], info["gf_max_steps"] = ed.ed_green_stats(h)
+        finally:
+            ed.ed_cluster_destroy(h)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+
+    def timed(to_host, steps, profile):
+        barrier()
+        if profile:
+            ed.ed_profile_enable(1)
+        launches0 = ed.ed_launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            solve(to_host)
+        e1.record()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        launches = ed.ed_launch_count() - launches0
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, launches
+
+    for _ in range(args.warmup):
+        solve(False)
+    with ClockSampler(local_rank) as clk:
+        ms, launches = timed(False, args.steps, True)
+    prof = {k: ed.ed_profile_read(k) for k in range(ed.ED_K_COUNT)}
+    ed.ed_profile_enable(0)
+    e2e = None
+    if not args.no_e2e:
+        ms_e2e, _ = timed(True, args.steps, False)
+        e2e = {"value": world * args.steps / (ms_e2e / 1e3), "unit": "solves/s",
+               "h2d_bytes_per_step": int(8 * (ns * ns + ns + len(c["eps"]) + c["theta"].size + 1)),
+               "d2h_bytes_per_step": int(G_host.numel() * 8 if gf != "none" else 0) + 8}
+    value = world * args.steps / (ms / 1e3)
+    n_step, ms_step, by_step = prof[ed.ED_K_LANCZOS_STEP]
+    peak, peak_kind = measured_peak_hbm()
+    achieved = (by_step / 1e9) / (ms_step / 1e3) if ms_step > 0 else None
+    traffic = ncu_traffic("hpsi.cu", "lanczos_step_4x4.txt") if args.workload == "4x4" else None
+    hpsi_per_solve = (prof[ed.ED_K_LANCZOS_STEP][0] + prof[ed.ED_K_HPSI][0]) / max(args.steps, 1)
+    result = {
+        "metric": "ED solves/s (H.psi HBM GB/s and % roofline in `roofline`)",
+        "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 vectors, f64 reductions" if prec == "fp32" else "f64",
+        "data": "synthetic (seeded cluster parameters)",
+        "config": {"workload": args.workload + ": " + label, "precision": prec, "green_function": gf,
+                   "n_freq": nfreq if gf != "none" else 0, "eta": ETA,
+                   "l2": "inputs larger than L2 (state vectors 0.66-1.33 GB)" if args.workload == "4x4"
+                   else "L2 flushed by the step's own traffic",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "kernel": "lanczos_step (fused H.psi + Lanczos epilogue)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
+                     "launches": n_step, "avg_launch_ms": ms_step / max(n_step, 1),
+                     "alg_bytes_per_launch": by_step / max(n_step, 1)},
+        "solve": {k: info.get(k) for k in ("E0", "residual", "gs_iters", "gs_status", "gf_steps", "gf_max_steps")},
+        "kernels_ms": {ed.ed_profile_kernel_name(k): round(v[1], 3) for k, v in prof.items() if v[0]},
+        "hpsi_per_solve": hpsi_per_solve,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(args.workload, c, hpsi_per_solve)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return result
+
+
+# ----------------------------------------------------------------------------- CPU (oracle) arm
+def oracle_sample(workload, c, rows_target_s=10.0):
+    """Time the oracle's factorized H.psi (Eq. factorized) on a block of rows of the workload's
+    ground-state sector; returns (seconds per full H.psi, sample description)."""
+    import oracle as O
+    m = O.Model(c["t"], c["U"], c["mu"], c["eps"], c["theta"])
+    du = len(O.sector_basis(m.L, c["n_up"]))
+    dd = len(O.sector_basis(m.L, c["n_dn"]))
+    psi = np.random.default_rng(0).standard_normal((du, dd))
+    nrows = max(1, min(du, 64))
+    while True:
+        rows = np.arange(nrows)
+        t0 = time.perf_counter()
+        O.apply_h_rows(m, c["n_up"], c["n_dn"], psi, rows)
+        dt = time.perf_counter() - t0
+        if dt > rows_target_s / 4 or nrows == du:
+            break
+        nrows = min(du, nrows * 4)
+    per_hpsi = dt * du / nrows
+    return per_hpsi, "oracle apply_h_rows (scipy factorized H.psi, FP64) on %d of %d rows of the %dx%d sector, " \
+                     "scaled to a full H.psi" % (nrows, du, du, dd)
+
+
+def cpu_baseline(workload, c, hpsi_per_solve):
+    per_hpsi, desc = oracle_sample(workload, c)
+    return {"value": 1.0 / (per_hpsi * max(hpsi_per_solve, 1.0)), "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": desc + "; solves/s = 1 / (t_hpsi x %.0f H.psi per solve, the count of the GPU run)"
+                      % hpsi_per_solve}
+
+
+def run_reference(args, rank, world):
+    gen, label, prec_d, gf_d, nfreq = WORKLOADS[args.workload]
+    c = gen(instance=0)
+    hpsi_per_solve = {"4x4": 1000.0, "cdmft": 2000.0, "2x4": 20000.0}[args.workload]
+    for _ in range(args.warmup):
+        oracle_sample(args.workload, c, rows_target_s=2.0)
+    t0 = time.perf_counter()
+    per = []
+    for _ in range(args.steps):
+        p, desc = oracle_sample(args.workload, c, rows_target_s=4.0)
+        per.append(p)
+    total = time.perf_counter() - t0
+    value = 1.0 / (float(np.mean(per)) * hpsi_per_solve)
+    return {"impl": "reference", "metric": "ED solves/s (H.psi HBM GB/s and % roofline in `roofline`)",
+            "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded cluster parameters)",
+            "config": {"workload": args.workload + ": " + label, "precision": "fp64 (oracle)"},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": desc + "; solves/s = 1 / (t_hpsi x %.0f H.psi per solve)" % hpsi_per_solve},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world, local_rank = dist_env()
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        print(json.dumps(run_reference(args, rank, world)))
+        return
+    res = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

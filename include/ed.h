@@ -138,6 +138,37 @@ ed_status ed_hop_table(ed_cluster* c, int N, int32_t* row_ptr, uint32_t* entries
 ed_status ed_hpsi(ed_cluster* c, int n_up, int n_dn, int dtype, const void* x, void* y, int64_t ld,
                   void* stream);
 
+/* ---- measurement of the library's own kernels (no counterpart in the paper) --------------- */
+
+/* Kernel families. */
+enum {
+  ED_K_TABLES = 0,        /* basis, rank and hopping-table construction */
+  ED_K_HPSI = 1,          /* standalone H.psi (ed_hpsi, ground-state polish) */
+  ED_K_LANCZOS_STEP = 2,  /* fused H.psi + Lanczos epilogue: algorithmic bytes 3 x d x elem */
+  ED_K_LANCZOS_NEXT = 3,  /* v_{n+1} = (w - a v_n) / b */
+  ED_K_TRIDIAG = 4,
+  ED_K_VECTOR = 5,        /* reductions, scaling, start vectors */
+  ED_K_APPLY_COP = 6,     /* c+ / c applied to the ground state */
+  ED_K_GF_EVAL = 7,       /* Green-function evaluation and assembly on the grid */
+  ED_K_BAND = 8,          /* band-Lanczos orthogonalization */
+  ED_K_COUNT = 9
+};
+
+/* Turns per-family timing on (1) or off (0) and clears the totals.  While on, each launch of a
+ * family is bracketed by CUDA events on the stream it is launched on. */
+ed_status ed_profile_enable(int on);
+
+/* Totals since the last ed_profile_enable: launches, summed event time (ms) and summed
+ * algorithmic bytes (the bytes the method must move; 0 for families without a byte model).
+ * Synchronizes with the recorded events.  Any output may be NULL. */
+ed_status ed_profile_read(int kernel, int64_t* launches, double* total_ms, double* alg_bytes);
+
+/* Name of a kernel family ("lanczos_step", ...). */
+const char* ed_profile_kernel_name(int kernel);
+
+/* Number of kernels this library has launched in the process so far (always counted). */
+int64_t ed_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

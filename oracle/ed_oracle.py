@@ -47,7 +47,7 @@ import scipy.sparse.linalg as spla
 __all__ = [
     "popcount", "one_body_matrix", "Model", "sector_basis", "basis_index",
     "hopping_matrix", "hop_entries", "interaction_diagonal", "sector_hamiltonian",
-    "apply_h", "apply_h_sampled", "jw_hamiltonian_dense", "ground_state",
+    "apply_h", "apply_h_rows", "apply_h_sampled", "jw_hamiltonian_dense", "ground_state",
     "apply_cdag", "apply_c", "density", "green_exact", "lanczos_coefficients",
     "cf_green", "green_cf", "band_lanczos_lehmann", "lehmann_green", "green_band",
     "frequency_grid",
@@ -219,6 +219,18 @@ def sector_hamiltonian(model, n_up, n_dn):
 def apply_h(op, psi):
     """H psi for psi[u, d] (2-D array) using the factorized form of Eq. factorized."""
     return op.matvec(np.asarray(psi).reshape(-1)).reshape(op.shape2)
+
+
+def apply_h_rows(model, n_up, n_dn, psi, rows):
+    """Rows y[rows, :] of y = H psi from Eq. factorized, without building the full operator:
+    y[u, :] = sum_u' K_up[u, u'] psi[u', :] + psi[u, :] K_dn^T + V_int[u, :] * psi[u, :]."""
+    rows = np.asarray(rows)
+    B_up = sector_basis(model.L, n_up)
+    B_dn = sector_basis(model.L, n_dn)
+    K_up = hopping_matrix(model.h, n_up)
+    K_dn = hopping_matrix(model.h, n_dn)
+    V = interaction_diagonal(model, B_up[rows], B_dn)
+    return K_up[rows] @ psi + (K_dn @ psi[rows].T).T + V * psi[rows]
 
 
 def apply_h_sampled(op, psi, us, ds):

@@ -40,6 +40,24 @@ void set_last_error(const std::string& msg);
 
 #define ED_CHECK_LAUNCH() ED_CUDA(cudaGetLastError())
 
+// Kernel families timed by the profiler (ed_profile_* in ed.h).
+enum KernelId {
+  K_TABLES = 0, K_HPSI, K_LANCZOS_STEP, K_LANCZOS_NEXT, K_TRIDIAG, K_VECTOR, K_APPLY_COP, K_GF_EVAL,
+  K_BAND, K_COUNT
+};
+const char* kernel_name(int kid);
+
+// Counts every launch of the library; when profiling is on, brackets the launch with CUDA
+// events on the launching stream and records the algorithmic bytes it moves.
+struct ProfScope {
+  int kid;
+  cudaStream_t s;
+  double bytes;
+  cudaEvent_t e0 = nullptr;
+  ProfScope(int kid_, cudaStream_t s_, double bytes_);
+  ~ProfScope();
+};
+
 // Device buffer with RAII ownership (cudaMalloc / cudaFree).
 template <typename T>
 struct DevBuf {

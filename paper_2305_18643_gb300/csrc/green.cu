@@ -275,14 +275,14 @@ static bool cf_part(ed_cluster& c, int spin, bool electron, int dtype, const Dev
     ED_CUDA(cudaMemsetAsync(counter.p, 0, rc * sizeof(unsigned), s));
     ED_CUDA(cudaMemsetAsync(prev.p, 0, (size_t)rc * nzs * sizeof(double2), s));
     dim3 g(ggrid(dim), rc);
-    k_apply_cop<<<g, kGT, 0, s>>>(c.omega.p, dd_s, dst.basis.p, rv, spin, electron ? 1 : 0, extra, druns.p + r0, dtype,
-                                  V0.p, dim, du, dd, dd);
+    { ProfScope ps_(K_APPLY_COP, s, 0.0); k_apply_cop<<<g, kGT, 0, s>>>(c.omega.p, dd_s, dst.basis.p, rv, spin, electron ? 1 : 0, extra, druns.p + r0, dtype,
+                                  V0.p, dim, du, dd, dd); }
     ED_CHECK_LAUNCH();
-    k_run_norm_partial<<<dim3(nblk, rc), kGT, 0, s>>>(dtype, V0.p, dim, du, dd, dd, partial.p);
+    { ProfScope ps_(K_VECTOR, s, 0.0); k_run_norm_partial<<<dim3(nblk, rc), kGT, 0, s>>>(dtype, V0.p, dim, du, dd, dd, partial.p); }
     ED_CHECK_LAUNCH();
-    k_run_norm_finish<<<rc, kGT, 0, s>>>(partial.p, nblk, b0sq.p, beta0.p, active.p);
+    { ProfScope ps_(K_VECTOR, s, 0.0); k_run_norm_finish<<<rc, kGT, 0, s>>>(partial.p, nblk, b0sq.p, beta0.p, active.p); }
     ED_CHECK_LAUNCH();
-    k_run_scale<<<g, kGT, 0, s>>>(dtype, V0.p, dim, du, dd, dd, beta0.p);
+    { ProfScope ps_(K_VECTOR, s, 0.0); k_run_scale<<<g, kGT, 0, s>>>(dtype, V0.p, dim, du, dd, dd, beta0.p); }
     ED_CHECK_LAUNCH();
     // relative breakdown test needs b_0 = 1 for the normalized start
     LanczosScalars ls{alpha.p, beta.p, beta0.p, active.p, partial.p, counter.p, M, 0.0, nsteps.p};
@@ -303,8 +303,8 @@ static bool cf_part(ed_cluster& c, int spin, bool electron, int dtype, const Dev
       cur ^= 1;
       if (n + 1 == next_check || n + 1 == M) {
         ED_CUDA(cudaMemsetAsync(nact.p, 0, sizeof(int), s));
-        k_cf_check<<<rc, kGT, 0, s>>>(alpha.p, beta.p, b0sq.p, nsteps.p, M, active.p, hits.p, c.gs.E0,
-                                      electron ? -1.0 : 1.0, zd.p, nz, zstride, prev.p, opt.tol, nact.p);
+        { ProfScope ps_(K_GF_EVAL, s, 0.0); k_cf_check<<<rc, kGT, 0, s>>>(alpha.p, beta.p, b0sq.p, nsteps.p, M, active.p, hits.p, c.gs.E0,
+                                      electron ? -1.0 : 1.0, zd.p, nz, zstride, prev.p, opt.tol, nact.p); }
         ED_CHECK_LAUNCH();
         ED_CUDA(cudaMemcpyAsync(host_active, nact.p, sizeof(int), cudaMemcpyDeviceToHost, s));
         ED_CUDA(cudaStreamSynchronize(s));
@@ -312,8 +312,8 @@ static bool cf_part(ed_cluster& c, int spin, bool electron, int dtype, const Dev
         next_check = n + 1 + std::max(32, (n + 1) / 8);
       }
     }
-    k_cf_eval_all<<<dim3((nz + kGT - 1) / kGT, rc), kGT, 0, s>>>(alpha.p, beta.p, b0sq.p, nsteps.p, M, c.gs.E0,
-                                                                  electron ? -1.0 : 1.0, zd.p, nz, Gk + (int64_t)r0 * nz, nz);
+    { ProfScope ps_(K_GF_EVAL, s, 0.0); k_cf_eval_all<<<dim3((nz + kGT - 1) / kGT, rc), kGT, 0, s>>>(alpha.p, beta.p, b0sq.p, nsteps.p, M, c.gs.E0,
+                                                                  electron ? -1.0 : 1.0, zd.p, nz, Gk + (int64_t)r0 * nz, nz); }
     ED_CHECK_LAUNCH();
     std::vector<int> st(rc);
     ED_CUDA(cudaMemcpyAsync(st.data(), nsteps.p, rc * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -339,7 +339,7 @@ void run_green_cf(ed_cluster& c, int spin, const double2* z_host, int nz, double
   c.gf_max_steps = 0;
   bool he = cf_part(c, spin, true, dtype, zd, nz, Ge.p, opt, &c.gf_total_steps, &c.gf_max_steps);
   bool hh = cf_part(c, spin, false, dtype, zd, nz, Gh.p, opt, &c.gf_total_steps, &c.gf_max_steps);
-  k_gf_combine<<<ggrid((int64_t)nz * p * p), kGT, 0, s>>>(he ? Ge.p : nullptr, hh ? Gh.p : nullptr, p, nz, G_dev);
+  { ProfScope ps_(K_GF_EVAL, s, 0.0); k_gf_combine<<<ggrid((int64_t)nz * p * p), kGT, 0, s>>>(he ? Ge.p : nullptr, hh ? Gh.p : nullptr, p, nz, G_dev); }
   ED_CHECK_LAUNCH();
   ED_CUDA(cudaStreamSynchronize(s));
 }

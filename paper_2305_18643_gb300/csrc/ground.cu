@@ -27,6 +27,7 @@ __global__ void k_scale_inv_sqrt(int dt, void* v, const double* nrm2, int64_t du
 void axpby_inv_sqrt(int dt, void* v, const double* nrm2, int64_t du, int64_t dd, int64_t ld, cudaStream_t s) {
   int64_t b = (du * dd + 255) / 256;
   int g = (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 8));
+  ProfScope ps_(K_VECTOR, s, 0.0);
   k_scale_inv_sqrt<<<g, 256, 0, s>>>(dt, v, nrm2, du, dd, ld);
   ED_CHECK_LAUNCH();
 }
@@ -40,6 +41,7 @@ __global__ void k_axpy_neg(double* y, const double* a, const double* x, int64_t 
 void axpy_neg(double* y, const double* a, const double* x, int64_t n, cudaStream_t s) {
   int64_t b = (n + 255) / 256;
   int g = (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 8));
+  ProfScope ps_(K_VECTOR, s, 0.0);
   k_axpy_neg<<<g, 256, 0, s>>>(y, a, x, n);
   ED_CHECK_LAUNCH();
 }

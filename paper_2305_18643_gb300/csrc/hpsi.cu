@@ -187,6 +187,8 @@ int lanczos_blocks(const SectorView& sv) { return grid_for(sv.d_up * sv.d_dn); }
 
 void launch_hpsi(const SectorView& sv, const HopParams& hp, int dtype, const void* x, void* y, cudaStream_t s) {
   int g = grid_for(sv.d_up * sv.d_dn);
+  const double es = dtype == ED_FP64 ? 8.0 : 4.0;
+  ProfScope ps_(K_HPSI, s, 2.0 * es * (double)(sv.d_up * sv.d_dn));
   if (dtype == ED_FP64)
     k_hpsi_flat<double><<<g, kThreads, 0, s>>>(sv, hp, (const double*)x, (double*)y);
   else
@@ -199,6 +201,8 @@ void launch_lanczos_step(const SectorView& sv, const HopParams& hp, int dtype, c
   int g = grid_for(sv.d_up * sv.d_dn);
   if (g > nblk_cap) throw Error(ED_ERR_INVALID, "partial buffer too small");
   dim3 grid(g, runs);
+  const double es = dtype == ED_FP64 ? 8.0 : 4.0;
+  ProfScope ps_(K_LANCZOS_STEP, s, 3.0 * es * (double)(sv.d_up * sv.d_dn) * runs);
   if (dtype == ED_FP64)
     k_lanczos_step<double><<<grid, kThreads, 0, s>>>(sv, hp, (const double*)X, (double*)XP, vstride, n, ls);
   else

@@ -61,6 +61,8 @@ __global__ void __launch_bounds__(kVT) k_lanczos_next(T* __restrict__ W0, const 
 void launch_lanczos_next(int dtype, void* W, const void* X, int64_t d_up, int64_t d_dn, int64_t ld, int64_t vstride,
                          int runs, int n, const LanczosScalars& ls, void* omega, const double* coef, cudaStream_t s) {
   dim3 g(vgrid(d_up * d_dn), runs);
+  const double es = dtype == ED_FP64 ? 8.0 : 4.0;
+  ProfScope ps_(K_LANCZOS_NEXT, s, (3.0 * es + (omega ? 16.0 : 0.0)) * (double)(d_up * d_dn) * runs);
   if (dtype == ED_FP64)
     k_lanczos_next<double><<<g, kVT, 0, s>>>((double*)W, (const double*)X, d_up, d_dn, ld, vstride, n, ls,
                                               (double*)omega, coef);
@@ -88,6 +90,7 @@ __global__ void k_start_vector(int dt, void* v, int64_t d_up, int64_t d_dn, int6
 }
 
 void launch_start_vector(int dtype, void* v, int64_t d_up, int64_t d_dn, int64_t ld, uint64_t seed, cudaStream_t s) {
+  ProfScope ps_(K_VECTOR, s, 0.0);
   k_start_vector<<<vgrid(d_up * d_dn), kVT, 0, s>>>(dtype, v, d_up, d_dn, ld, seed);
   ED_CHECK_LAUNCH();
 }
@@ -129,8 +132,12 @@ __global__ void k_sum_partials(const double* __restrict__ partial, int n, double
 void launch_dot(int dta, const void* a, int dtb, const void* b, int64_t d_up, int64_t d_dn, int64_t ld, double* partial,
                 int nblk, double* out, cudaStream_t s) {
   int g = std::min(vgrid(d_up * d_dn), nblk);
-  k_dot_partial<<<g, kVT, 0, s>>>(dta, a, dtb, b, d_up, d_dn, ld, partial);
-  ED_CHECK_LAUNCH();
+  {
+    ProfScope ps_(K_VECTOR, s, 0.0);
+    k_dot_partial<<<g, kVT, 0, s>>>(dta, a, dtb, b, d_up, d_dn, ld, partial);
+    ED_CHECK_LAUNCH();
+  }
+  ProfScope ps_(K_VECTOR, s, 0.0);
   k_sum_partials<<<1, kVT, 0, s>>>(partial, g, out);
   ED_CHECK_LAUNCH();
 }
@@ -158,6 +165,7 @@ __global__ void k_axpby(int dty, void* y, int dta, const void* a, const double* 
 
 static void axpby(int dty, void* y, int dta, const void* a, const double* ca, int dtb, const void* b, const double* cb,
                   int64_t d_up, int64_t d_dn, int64_t ld, cudaStream_t s, int inv_sqrt_a = 0, int neg_b = 0) {
+  ProfScope ps_(K_VECTOR, s, 0.0);
   k_axpby<<<vgrid(d_up * d_dn), kVT, 0, s>>>(dty, y, dta, a, ca, dtb, b, cb, d_up, d_dn, ld, inv_sqrt_a, neg_b);
   ED_CHECK_LAUNCH();
 }
@@ -260,6 +268,7 @@ __global__ void __launch_bounds__(kVT) k_tridiag_lowest(const double* __restrict
 
 void launch_tridiag_lowest(const double* alpha, const double* beta, int n, double* out_eval, double* out_vec,
                            cudaStream_t s) {
+  ProfScope ps_(K_TRIDIAG, s, 0.0);
   k_tridiag_lowest<<<1, kVT, 0, s>>>(alpha, beta, n, out_eval, out_vec);
   ED_CHECK_LAUNCH();
 }

@@ -175,12 +175,12 @@ std::unique_ptr<SpinTables> build_spin_tables(const ModelHost& m, int N, cudaStr
   t->ediag.alloc(std::max<int64_t>(dim, 1));
   t->ediag32.alloc(std::max<int64_t>(dim, 1));
   if (dim > 0) {
-    k_unrank<<<nblocks(dim, bs), bs, 0, s>>>(m.L, N, dim, bn, t->basis.p);
+    { ProfScope ps_(K_TABLES, s, 0.0); k_unrank<<<nblocks(dim, bs), bs, 0, s>>>(m.L, N, dim, bn, t->basis.p); }
     ED_CHECK_LAUNCH();
   }
-  k_rank_lo<<<nblocks(int64_t(1) << t->split, bs), bs, 0, s>>>(t->split, bn, t->rank_lo.p);
+  { ProfScope ps_(K_TABLES, s, 0.0); k_rank_lo<<<nblocks(int64_t(1) << t->split, bs), bs, 0, s>>>(t->split, bn, t->rank_lo.p); }
   ED_CHECK_LAUNCH();
-  k_rank_hi<<<nblocks(int64_t(1) << (m.L - t->split), bs), bs, 0, s>>>(m.L, N, t->split, bn, t->rank_hi.p);
+  { ProfScope ps_(K_TABLES, s, 0.0); k_rank_hi<<<nblocks(int64_t(1) << (m.L - t->split), bs), bs, 0, s>>>(m.L, N, t->split, bn, t->rank_hi.p); }
   ED_CHECK_LAUNCH();
 
   std::vector<PairDev> hp(m.pair_a.size());
@@ -195,10 +195,10 @@ std::unique_ptr<SpinTables> build_spin_tables(const ModelHost& m, int N, cudaStr
   if (npairs) ED_CUDA(cudaMemcpyAsync(dpairs.p, hp.data(), npairs * sizeof(PairDev), cudaMemcpyHostToDevice, s));
   DevBuf<int32_t> cnt(std::max<int64_t>(dim, 1));
   if (dim > 0) {
-    k_hop_count<<<nblocks(dim, bs), bs, 0, s>>>(dim, t->basis.p, dpairs.p, npairs, cnt.p);
+    { ProfScope ps_(K_TABLES, s, 0.0); k_hop_count<<<nblocks(dim, bs), bs, 0, s>>>(dim, t->basis.p, dpairs.p, npairs, cnt.p); }
     ED_CHECK_LAUNCH();
   }
-  k_scan_one_block<<<1, 1024, 0, s>>>(cnt.p, dim, t->ptr.p);
+  { ProfScope ps_(K_TABLES, s, 0.0); k_scan_one_block<<<1, 1024, 0, s>>>(cnt.p, dim, t->ptr.p); }
   ED_CHECK_LAUNCH();
   int32_t nnz = 0;
   ED_CUDA(cudaMemcpyAsync(&nnz, t->ptr.p + dim, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -207,13 +207,13 @@ std::unique_ptr<SpinTables> build_spin_tables(const ModelHost& m, int N, cudaStr
   t->ent.alloc(std::max<int64_t>(nnz, 1));
   RankView rv{t->rank_lo.p, t->rank_hi.p, t->split, (uint32_t)((1u << t->split) - 1u)};
   if (dim > 0 && nnz > 0) {
-    k_hop_fill<<<nblocks(dim, bs), bs, 0, s>>>(dim, t->basis.p, rv, dpairs.p, npairs, t->ptr.p, t->ent.p);
+    { ProfScope ps_(K_TABLES, s, 0.0); k_hop_fill<<<nblocks(dim, bs), bs, 0, s>>>(dim, t->basis.p, rv, dpairs.p, npairs, t->ptr.p, t->ent.p); }
     ED_CHECK_LAUNCH();
   }
   Diag32 hd;
   for (int a = 0; a < kMaxOrb; ++a) hd.h[a] = a < m.L ? m.h[a * m.L + a] : 0.0;
   if (dim > 0) {
-    k_ediag<<<nblocks(dim, bs), bs, 0, s>>>(dim, m.L, t->basis.p, hd, t->ediag.p, t->ediag32.p);
+    { ProfScope ps_(K_TABLES, s, 0.0); k_ediag<<<nblocks(dim, bs), bs, 0, s>>>(dim, m.L, t->basis.p, hd, t->ediag.p, t->ediag32.p); }
     ED_CHECK_LAUNCH();
   }
   ED_CUDA(cudaStreamSynchronize(s));  // dpairs and cnt are released on return
@@ -224,7 +224,7 @@ void basis_to_host(int L, int N, uint32_t* out, int64_t dim) {
   static const Binom bn = make_binom();
   DevBuf<uint32_t> d(std::max<int64_t>(dim, 1));
   if (dim > 0) {
-    k_unrank<<<nblocks(dim, 256), 256>>>(L, N, dim, bn, d.p);
+    { ProfScope ps_(K_TABLES, 0, 0.0); k_unrank<<<nblocks(dim, 256), 256>>>(L, N, dim, bn, d.p); }
     ED_CHECK_LAUNCH();
     ED_CUDA(cudaMemcpy(out, d.p, dim * sizeof(uint32_t), cudaMemcpyDeviceToHost));
   }

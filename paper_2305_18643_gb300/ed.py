@@ -65,6 +65,10 @@ def lib():
             "ed_hop_table": (i32, [vp, i32, vp, vp, vp, i64, C.POINTER(i64), C.POINTER(i32)]),
             "ed_hpsi": (i32, [vp, i32, i32, i32, vp, vp, i64, vp]),
             "ed_last_error": (C.c_char_p, []),
+            "ed_profile_enable": (i32, [i32]),
+            "ed_profile_read": (i32, [i32, C.POINTER(i64), _dp, _dp]),
+            "ed_profile_kernel_name": (C.c_char_p, [i32]),
+            "ed_launch_count": (i64, []),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -183,6 +187,29 @@ def ed_hpsi(h, n_up, n_dn, dtype, x_ptr, y_ptr, ld=0, stream=0):
     """y = H x on device pointers (FP64 or FP32), asynchronous on `stream` (0 = the cluster's)."""
     _check(lib().ed_hpsi(h, int(n_up), int(n_dn), int(dtype), C.c_void_p(x_ptr), C.c_void_p(y_ptr), int(ld),
                          C.c_void_p(stream) if stream else None))
+
+
+ED_K_TABLES, ED_K_HPSI, ED_K_LANCZOS_STEP, ED_K_LANCZOS_NEXT, ED_K_TRIDIAG = 0, 1, 2, 3, 4
+ED_K_VECTOR, ED_K_APPLY_COP, ED_K_GF_EVAL, ED_K_BAND, ED_K_COUNT = 5, 6, 7, 8, 9
+
+
+def ed_profile_enable(on):
+    _check(lib().ed_profile_enable(1 if on else 0))
+
+
+def ed_profile_read(kernel):
+    """(launches, total_ms, algorithmic_bytes) of one kernel family since ed_profile_enable."""
+    n, ms, by = C.c_int64(), C.c_double(), C.c_double()
+    _check(lib().ed_profile_read(int(kernel), C.byref(n), C.byref(ms), C.byref(by)))
+    return n.value, ms.value, by.value
+
+
+def ed_profile_kernel_name(kernel):
+    return lib().ed_profile_kernel_name(int(kernel)).decode()
+
+
+def ed_launch_count():
+    return int(lib().ed_launch_count())
 
 
 class Cluster:

@@ -102,6 +102,8 @@ def test_sampled_matvec_matches_full():
     us = np.arange(op.shape2[0]).repeat(3)[: 40]
     ds = (np.arange(len(us)) * 7) % op.shape2[1]
     assert np.allclose(O.apply_h_sampled(op, psi, us, ds), y[us, ds], atol=1e-13)
+    rows = np.array([0, 2, op.shape2[0] - 1])
+    assert np.allclose(O.apply_h_rows(_model(c), 3, 2, psi, rows), y[rows], atol=1e-13)
     H = op.sparse()
     assert abs(H - H.T).max() < 1e-14
 
