@@ -104,9 +104,20 @@ ed_status ed_ground_vector(ed_cluster* c, double* out, int out_is_device);
  * (0 = up, 1 = down), on z_k = omega[k] + i eta (ED_AXIS_REAL) or z_k = i omega[k]
  * (ED_AXIS_MATSUBARA).  Method from desc.gf_method.  Runs ed_ground_state first if needed.
  * G_out: interleaved complex128 [n_freq][n_sites][n_sites] (2 doubles per element), host or
- * device memory as out_is_device says; owned by the caller. */
+ * device memory as out_is_device says; owned by the caller.  Returns ED_WARN_NOT_CONVERGED when
+ * a band run reached its size limit before G converged on the grid (G is still written). */
 ed_status ed_green(ed_cluster* c, const double* omega, int n_freq, double eta, int axis, int spin,
                    double* G_out, int out_is_device);
+
+/* Options of a cluster's Green-function runs (defaults in brackets):
+ *  ED_OPT_BAND_MAX_DIM  Krylov vectors per part (electron / hole) of the band method [20000];
+ *                       the paper's runs stop between 100 and 500 (Sec. 4.4)
+ *  ED_OPT_CF_MAX_STEPS  Lanczos steps per continued fraction [20000]
+ *  ED_OPT_GF_TOL        a run stops once G on the grid changes by less than this between two
+ *                       successive checks, twice [1e-10 for FP64, 1e-6 for FP32 vectors]
+ * ED_ERR_INVALID for an unknown option or a non-finite value. */
+enum { ED_OPT_BAND_MAX_DIM = 1, ED_OPT_CF_MAX_STEPS = 2, ED_OPT_GF_TOL = 3 };
+ed_status ed_set_option(ed_cluster* c, int option, double value);
 
 /* Statistics of the last ed_green: total Lanczos (or band) steps over all starting vectors and
  * the longest run.  Any pointer may be NULL. */
@@ -133,7 +144,7 @@ ed_status ed_hop_table(ed_cluster* c, int N, int32_t* row_ptr, uint32_t* entries
 
 /* y = H x in sector (n_up, n_dn) on device arrays of d_up rows, leading dimension ld >= d_dn
  * (elements; ld <= 0 means d_dn); dtype ED_FP64 (double) or ED_FP32 (float; products and sums in FP32).  x and y
- * must not overlap.  stream: a cudaStream_t or NULL for the cluster's own stream.  Asynchronous
+ * must not overlap.  stream: a cudaStream_t; NULL is the CUDA default stream.  Asynchronous
  * on that stream. */
 ed_status ed_hpsi(ed_cluster* c, int n_up, int n_dn, int dtype, const void* x, void* y, int64_t ld,
                   void* stream);

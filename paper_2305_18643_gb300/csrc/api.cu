@@ -21,6 +21,7 @@ void throw_cuda(cudaError_t e, const char* what, const char* file, int line) {
 
 GroundResult run_ground_state(ed_cluster& c, int dtype, double tol, int max_iter, uint64_t seed);
 void run_green_cf(ed_cluster& c, int spin, const double2* z_host, int nz, double2* G_dev);
+bool run_green_band(ed_cluster& c, int spin, const double2* z_host, int nz, double2* G_dev);
 
 template <typename F>
 static ed_status guarded(F&& f) {
@@ -71,6 +72,7 @@ SectorView ed_cluster::view(int n_up, int n_dn, int64_t ld) {
   v.ent_up = u.ent.p;
   v.ptr_dn = d.ptr.p;
   v.ent_dn = d.ent.p;
+  v.ell_dn = d.ell.p;
   v.e_up = u.ediag.p;
   v.e_dn = d.ediag.p;
   v.e_up32 = u.ediag32.p;
@@ -229,13 +231,28 @@ ed_status ed_green(ed_cluster* c, const double* omega, int n_freq, double eta, i
     if (c->desc.gf_method == ED_GF_CF) {
       run_green_cf(*c, spin, z.data(), n_freq, Gdev);
     } else {
-      throw Error(ED_ERR_INVALID, "band Lanczos Green function is not available in this build");
+      c->gf_converged = run_green_band(*c, spin, z.data(), n_freq, Gdev);
+      if (!c->gf_converged && st == ED_OK) st = ED_WARN_NOT_CONVERGED;
     }
     if (!out_is_device) {
       ED_CUDA(cudaMemcpyAsync(G_out, Gd.p, (size_t)n_freq * p * p * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
       ED_CUDA(cudaStreamSynchronize(c->stream));
     }
     return st;
+  });
+}
+
+ed_status ed_set_option(ed_cluster* c, int option, double value) {
+  return guarded([&]() -> ed_status {
+    require(c != nullptr, "cluster is NULL");
+    require(is_finite(value), "option value is not finite");
+    switch (option) {
+      case ED_OPT_BAND_MAX_DIM: c->band_max_dim = (int)value; break;
+      case ED_OPT_CF_MAX_STEPS: c->cf_max_steps = (int)value; break;
+      case ED_OPT_GF_TOL: c->gf_tol = value; break;
+      default: throw Error(ED_ERR_INVALID, "unknown option");
+    }
+    return ED_OK;
   });
 }
 
@@ -293,7 +310,7 @@ ed_status ed_hpsi(ed_cluster* c, int n_up, int n_dn, int dtype, const void* x, v
     require(dtype == ED_FP64 || dtype == ED_FP32, "dtype must be ED_FP64 or ED_FP32");
     SectorView sv = c->view(n_up, n_dn, ld);
     require(ld <= 0 || ld >= sv.d_dn, "ld must be >= d_dn (or <= 0 for d_dn)");
-    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    cudaStream_t s = (cudaStream_t)stream;  // NULL is the CUDA default stream
     launch_hpsi(sv, c->hp, dtype, x, y, s);
     return ED_OK;
   });

@@ -1,0 +1,555 @@
+// K8 + K9: band-Lanczos Green function (Sec. 4.4) on the GPU.
+//
+// The p = n_sites starting vectors phi_i = c+_i W (electron part) or c_i W (hole part) span the
+// first block of the Krylov space {Phi, H Phi, H^2 Phi, ...} of Sec. 4.4.  The space is built a
+// block at a time (the band recursion of Sec. 4.4 applied to all p current vectors at once):
+//
+//   W = H X_j - X_{j-1} B_{j-1}^T,  A_j = X_j^T W,  W -= X_j A_j,
+//   W = X_{j+1} B_j  by SVQB: eigen-decomposition G = W^T W = U diag(l) U^T, X_{j+1} = W U l^{-1/2},
+//   B_j = l^{1/2} U^T, directions with l below the deflation threshold dropped (kept as zero
+//   columns, so the block width stays p and deflated directions decouple).
+//
+// When the whole basis fits the memory budget, every new block is also orthogonalized against
+// all stored blocks (twice); otherwise against the previous two blocks only.  The projection of
+// H on the space is the block-tridiagonal matrix T (diagonal blocks A_j, off-diagonal B_j), and
+// the Green function of the part is the matrix element of its resolvent between the starting
+// vectors, Phi = X_1 R_0:
+//
+//   G^e(z) = R_0^T [(z + E0) - T]^{-1}_{11} R_0,   G^h(z) = R_0^T [(z - E0) + T]^{-1}_{11} R_0,
+//
+// which equals the Lehmann sum over the eigenpairs of T (Eq. spectral1 restricted to the
+// Krylov space).  It is evaluated bottom-up as a block continued fraction
+//   M_k = s - A_k,  M_j = s - A_j - B_j^T M_{j+1}^{-1} B_j,  G = R_0^T M_1^{-1} R_0
+// (with A -> -A, s = z - E0 for the hole part).  Every M_j has a positive-definite imaginary
+// part for Im z > 0, so Gaussian elimination without pivoting is stable.
+#include <algorithm>
+#include <cmath>
+
+#include "ed_common.cuh"
+
+namespace ed {
+
+constexpr int kBP = 32;     // maximum block width (cluster sites)
+constexpr int kGT2 = 256;
+constexpr int kTile = 64;   // elements per Gram tile
+
+// ---- Gram of two blocks: G[i][j] = sum_o X_i[o] Y_j[o] over the padded storage (padding is 0)
+template <typename T>
+struct GAcc;
+template <>
+struct GAcc<double> {
+  double s = 0.0;
+  __device__ void add(double v) { s += v; }
+  __device__ double get() const { return s; }
+};
+template <>
+struct GAcc<float> {
+  float s = 0.f, k = 0.f;
+  __device__ void add(float v) {
+    const float y = v - k;
+    const float t = s + y;
+    k = (t - s) - y;
+    s = t;
+  }
+  __device__ double get() const { return (double)s - (double)k; }
+};
+
+// blockIdx.y selects a block of X (X + blockIdx.y * xbstride); partial sums per CTA.
+template <typename T>
+__global__ void __launch_bounds__(kGT2) k_gram_partial(const T* __restrict__ X0, int64_t xbstride, int px,
+                                                       const T* __restrict__ Y, int py, int64_t vstride, int64_t n,
+                                                       double* __restrict__ P) {
+  __shared__ T sx[kBP][kTile + 1];
+  __shared__ T sy[kBP][kTile + 1];
+  const T* X = X0 + blockIdx.y * xbstride;
+  const int npair = px * py;
+  GAcc<T> acc[kBP * kBP / kGT2];
+  for (int64_t o0 = (int64_t)blockIdx.x * kTile; o0 < n; o0 += (int64_t)gridDim.x * kTile) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < kBP * kTile; t += blockDim.x) {
+      const int i = t / kTile, e = t - i * kTile;
+      const int64_t o = o0 + e;
+      if (i < px) sx[i][e] = o < n ? X[i * vstride + o] : T(0);
+      if (i < py) sy[i][e] = o < n ? Y[i * vstride + o] : T(0);
+    }
+    __syncthreads();
+    int q = 0;
+    for (int t = threadIdx.x; t < npair; t += blockDim.x, ++q) {
+      const int i = t / py, j = t - i * py;
+      T s = T(0);
+#pragma unroll 8
+      for (int e = 0; e < kTile; ++e) s += sx[i][e] * sy[j][e];
+      acc[q].add(s);
+    }
+  }
+  int q = 0;
+  const int64_t base = ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * npair;
+  for (int t = threadIdx.x; t < npair; t += blockDim.x, ++q) P[base + t] = acc[q].get();
+}
+
+__global__ void k_gram_finish(const double* __restrict__ P, int nchunk, int npair, double* __restrict__ G) {
+  // blockIdx.x: X block; thread: pair
+  const int b = blockIdx.x;
+  for (int t = threadIdx.x; t < npair; t += blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < nchunk; ++c) s += P[((int64_t)b * nchunk + c) * npair + t];
+    G[(int64_t)b * npair + t] = s;
+  }
+}
+
+// Y_j[o] (mode 0: =, 1: -=) sum over X blocks b < nb and i < px of X_{b,i}[o] C[b][i][j].
+template <typename T>
+__global__ void __launch_bounds__(kGT2) k_block_axpy(T* __restrict__ Y, int py, const T* __restrict__ X0,
+                                                     int64_t xbstride, int nb, int px, const double* __restrict__ C,
+                                                     int64_t vstride, int64_t n, int mode) {
+  extern __shared__ unsigned char smraw[];
+  T* sc = reinterpret_cast<T*>(smraw);  // [nb][px][py]
+  const int nc = nb * px * py;
+  for (int t = threadIdx.x; t < nc; t += blockDim.x) sc[t] = (T)C[t];
+  __syncthreads();
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
+    T out[kBP];
+#pragma unroll
+    for (int j = 0; j < kBP; ++j) out[j] = T(0);
+    for (int b = 0; b < nb; ++b) {
+      const T* X = X0 + b * xbstride;
+      for (int i = 0; i < px; ++i) {
+        const T x = X[i * vstride + o];
+        const T* c = sc + (b * px + i) * py;
+#pragma unroll
+        for (int j = 0; j < kBP; ++j)
+          if (j < py) out[j] += x * c[j];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kBP; ++j) {
+      if (j >= py) break;
+      T* y = Y + j * vstride + o;
+      *y = mode ? *y - out[j] : out[j];
+    }
+  }
+}
+
+// ---- small dense work of one block step (one thread block) ---------------------------------
+// Cyclic Jacobi eigen-decomposition of a symmetric p x p matrix (p <= 32) in place: a -> diag,
+// v -> eigenvectors (columns).
+__device__ void jacobi_eig(double* a, double* v, int p) {
+  for (int i = 0; i < p; ++i)
+    for (int j = 0; j < p; ++j) v[i * p + j] = i == j ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < p; ++i)
+      for (int j = 0; j < p; ++j) {
+        tot += a[i * p + j] * a[i * p + j];
+        if (i != j) off += a[i * p + j] * a[i * p + j];
+      }
+    if (off <= 1e-30 * tot || off == 0.0) break;
+    for (int r = 0; r < p; ++r)
+      for (int q = r + 1; q < p; ++q) {
+        const double arq = a[r * p + q];
+        if (fabs(arq) < 1e-300) continue;
+        const double theta = (a[q * p + q] - a[r * p + r]) / (2.0 * arq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < p; ++k) {
+          const double akr = a[k * p + r], akq = a[k * p + q];
+          a[k * p + r] = c * akr - s * akq;
+          a[k * p + q] = s * akr + c * akq;
+        }
+        for (int k = 0; k < p; ++k) {
+          const double ark = a[r * p + k], aqk = a[q * p + k];
+          a[r * p + k] = c * ark - s * aqk;
+          a[q * p + k] = s * ark + c * aqk;
+        }
+        for (int k = 0; k < p; ++k) {
+          const double vkr = v[k * p + r], vkq = v[k * p + q];
+          v[k * p + r] = c * vkr - s * vkq;
+          v[k * p + q] = s * vkr + c * vkq;
+        }
+      }
+  }
+}
+
+// SVQB of a block with Gram G: Cout = U l^{-1/2} (new basis = W Cout), Bout = l^{1/2} U^T
+// (W = new basis * Bout); directions with l <= thr are dropped (zero columns / rows).  Writes
+// the number of kept directions to *rank.  One thread does the work (p <= 32).
+__global__ void k_svqb(const double* __restrict__ G, int p, double thr, double* __restrict__ Cout,
+                       double* __restrict__ Bout, int* __restrict__ rank) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double a[kBP * kBP], v[kBP * kBP];
+  for (int i = 0; i < p * p; ++i) a[i] = 0.5 * (G[i] + G[(i % p) * p + i / p]);
+  jacobi_eig(a, v, p);
+  int r = 0;
+  for (int k = 0; k < p; ++k) {
+    const double l = a[k * p + k];
+    const bool keep = l > thr;
+    r += keep;
+    const double f = keep ? 1.0 / sqrt(l) : 0.0, g = keep ? sqrt(l) : 0.0;
+    for (int i = 0; i < p; ++i) {
+      Cout[i * p + k] = v[i * p + k] * f;  // column k of C
+      Bout[k * p + i] = v[i * p + k] * g;  // row k of B
+    }
+  }
+  *rank = r;
+}
+
+// out = a * b (p x p), optionally transposing b: used to chain the two SVQB factors and to form
+// the corrections of the recursion.
+__global__ void k_small_gemm(const double* __restrict__ a, const double* __restrict__ b, int p, int tb,
+                             double* __restrict__ out, double scale) {
+  for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
+    const int i = t / p, j = t - i * p;
+    double s = 0.0;
+    for (int k = 0; k < p; ++k) s += a[i * p + k] * (tb ? b[j * p + k] : b[k * p + j]);
+    out[t] = scale * s;
+  }
+}
+
+__global__ void k_small_copy(const double* __restrict__ a, int n, double* __restrict__ out, int sym) {
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    const int i = t / n, j = t - i * n;
+    out[t] = sym ? 0.5 * (a[t] + a[j * n + i]) : a[t];
+  }
+}
+
+// ---- block continued fraction on the grid --------------------------------------------------
+struct BandCoeffs {
+  const double* A;   // [k][p][p]
+  const double* B;   // [k][p][p]   W_j = X_{j+1} B_j
+  const double* R0;  // [p][p]      Phi = X_1 R0
+  int k, p;
+  double E0, sgn;    // sgn = +1 electron (s = z + E0, M = s - A), -1 hole (s = z - E0, M = s + A)
+};
+
+// One thread block per frequency: complex p x p matrices in shared memory.
+__global__ void __launch_bounds__(256) k_band_cf(BandCoeffs bc, const double2* __restrict__ z, int nz, int zstride,
+                                                 double2* __restrict__ out /* [nz][p][p] */, double2* __restrict__ prev,
+                                                 double* __restrict__ maxdiff) {
+  __shared__ double2 M[kBP][kBP + 1];
+  __shared__ double2 Y[kBP][2 * kBP + 1];
+  __shared__ double2 fcol[kBP];
+  const int zi = blockIdx.x;
+  if (zi * zstride >= nz) return;
+  const double2 zz = z[zi * zstride];
+  const int p = bc.p;
+  const double2 s = make_double2(zz.x + bc.sgn * bc.E0, zz.y);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  auto init_M = [&](int j) {
+    for (int t = tid; t < p * p; t += nt) {
+      const int a = t / p, b = t - a * p;
+      double v = -bc.sgn * bc.A[((int64_t)j * p + a) * p + b];
+      M[a][b] = make_double2((a == b ? s.x : 0.0) + v, a == b ? s.y : 0.0);
+    }
+  };
+  // Solve M Y = rhs (rhs p x m, real) in place: augmented [M | rhs] in Y, no pivoting.
+  auto solve = [&](const double* rhs, int m, bool rhs_t) {
+    for (int t = tid; t < p * (p + m); t += nt) {
+      const int a = t / (p + m), b = t - a * (p + m);
+      if (b < p)
+        Y[a][b] = M[a][b];
+      else {
+        const double r = rhs_t ? rhs[(b - p) * p + a] : rhs[a * p + (b - p)];
+        Y[a][b] = make_double2(r, 0.0);
+      }
+    }
+    __syncthreads();
+    for (int c = 0; c < p; ++c) {
+      const double2 piv = Y[c][c];
+      const double den = piv.x * piv.x + piv.y * piv.y;
+      const double2 ip = make_double2(piv.x / den, -piv.y / den);
+      __syncthreads();
+      for (int t = tid; t < p + m; t += nt) {  // scale pivot row
+        const double2 v = Y[c][t];
+        if (t >= c) Y[c][t] = make_double2(v.x * ip.x - v.y * ip.y, v.x * ip.y + v.y * ip.x);
+      }
+      for (int t = tid; t < p; t += nt) fcol[t] = Y[t][c];
+      __syncthreads();
+      for (int t = tid; t < p * (p + m); t += nt) {
+        const int a = t / (p + m), b = t - a * (p + m);
+        if (a == c || b < c) continue;
+        const double2 f = fcol[a], v = Y[c][b];
+        Y[a][b].x -= f.x * v.x - f.y * v.y;
+        Y[a][b].y -= f.x * v.y + f.y * v.x;
+      }
+      __syncthreads();
+    }
+  };
+  init_M(bc.k - 1);
+  __syncthreads();
+  for (int j = bc.k - 2; j >= 0; --j) {
+    // Y = M_{j+1}^{-1} B_j  (B_j: p x p, row index = new-basis direction)
+    solve(bc.B + (int64_t)j * p * p, p, false);
+    // M_j = s -/+ A_j - B_j^T Y
+    for (int t = tid; t < p * p; t += nt) {
+      const int a = t / p, b = t - a * p;
+      double2 acc = make_double2(0.0, 0.0);
+      for (int k2 = 0; k2 < p; ++k2) {
+        const double bk = bc.B[((int64_t)j * p + k2) * p + a];
+        acc.x += bk * Y[k2][p + b].x;
+        acc.y += bk * Y[k2][p + b].y;
+      }
+      const double v = -bc.sgn * bc.A[((int64_t)j * p + a) * p + b];
+      M[a][b] = make_double2((a == b ? s.x : 0.0) + v - acc.x, (a == b ? s.y : 0.0) - acc.y);
+    }
+    __syncthreads();
+  }
+  // G = R0^T M_1^{-1} R0
+  solve(bc.R0, p, false);
+  double local = 0.0;
+  for (int t = tid; t < p * p; t += nt) {
+    const int a = t / p, b = t - a * p;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k2 = 0; k2 < p; ++k2) {
+      const double r = bc.R0[k2 * p + a];
+      acc.x += r * Y[k2][p + b].x;
+      acc.y += r * Y[k2][p + b].y;
+    }
+    const int64_t o = (int64_t)zi * p * p + t;
+    if (prev) {
+      const double2 q = prev[o];
+      local = fmax(local, hypot(acc.x - q.x, acc.y - q.y));
+      prev[o] = acc;
+    } else {
+      out[o] = acc;
+    }
+  }
+  if (maxdiff) {
+    for (int off = 16; off > 0; off >>= 1) local = fmax(local, __shfl_down_sync(0xffffffffu, local, off));
+    if ((tid & 31) == 0) atomicMax((unsigned long long*)maxdiff, __double_as_longlong(local));
+  }
+}
+
+// ---- driver -----------------------------------------------------------------------------------
+static int g_grid(int64_t n, int per) {
+  int64_t b = (n + per - 1) / per;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 4));
+}
+
+template <typename T>
+static void gram(const T* X, int64_t xbstride, int nb, int px, const T* Y, int py, int64_t vstride, int64_t n,
+                 DevBuf<double>& P, double* G, cudaStream_t s) {
+  const int nchunk = std::min<int64_t>((n + kTile - 1) / kTile, 304);
+  const int npair = px * py;
+  if (P.n < (size_t)nb * nchunk * npair) P.alloc((size_t)nb * nchunk * npair);
+  {
+    ProfScope ps_(K_BAND, s, 0.0);
+    k_gram_partial<T><<<dim3(nchunk, nb), kGT2, 0, s>>>(X, xbstride, px, Y, py, vstride, n, P.p);
+    ED_CHECK_LAUNCH();
+  }
+  ProfScope ps_(K_BAND, s, 0.0);
+  k_gram_finish<<<nb, 256, 0, s>>>(P.p, nchunk, npair, G);
+  ED_CHECK_LAUNCH();
+}
+
+template <typename T>
+static void block_axpy(T* Y, int py, const T* X, int64_t xbstride, int nb, int px, const double* C, int64_t vstride,
+                       int64_t n, int mode, cudaStream_t s) {
+  // coefficients of at most `per` blocks are staged in 48 KB of shared memory per launch
+  const int per = std::max(1, (int)((48 * 1024) / ((size_t)px * py * sizeof(T))));
+  for (int b0 = 0; b0 < nb; b0 += per) {
+    const int m = std::min(per, nb - b0);
+    const size_t smem = (size_t)m * px * py * sizeof(T);
+    if (mode == 0 && b0 > 0) throw Error(ED_ERR_INVALID, "block_axpy: assignment over several chunks");
+    ProfScope ps_(K_BAND, s, 0.0);
+    k_block_axpy<T><<<g_grid(n, kGT2), kGT2, smem, s>>>(Y, py, X + (int64_t)b0 * xbstride, xbstride, m, px,
+                                                        C + (int64_t)b0 * px * py, vstride, n, mode);
+    ED_CHECK_LAUNCH();
+  }
+}
+
+struct BandOptions {
+  double tol;         // |Delta G| on the grid between checks
+  int max_dim;        // Krylov vectors per part
+  size_t mem_budget;  // bytes for stored blocks (full reorthogonalization when they fit)
+};
+
+void launch_apply_cop_runs(ed_cluster& c, int spin, bool electron, int dtype, const int2* runs_dev, int nruns,
+                           void* phi, int64_t vstride, int64_t du, int64_t dd, int64_t ld, cudaStream_t s);
+
+template <typename T>
+static bool band_part(ed_cluster& c, int spin, bool electron, const DevBuf<double2>& zd, int nz, double2* Gout,
+                      const BandOptions& opt, int64_t* total, int* maxd, bool* converged) {
+  cudaStream_t s = c.stream;
+  const int dtype = sizeof(T) == 8 ? ED_FP64 : ED_FP32;
+  const int nu = c.desc.n_up, nd = c.desc.n_dn, L = c.model.L;
+  const int dN = electron ? 1 : -1;
+  const int nu_t = nu + (spin == 0 ? dN : 0), nd_t = nd + (spin == 1 ? dN : 0);
+  if (nu_t < 0 || nd_t < 0 || nu_t > L || nd_t > L) return false;
+  const int p = c.model.ns;
+  if (p > kBP) throw Error(ED_ERR_INVALID, "band Lanczos supports at most 32 cluster sites");
+  const int64_t ld = padded_ld(c.tables(nd_t).dim);
+  SectorView sv = c.view(nu_t, nd_t, ld);
+  const int64_t du = sv.d_up, dd = sv.d_dn;
+  const int64_t vstride = du * ld;  // one vector (padded storage)
+  const int64_t n = vstride;
+  const int64_t blk = (int64_t)p * vstride;  // one block of p vectors
+  const int64_t reach = du * dd;
+  const int kmax = (int)std::max<int64_t>(2, std::min<int64_t>((opt.max_dim + p - 1) / p, (2 * reach) / p + 4));
+  const bool full = (size_t)(kmax + 2) * blk * sizeof(T) <= opt.mem_budget;
+  // storage: full reorthogonalization keeps every block; otherwise a ring of 3 blocks.
+  const int nstore = full ? kmax + 2 : 3;
+  DevBuf<T> Vs((size_t)nstore * blk), Wb(blk);
+  ED_CUDA(cudaMemsetAsync(Vs.p, 0, (size_t)nstore * blk * sizeof(T), s));
+  ED_CUDA(cudaMemsetAsync(Wb.p, 0, blk * sizeof(T), s));
+  auto Xb = [&](int j) { return Vs.p + (int64_t)(full ? j : j % 3) * blk; };
+  const int pp = p * p;
+  double scale2 = 1.0;
+  DevBuf<double> A((size_t)kmax * pp), B((size_t)kmax * pp), R0(pp), G((size_t)(kmax + 2) * pp), Cm(pp), Bm(pp),
+      C2(pp), B2(pp), tmp(pp), P;
+  DevBuf<int> rank(1);
+  ED_CUDA(cudaMemsetAsync(A.p, 0, (size_t)kmax * pp * sizeof(double), s));
+  ED_CUDA(cudaMemsetAsync(B.p, 0, (size_t)kmax * pp * sizeof(double), s));
+  // starting block Phi (into W), orthonormalized into X_0 with Phi = X_0 R0
+  std::vector<int2> runs_h(p);
+  for (int i = 0; i < p; ++i) runs_h[i] = make_int2(i, -1);
+  DevBuf<int2> druns(p);
+  ED_CUDA(cudaMemcpyAsync(druns.p, runs_h.data(), p * sizeof(int2), cudaMemcpyHostToDevice, s));
+  launch_apply_cop_runs(c, spin, electron, dtype, druns.p, p, Wb.p, vstride, du, dd, ld, s);
+  // deflation: a direction is dropped when its norm is below eps_rel times the operator scale
+  double hscale = 1.0;
+  for (double v : c.model.h) hscale = std::max(hscale, std::fabs(v));
+  for (double v : c.model.U) hscale = std::max(hscale, std::fabs(v));
+  const double eps_rel = dtype == ED_FP64 ? 1e-10 : 1e-4;
+  auto orthonormalize = [&](double scale2, double* Bfinal) -> int {
+    // two SVQB passes: W = X (B2 B1)
+    int r = 0;
+    gram<T>(Wb.p, 0, 1, p, Wb.p, p, vstride, n, P, G.p, s);
+    { ProfScope ps_(K_BAND, s, 0.0); k_svqb<<<1, 32, 0, s>>>(G.p, p, eps_rel * eps_rel * scale2, Cm.p, Bm.p, rank.p); }
+    ED_CHECK_LAUNCH();
+    block_axpy<T>(Wb.p, p, Wb.p, 0, 1, p, Cm.p, vstride, n, 0, s);
+    gram<T>(Wb.p, 0, 1, p, Wb.p, p, vstride, n, P, G.p, s);
+    { ProfScope ps_(K_BAND, s, 0.0); k_svqb<<<1, 32, 0, s>>>(G.p, p, 0.25, C2.p, B2.p, rank.p); }
+    ED_CHECK_LAUNCH();
+    block_axpy<T>(Wb.p, p, Wb.p, 0, 1, p, C2.p, vstride, n, 0, s);
+    { ProfScope ps_(K_BAND, s, 0.0); k_small_gemm<<<1, 256, 0, s>>>(B2.p, Bm.p, p, 0, Bfinal, 1.0); }
+    ED_CHECK_LAUNCH();
+    ED_CUDA(cudaMemcpyAsync(&r, rank.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ED_CUDA(cudaStreamSynchronize(s));
+    return r;
+  };
+  orthonormalize(1.0, R0.p);
+  scale2 = hscale * hscale;
+  ED_CUDA(cudaMemcpyAsync(Xb(0), Wb.p, blk * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  // check grid (every zstride-th frequency)
+  const int zstride = std::max(1, nz / 512);
+  const int nzc = (nz + zstride - 1) / zstride;
+  DevBuf<double2> prev((size_t)nzc * pp);
+  ED_CUDA(cudaMemsetAsync(prev.p, 0, (size_t)nzc * pp * sizeof(double2), s));
+  DevBuf<double> dmax(1);
+  double* hmax = nullptr;
+  ED_CUDA(cudaMallocHost(&hmax, sizeof(double)));
+  struct HF {
+    double* p;
+    ~HF() { cudaFreeHost(p); }
+  } hf{hmax};
+  const double sgn = electron ? 1.0 : -1.0;
+  int k = 0, hits = 0, next_check = 2;
+  bool conv = false;
+  for (int j = 0; j < kmax; ++j) {
+    // W = H X_j
+    for (int i = 0; i < p; ++i) launch_hpsi(sv, c.hp, dtype, Xb(j) + i * vstride, Wb.p + i * vstride, s);
+    // A_j = X_j^T W ; W -= X_j A_j
+    gram<T>(Xb(j), 0, 1, p, Wb.p, p, vstride, n, P, A.p + (int64_t)j * pp, s);
+    { ProfScope ps_(K_BAND, s, 0.0); k_small_copy<<<1, 256, 0, s>>>(A.p + (int64_t)j * pp, p, A.p + (int64_t)j * pp, 1); }
+    ED_CHECK_LAUNCH();
+    block_axpy<T>(Wb.p, p, Xb(j), 0, 1, p, A.p + (int64_t)j * pp, vstride, n, 1, s);
+    if (j > 0) {
+      // W -= X_{j-1} B_{j-1}^T via the Gram with X_{j-1} (equal to B_{j-1}^T up to rounding)
+      gram<T>(Xb(j - 1), 0, 1, p, Wb.p, p, vstride, n, P, tmp.p, s);
+      block_axpy<T>(Wb.p, p, Xb(j - 1), 0, 1, p, tmp.p, vstride, n, 1, s);
+    }
+    // reorthogonalization: twice against every stored block, or once against the last two
+    for (int pass = 0; pass < (full ? 2 : 1); ++pass) {
+      const int first = full ? 0 : std::max(0, j - 1);
+      const int nbk = j - first + 1;
+      if (full) {
+        gram<T>(Xb(first), blk, nbk, p, Wb.p, p, vstride, n, P, G.p, s);
+        block_axpy<T>(Wb.p, p, Xb(first), blk, nbk, p, G.p, vstride, n, 1, s);
+      } else {
+        for (int b = first; b <= j; ++b) {
+          gram<T>(Xb(b), 0, 1, p, Wb.p, p, vstride, n, P, G.p, s);
+          block_axpy<T>(Wb.p, p, Xb(b), 0, 1, p, G.p, vstride, n, 1, s);
+        }
+      }
+    }
+    // W = X_{j+1} B_j
+    const int r = orthonormalize(scale2, B.p + (int64_t)j * pp);
+    k = j + 1;
+    if (r == 0) {
+      conv = true;  // the Krylov space is exhausted: T is exact
+      break;
+    }
+    if (j + 1 < kmax) ED_CUDA(cudaMemcpyAsync(Xb(j + 1), Wb.p, blk * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    if (k == next_check || j + 1 == kmax) {
+      BandCoeffs bc{A.p, B.p, R0.p, k, p, c.gs.E0, sgn};
+      ED_CUDA(cudaMemsetAsync(dmax.p, 0, sizeof(double), s));
+      { ProfScope ps_(K_GF_EVAL, s, 0.0); k_band_cf<<<nzc, 256, 0, s>>>(bc, zd.p, nz, zstride, nullptr, prev.p, dmax.p); }
+      ED_CHECK_LAUNCH();
+      ED_CUDA(cudaMemcpyAsync(hmax, dmax.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+      ED_CUDA(cudaStreamSynchronize(s));
+      if (*hmax < opt.tol) {
+        if (++hits >= 2) {
+          conv = true;
+          break;
+        }
+      } else {
+        hits = 0;
+      }
+      next_check = k + std::max(2, k / 8);
+    }
+  }
+  BandCoeffs bc{A.p, B.p, R0.p, k, p, c.gs.E0, sgn};
+  { ProfScope ps_(K_GF_EVAL, s, 0.0); k_band_cf<<<nz, 256, 0, s>>>(bc, zd.p, nz, 1, Gout, nullptr, nullptr); }
+  ED_CHECK_LAUNCH();
+  ED_CUDA(cudaStreamSynchronize(s));
+  *total += (int64_t)k * p;
+  *maxd = std::max(*maxd, k * p);
+  *converged = *converged && conv;
+  return true;
+}
+
+__global__ void k_gf_add(const double2* __restrict__ a, const double2* __restrict__ b, int64_t n, double2* __restrict__ out) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    double2 v = make_double2(0.0, 0.0);
+    if (a) {
+      v.x += a[t].x;
+      v.y += a[t].y;
+    }
+    if (b) {
+      v.x += b[t].x;
+      v.y += b[t].y;
+    }
+    out[t] = v;
+  }
+}
+
+bool run_green_band(ed_cluster& c, int spin, const double2* z_host, int nz, double2* G_dev) {
+  cudaStream_t s = c.stream;
+  const int p = c.model.ns;
+  const int dtype = c.desc.precision;
+  BandOptions opt{c.gf_tol > 0 ? c.gf_tol : (dtype == ED_FP64 ? 1e-10 : 1e-6), c.band_max_dim > 0 ? c.band_max_dim : 20000,
+                  size_t(32) << 30};
+  DevBuf<double2> zd(nz);
+  ED_CUDA(cudaMemcpyAsync(zd.p, z_host, nz * sizeof(double2), cudaMemcpyHostToDevice, s));
+  DevBuf<double2> Ge((size_t)nz * p * p), Gh((size_t)nz * p * p);
+  c.gf_total_steps = 0;
+  c.gf_max_steps = 0;
+  bool conv = true, he, hh;
+  if (dtype == ED_FP64) {
+    he = band_part<double>(c, spin, true, zd, nz, Ge.p, opt, &c.gf_total_steps, &c.gf_max_steps, &conv);
+    hh = band_part<double>(c, spin, false, zd, nz, Gh.p, opt, &c.gf_total_steps, &c.gf_max_steps, &conv);
+  } else {
+    he = band_part<float>(c, spin, true, zd, nz, Ge.p, opt, &c.gf_total_steps, &c.gf_max_steps, &conv);
+    hh = band_part<float>(c, spin, false, zd, nz, Gh.p, opt, &c.gf_total_steps, &c.gf_max_steps, &conv);
+  }
+  {
+    ProfScope ps_(K_GF_EVAL, s, 0.0);
+    const int64_t nn = (int64_t)nz * p * p;
+    k_gf_add<<<(unsigned)std::min<int64_t>((nn + 255) / 256, 1024), 256, 0, s>>>(he ? Ge.p : nullptr, hh ? Gh.p : nullptr, nn, G_dev);
+    ED_CHECK_LAUNCH();
+  }
+  ED_CUDA(cudaStreamSynchronize(s));
+  return conv;
+}
+
+}  // namespace ed

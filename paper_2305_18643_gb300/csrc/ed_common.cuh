@@ -46,6 +46,11 @@ enum KernelId {
   K_BAND, K_COUNT
 };
 const char* kernel_name(int kid);
+void note_launch();  // counts a launch that is timed inside another kernel's scope
+
+// Leading dimension of the library's internal state vectors: rows padded to 128 elements so
+// that every vectorized access of the two-pass H.psi stays inside its row.
+inline int64_t padded_ld(int64_t d_dn) { return (d_dn + 127) / 128 * 128; }
 
 // Counts every launch of the library; when profiling is on, brackets the launch with CUDA
 // events on the launching stream and records the algorithmic bytes it moves.
@@ -119,6 +124,8 @@ struct SpinTables {
   DevBuf<int32_t> rank_hi;     // [2^(L-split)]
   DevBuf<int32_t> ptr;         // [dim + 1]
   DevBuf<uint32_t> ent;        // [nnz]
+  int zmax = 0;                // longest row of the table
+  DevBuf<uint32_t> ell;        // [zmax][dim] slot-major copy: ell[k * dim + r] = k-th entry of row r
   DevBuf<double> ediag;        // [dim] sum_a h_aa n_a
   DevBuf<float> ediag32;       // [dim]
 };
@@ -132,6 +139,7 @@ struct SectorView {
   const uint32_t* ent_up;
   const int32_t* ptr_dn;
   const uint32_t* ent_dn;
+  const uint32_t* ell_dn;   // slot-major down-spin table (coalesced across a warp's columns)
   const double* e_up;
   const double* e_dn;
   const float* e_up32;
@@ -144,6 +152,23 @@ struct RankView {
   int split;
   uint32_t lomask;
 };
+
+// Visits every logical element (u, d) of a d_up x d_dn array, f(u, d, u * d_dn + d), without
+// 64-bit division: rows over blocks and columns over threads when rows are long, else a flat
+// 32-bit index (d_dn < 64 keeps d_up * d_dn < 2^30).
+template <typename F>
+__device__ __forceinline__ void for_each_element(int64_t du, int64_t dd, F&& f) {
+  if (dd >= 64) {
+    for (int64_t u = blockIdx.x; u < du; u += gridDim.x)
+      for (int64_t d = threadIdx.x; d < dd; d += blockDim.x) f(u, d, u * dd + d);
+  } else {
+    const uint32_t n = (uint32_t)(du * dd), ddu = (uint32_t)dd;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+      const uint32_t u = i / ddu;
+      f((int64_t)u, (int64_t)(i - u * ddu), (int64_t)i);
+    }
+  }
+}
 
 __device__ __forceinline__ int32_t rank_of(const RankView& r, uint32_t b) {
   return r.lo[b & r.lomask] + r.hi[b >> r.split];
@@ -174,12 +199,13 @@ void launch_hpsi(const SectorView& sv, const HopParams& hp, int dtype, const voi
 void launch_lanczos_step(const SectorView& sv, const HopParams& hp, int dtype, const void* X,
                          void* XP, int64_t vstride, int runs, int n, const LanczosScalars& ls,
                          int nblk_cap, cudaStream_t s);
-int lanczos_blocks(const SectorView& sv);   // blocks per run of the fused step
+int lanczos_blocks(const SectorView& sv);   // partial-sum slots per run of the fused step
+int two_pass_blocks(const SectorView& sv, int dtype);
 
 // lanczos.cu
 void launch_lanczos_next(int dtype, void* W, const void* X, int64_t d_up, int64_t d_dn, int64_t ld,
                          int64_t vstride, int runs, int n, const LanczosScalars& ls,
-                         void* omega, const double* coef, cudaStream_t s);
+                         void* omega, const double* coef, cudaStream_t s);  // omega: dtype, contiguous
 void launch_start_vector(int dtype, void* v, int64_t d_up, int64_t d_dn, int64_t ld, uint64_t seed,
                          cudaStream_t s);
 // Reductions into a device double: out = <a, b> over d_up x d_dn (two-stage, fixed order).
@@ -189,6 +215,9 @@ void launch_dot(int dtype_a, const void* a, int dtype_b, const void* b, int64_t 
 void launch_axpby(int dtype_y, void* y, int dtype_a, const void* a, const double* ca, int dtype_b,
                   const void* b, const double* cb, int64_t d_up, int64_t d_dn, int64_t ld,
                   cudaStream_t s);
+// y[u][d] (leading dimension ld_y) = scale * a[u][d] (leading dimension ld_a); scale NULL = 1.
+void launch_copy_ld(int dty, void* y, int64_t ld_y, int dta, const void* a, int64_t ld_a, const double* scale,
+                    int64_t d_up, int64_t d_dn, cudaStream_t s);
 void launch_tridiag_lowest(const double* alpha, const double* beta, int n, double* out_eval,
                            double* out_vec, cudaStream_t s);
 
@@ -213,6 +242,10 @@ struct ed_cluster {
   bool have_gs = false;
   ed::GroundResult gs;
   int64_t gf_total_steps = 0;
+  int band_max_dim = 0;        // Krylov vectors per part of the band Green function (0: default)
+  int cf_max_steps = 0;        // steps per continued fraction (0: default)
+  double gf_tol = 0.0;         // |Delta G| between convergence checks (0: default)
+  bool gf_converged = true;
   int gf_max_steps = 0;
   ed::SpinTables& tables(int N);
   ed::SectorView view(int n_up, int n_dn, int64_t ld);

@@ -28,8 +28,7 @@ __global__ void k_apply_cop(const double* __restrict__ omega, int64_t dd_s, cons
   const int run = blockIdx.y;
   const int2 rs = runs[run];
   const int64_t dim = du_t * dd_t;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < dim; idx += (int64_t)gridDim.x * blockDim.x) {
-    int64_t u = idx / dd_t, d = idx - u * dd_t;
+  for_each_element(du_t, dd_t, [&](int64_t u, int64_t d, int64_t idx) {
     uint32_t bt = spin == 0 ? B_dst[u] : B_dst[d];
     double acc = 0.0;
 #pragma unroll
@@ -50,7 +49,7 @@ __global__ void k_apply_cop(const double* __restrict__ omega, int64_t dd_s, cons
       ((double*)phi0)[o] = acc;
     else
       ((float*)phi0)[o] = (float)acc;
-  }
+    });
 }
 
 __device__ __forceinline__ double blk_sum(double a) {
@@ -87,12 +86,11 @@ __global__ void k_run_norm_partial(int dtype, const void* V0, int64_t vstride, i
   const int run = blockIdx.y;
   const int64_t dim = du * dd;
   double s = 0.0;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < dim; idx += (int64_t)gridDim.x * blockDim.x) {
-    int64_t u = idx / dd, d = idx - u * dd;
+  for_each_element(du, dd, [&](int64_t u, int64_t d, int64_t idx) {
     int64_t o = run * vstride + u * ld + d;
     double v = dtype == ED_FP64 ? ((const double*)V0)[o] : (double)((const float*)V0)[o];
     s += v * v;
-  }
+    });
   s = blk_sum(s);
   if (threadIdx.x == 0) partial[(int64_t)run * gridDim.x + blockIdx.x] = s;
 }
@@ -116,14 +114,13 @@ __global__ void k_run_scale(int dtype, void* V0, int64_t vstride, int64_t du, in
   const double b = beta0[run];
   const double f = b > 0.0 ? 1.0 / b : 0.0;
   const int64_t dim = du * dd;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < dim; idx += (int64_t)gridDim.x * blockDim.x) {
-    int64_t u = idx / dd, d = idx - u * dd;
+  for_each_element(du, dd, [&](int64_t u, int64_t d, int64_t idx) {
     int64_t o = run * vstride + u * ld + d;
     if (dtype == ED_FP64)
       ((double*)V0)[o] *= f;
     else
       ((float*)V0)[o] = (float)((double)((float*)V0)[o] * f);
-  }
+    });
 }
 
 // Continued fraction of Eq. jacobi shifted by E0 (electron: s = -1, hole: s = +1):
@@ -241,12 +238,14 @@ static bool cf_part(ed_cluster& c, int spin, bool electron, int dtype, const Dev
   SpinTables& src = c.tables(spin == 0 ? nu : nd);
   SpinTables& dst = c.tables(spin == 0 ? nu_t : nd_t);
   c.tables(spin == 0 ? nd : nu);
-  SectorView sv = c.view(nu_t, nd_t, 0);
+  const int64_t ld = padded_ld(c.tables(nd_t).dim);
+  SectorView sv = c.view(nu_t, nd_t, ld);
   const int64_t du = sv.d_up, dd = sv.d_dn, dim = du * dd;
   const int64_t dd_s = c.view(nu, nd, 0).d_dn;
   if (dim == 0) return false;
   const size_t es = dtype == ED_FP64 ? 8 : 4;
-  int Rc = (int)std::max<int64_t>(1, std::min<int64_t>(R, (int64_t)(opt.mem_budget / (2 * dim * es))));
+  const int64_t vstride = du * ld;
+  int Rc = (int)std::max<int64_t>(1, std::min<int64_t>(R, (int64_t)(opt.mem_budget / (2 * vstride * es))));
   const int M = std::max(64, std::min<int>(opt.max_steps, (int)std::min<int64_t>(2 * dim + 16, 1 << 30)));
   const int nblk = lanczos_blocks(sv);
   RankView rv{src.rank_lo.p, src.rank_hi.p, src.split, (uint32_t)((1u << src.split) - 1u)};
@@ -263,12 +262,13 @@ static bool cf_part(ed_cluster& c, int spin, bool electron, int dtype, const Dev
   } hf{host_active};
   for (int r0 = 0; r0 < R; r0 += Rc) {
     const int rc = std::min(Rc, R - r0);
-    DevBuf<char> V0(rc * dim * es), V1(rc * dim * es);
+    DevBuf<char> V0(rc * vstride * es), V1(rc * vstride * es);
+    ED_CUDA(cudaMemsetAsync(V0.p, 0, rc * vstride * es, s));
     DevBuf<double> alpha((size_t)rc * M), beta((size_t)rc * (M + 1)), beta0(rc), b0sq(rc), partial((size_t)rc * nblk * 3 + 8);
     DevBuf<int> active(rc), nsteps(rc), hits(rc), nact(1);
     DevBuf<unsigned> counter(rc);
     DevBuf<double2> prev((size_t)rc * nzs);
-    ED_CUDA(cudaMemsetAsync(V1.p, 0, rc * dim * es, s));
+    ED_CUDA(cudaMemsetAsync(V1.p, 0, rc * vstride * es, s));
     ED_CUDA(cudaMemsetAsync(beta.p, 0, (size_t)rc * (M + 1) * sizeof(double), s));
     ED_CUDA(cudaMemsetAsync(nsteps.p, 0, rc * sizeof(int), s));
     ED_CUDA(cudaMemsetAsync(hits.p, 0, rc * sizeof(int), s));
@@ -276,13 +276,13 @@ static bool cf_part(ed_cluster& c, int spin, bool electron, int dtype, const Dev
     ED_CUDA(cudaMemsetAsync(prev.p, 0, (size_t)rc * nzs * sizeof(double2), s));
     dim3 g(ggrid(dim), rc);
     { ProfScope ps_(K_APPLY_COP, s, 0.0); k_apply_cop<<<g, kGT, 0, s>>>(c.omega.p, dd_s, dst.basis.p, rv, spin, electron ? 1 : 0, extra, druns.p + r0, dtype,
-                                  V0.p, dim, du, dd, dd); }
+                                  V0.p, vstride, du, dd, ld); }
     ED_CHECK_LAUNCH();
-    { ProfScope ps_(K_VECTOR, s, 0.0); k_run_norm_partial<<<dim3(nblk, rc), kGT, 0, s>>>(dtype, V0.p, dim, du, dd, dd, partial.p); }
+    { ProfScope ps_(K_VECTOR, s, 0.0); k_run_norm_partial<<<dim3(nblk, rc), kGT, 0, s>>>(dtype, V0.p, vstride, du, dd, ld, partial.p); }
     ED_CHECK_LAUNCH();
     { ProfScope ps_(K_VECTOR, s, 0.0); k_run_norm_finish<<<rc, kGT, 0, s>>>(partial.p, nblk, b0sq.p, beta0.p, active.p); }
     ED_CHECK_LAUNCH();
-    { ProfScope ps_(K_VECTOR, s, 0.0); k_run_scale<<<g, kGT, 0, s>>>(dtype, V0.p, dim, du, dd, dd, beta0.p); }
+    { ProfScope ps_(K_VECTOR, s, 0.0); k_run_scale<<<g, kGT, 0, s>>>(dtype, V0.p, vstride, du, dd, ld, beta0.p); }
     ED_CHECK_LAUNCH();
     // relative breakdown test needs b_0 = 1 for the normalized start
     LanczosScalars ls{alpha.p, beta.p, beta0.p, active.p, partial.p, counter.p, M, 0.0, nsteps.p};
@@ -298,8 +298,8 @@ static bool cf_part(ed_cluster& c, int spin, bool electron, int dtype, const Dev
     int cur = 0;
     int next_check = 32;
     for (int n = 0; n < M; ++n) {
-      launch_lanczos_step(sv, c.hp, dtype, V[cur], V[cur ^ 1], dim, rc, n, ls, nblk, s);
-      launch_lanczos_next(dtype, V[cur ^ 1], V[cur], du, dd, dd, dim, rc, n, ls, nullptr, nullptr, s);
+      launch_lanczos_step(sv, c.hp, dtype, V[cur], V[cur ^ 1], vstride, rc, n, ls, nblk, s);
+      launch_lanczos_next(dtype, V[cur ^ 1], V[cur], du, dd, ld, vstride, rc, n, ls, nullptr, nullptr, s);
       cur ^= 1;
       if (n + 1 == next_check || n + 1 == M) {
         ED_CUDA(cudaMemsetAsync(nact.p, 0, sizeof(int), s));
@@ -326,12 +326,31 @@ static bool cf_part(ed_cluster& c, int spin, bool electron, int dtype, const Dev
   return true;
 }
 
+// phi[r] = (sum over the sites of runs[r]) c+_i W (create) or c_i W, in the target sector of the
+// changed spin, rows padded to ld; vectors vstride apart.
+void launch_apply_cop_runs(ed_cluster& c, int spin, bool electron, int dtype, const int2* runs_dev, int nruns,
+                           void* phi, int64_t vstride, int64_t du, int64_t dd, int64_t ld, cudaStream_t s) {
+  const int nu = c.desc.n_up, nd = c.desc.n_dn;
+  const int dN = electron ? 1 : -1;
+  SpinTables& src = c.tables(spin == 0 ? nu : nd);
+  SpinTables& dst = c.tables(spin == 0 ? nu + dN : nd + dN);
+  const int64_t dd_s = c.tables(nd).dim;
+  RankView rv{src.rank_lo.p, src.rank_hi.p, src.split, (uint32_t)((1u << src.split) - 1u)};
+  const int extra = spin == 1 ? (nu & 1) : 0;
+  dim3 g(ggrid(du * dd), nruns);
+  ProfScope ps_(K_APPLY_COP, s, 0.0);
+  k_apply_cop<<<g, kGT, 0, s>>>(c.omega.p, dd_s, dst.basis.p, rv, spin, electron ? 1 : 0, extra, runs_dev, dtype, phi,
+                                vstride, du, dd, ld);
+  ED_CHECK_LAUNCH();
+}
+
 void run_green_cf(ed_cluster& c, int spin, const double2* z_host, int nz, double2* G_dev) {
   cudaStream_t s = c.stream;
   const int p = c.model.ns;
   const int R = p + p * (p - 1) / 2;
   const int dtype = c.desc.precision;
-  GreenOptions opt{dtype == ED_FP64 ? 1e-10 : 1e-6, 20000, size_t(48) << 30};
+  GreenOptions opt{c.gf_tol > 0 ? c.gf_tol : (dtype == ED_FP64 ? 1e-10 : 1e-6), c.cf_max_steps > 0 ? c.cf_max_steps : 20000,
+                   size_t(48) << 30};
   DevBuf<double2> zd(nz);
   ED_CUDA(cudaMemcpyAsync(zd.p, z_host, nz * sizeof(double2), cudaMemcpyHostToDevice, s));
   DevBuf<double2> Ge((size_t)R * nz), Gh((size_t)R * nz);

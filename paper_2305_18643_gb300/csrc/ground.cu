@@ -14,14 +14,13 @@ constexpr int kCheck = 10;
 __global__ void k_scale_inv_sqrt(int dt, void* v, const double* nrm2, int64_t du, int64_t dd, int64_t ld) {
   double f = *nrm2 > 0.0 ? 1.0 / sqrt(*nrm2) : 0.0;
   const int64_t dim = du * dd;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < dim; idx += (int64_t)gridDim.x * blockDim.x) {
-    int64_t u = idx / dd, d = idx - u * dd;
+  for_each_element(du, dd, [&](int64_t u, int64_t d, int64_t idx) {
     int64_t o = u * ld + d;
     if (dt == ED_FP64)
       ((double*)v)[o] *= f;
     else
       ((float*)v)[o] = (float)((double)((float*)v)[o] * f);
-  }
+    });
 }
 
 void axpby_inv_sqrt(int dt, void* v, const double* nrm2, int64_t du, int64_t dd, int64_t ld, cudaStream_t s) {
@@ -89,9 +88,9 @@ static size_t esize(int dtype) { return dtype == ED_FP64 ? sizeof(double) : size
 
 // Runs pass 1 (until the Ritz estimate < tol_ritz) and the retrace; returns levels used.
 static int lanczos_pass(ed_cluster& c, const SectorView& sv, int dtype, LanczosRun& L, char* V0, char* V1, char* Vstart,
-                        double* omega, double tol_ritz, double* host, bool* breakdown, cudaStream_t s) {
+                        void* omega, double tol_ritz, double* host, bool* breakdown, cudaStream_t s) {
   const int64_t du = sv.d_up, dd = sv.d_dn, ld = sv.ld, dim = du * dd;
-  const size_t bytes = (size_t)dim * esize(dtype);
+  const size_t bytes = (size_t)du * ld * esize(dtype);
   char* V[2] = {V0, V1};
   int m = 0;
   *breakdown = false;
@@ -99,7 +98,7 @@ static int lanczos_pass(ed_cluster& c, const SectorView& sv, int dtype, LanczosR
     L.reset(s);
     ED_CUDA(cudaMemcpyAsync(V[0], Vstart, bytes, cudaMemcpyDeviceToDevice, s));
     ED_CUDA(cudaMemsetAsync(V[1], 0, bytes, s));
-    if (pass == 1) launch_axpby(ED_FP64, omega, dtype, V[0], L.svec.p, dtype, nullptr, nullptr, du, dd, ld, s);
+    if (pass == 1) launch_copy_ld(dtype, omega, dd, dtype, V[0], ld, L.svec.p, du, dd, s);
     int cur = 0;
     const int nmax = pass == 0 ? L.M : m - 1;
     for (int n = 0; n < nmax; ++n) {
@@ -137,7 +136,9 @@ GroundResult run_ground_state(ed_cluster& c, int dtype, double tol, int max_iter
   SpinTables& td = c.tables(nd);
   (void)tu;
   (void)td;
-  SectorView sv = c.view(nu, nd, 0);
+  const int64_t ld = padded_ld(c.tables(nd).dim);
+  SectorView sv = c.view(nu, nd, ld);     // padded internal vectors
+  SectorView svc = c.view(nu, nd, 0);     // the contiguous ground state
   const int64_t du = sv.d_up, dd = sv.d_dn, dim = du * dd;
   GroundResult R;
   c.omega.alloc(std::max<int64_t>(dim, 1));
@@ -153,26 +154,34 @@ GroundResult run_ground_state(ed_cluster& c, int dtype, double tol, int max_iter
   int total_iters = 0;
   bool have_start = false;
   for (int attempt = 0; attempt < 6; ++attempt) {
-    const size_t bytes = (size_t)dim * esize(dt);
+    const size_t bytes = (size_t)du * ld * esize(dt);
     DevBuf<char> V0(bytes), V1(bytes), Vs(bytes);
+    ED_CUDA(cudaMemsetAsync(V0.p, 0, bytes, s));
+    ED_CUDA(cudaMemsetAsync(V1.p, 0, bytes, s));
+    ED_CUDA(cudaMemsetAsync(Vs.p, 0, bytes, s));
     if (!have_start) {
-      launch_start_vector(dt, Vs.p, du, dd, dd, seed, s);
+      launch_start_vector(dt, Vs.p, du, dd, ld, seed, s);
     } else {
-      launch_axpby(dt, Vs.p, ED_FP64, c.omega.p, scal.p + 7, ED_FP64, nullptr, nullptr, du, dd, dd, s);
+      launch_copy_ld(dt, Vs.p, ld, ED_FP64, c.omega.p, dd, nullptr, du, dd, s);
     }
     // normalize the start vector
-    launch_dot(dt, Vs.p, dt, Vs.p, du, dd, dd, part.p, nblk + 8, scal.p + 0, s);
-    axpby_inv_sqrt(dt, Vs.p, scal.p + 0, du, dd, dd, s);  // Vs <- Vs / sqrt(<Vs,Vs>)
+    launch_dot(dt, Vs.p, dt, Vs.p, du, dd, ld, part.p, nblk + 8, scal.p + 0, s);
+    axpby_inv_sqrt(dt, Vs.p, scal.p + 0, du, dd, ld, s);  // Vs <- Vs / sqrt(<Vs,Vs>)
     LanczosRun L(std::max(2, max_iter), nblk);
     const double tol_ritz = dt == ED_FP64 ? std::min(1e-2, 0.1 * tol) : 1e-7;
     bool breakdown = false;
-    int m = lanczos_pass(c, sv, dt, L, V0.p, V1.p, Vs.p, c.omega.p, tol_ritz, host, &breakdown, s);
+    // the retrace accumulates the ground state in the vectors' precision (FP32 form: FP32 sum of
+    // the s_n v_n, converted to FP64 once)
+    DevBuf<float> om32(dt == ED_FP32 ? dim : 0);
+    void* acc = dt == ED_FP32 ? (void*)om32.p : (void*)c.omega.p;
+    int m = lanczos_pass(c, sv, dt, L, V0.p, V1.p, Vs.p, acc, tol_ritz, host, &breakdown, s);
+    if (dt == ED_FP32) launch_copy_ld(ED_FP64, c.omega.p, dd, ED_FP32, om32.p, dd, nullptr, du, dd, s);
     total_iters += m;
     const double lam0 = host[0], lam1 = host[1], ritz = host[2];
     // FP64 polish: normalize omega, Rayleigh quotient and explicit residual.
     launch_dot(ED_FP64, c.omega.p, ED_FP64, c.omega.p, du, dd, dd, part.p, nblk + 8, scal.p + 1, s);
     axpby_inv_sqrt(ED_FP64, c.omega.p, scal.p + 1, du, dd, dd, s);
-    launch_hpsi(sv, c.hp, ED_FP64, c.omega.p, y64.p, s);
+    launch_hpsi(svc, c.hp, ED_FP64, c.omega.p, y64.p, s);
     launch_dot(ED_FP64, c.omega.p, ED_FP64, y64.p, du, dd, dd, part.p, nblk + 8, scal.p + 2, s);
     axpy_neg(y64.p, scal.p + 2, c.omega.p, dim, s);  // y <- y - E omega
     launch_dot(ED_FP64, y64.p, ED_FP64, y64.p, du, dd, dd, part.p, nblk + 8, scal.p + 3, s);

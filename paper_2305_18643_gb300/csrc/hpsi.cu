@@ -14,6 +14,8 @@
 // (ticket counter) adds the block partials in a fixed order and finishes
 // alpha_n = <x,w>/<x,x> and b_{n+1}^2 = <w,w> - <x,w>^2/<x,x>, so the recursion never leaves
 // the device and repeated runs are bitwise identical.
+#include <algorithm>
+
 #include "ed_common.cuh"
 
 namespace ed {
@@ -110,10 +112,9 @@ __global__ void __launch_bounds__(kThreads) k_hpsi_flat(SectorView sv, HopParams
   __shared__ T sU[kMaxOrb];
   load_params<T>(hp, sval, sU);
   const int64_t dim = sv.d_up * sv.d_dn;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < dim; idx += (int64_t)gridDim.x * blockDim.x) {
-    int64_t u = idx / sv.d_dn, d = idx - u * sv.d_dn;
+  for_each_element(sv.d_up, sv.d_dn, [&](int64_t u, int64_t d, int64_t idx) {
     Y[u * sv.ld + d] = hpsi_element<T>(sv, sval, sU, hp.umask, X, u, d);
-  }
+    });
 }
 
 // Fused Lanczos step, one run per blockIdx.y.  Grid x is fixed (lanczos_blocks) so that the
@@ -133,8 +134,7 @@ __global__ void __launch_bounds__(kThreads) k_lanczos_step(SectorView sv, HopPar
   const double bn = ls.beta[(int64_t)run * (ls.mstride + 1) + n];
   const int64_t dim = sv.d_up * sv.d_dn;
   double sxw = 0.0, sww = 0.0, sxx = 0.0;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < dim; idx += (int64_t)gridDim.x * blockDim.x) {
-    int64_t u = idx / sv.d_dn, d = idx - u * sv.d_dn;
+  for_each_element(sv.d_up, sv.d_dn, [&](int64_t u, int64_t d, int64_t idx) {
     int64_t o = u * sv.ld + d;
     T hx = hpsi_element<T>(sv, sval, sU, hp.umask, X, u, d);
     T w = hx - (T)bn * XP[o];
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(kThreads) k_lanczos_step(SectorView sv, HopPar
     sxw += x * wd;
     sww += wd * wd;
     sxx += x * x;
-  }
+    });
   block_sum3(sxw, sww, sxx);
   double* part = ls.partial + ((int64_t)run * gridDim.x) * 3;
   if (threadIdx.x == 0) {
@@ -177,15 +177,307 @@ __global__ void __launch_bounds__(kThreads) k_lanczos_step(SectorView sv, HopPar
   }
 }
 
+// ---- two-pass form for vectors larger than L2 ------------------------------------------
+// Row pass: R rows are staged in shared memory interleaved as [d][R] (one 16-byte vector per
+// column), so every down-spin gather serves R rows; the diagonal and -b_n x_prev are applied
+// in the same pass, in place on the output.  Column pass: the grid walks column chunks of
+// 32 * NV columns (slow index) over row blocks (fast index), so the chunk of x that the up-spin
+// hops read, d_up x 32 NV elements, stays in L2 while every row block reads it; each warp owns
+// one row at a time and gathers whole 16-byte-per-lane row segments; the Lanczos reductions are
+// fused.  Requires ld >= round_up(d_dn, 128), ld % NV == 0, 16-byte aligned vectors and zero
+// padding columns (kept zero by every kernel).
+template <typename T>
+struct Vec;
+template <>
+struct Vec<float> {
+  using t = float4;
+  static constexpr int n = 4;
+  __device__ static float get(const float4& v, int j) { return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w; }
+  __device__ static float4 make(const float* a) { return make_float4(a[0], a[1], a[2], a[3]); }
+  __device__ static void fma(float4& acc, float s, const float4& x) {
+    acc.x = fmaf(s, x.x, acc.x);
+    acc.y = fmaf(s, x.y, acc.y);
+    acc.z = fmaf(s, x.z, acc.z);
+    acc.w = fmaf(s, x.w, acc.w);
+  }
+};
+template <>
+struct Vec<double> {
+  using t = double2;
+  static constexpr int n = 2;
+  __device__ static double get(const double2& v, int j) { return j == 0 ? v.x : v.y; }
+  __device__ static double2 make(const double* a) { return make_double2(a[0], a[1]); }
+  __device__ static void fma(double2& acc, double s, const double2& x) {
+    acc.x = ::fma(s, x.x, acc.x);
+    acc.y = ::fma(s, x.y, acc.y);
+  }
+};
+
+constexpr int kRowThreads = 1024;
+
+// Per-thread partial sums of <x,w>, <w,w>, <x,x>: FP64 for FP64 vectors; compensated (Kahan)
+// FP32 for FP32 vectors, so that no per-element FP64 arithmetic is needed (FP64 runs at a
+// small fraction of the FP32 rate on this GPU).
+template <typename T>
+struct Partial3;
+template <>
+struct Partial3<double> {
+  double s[3] = {0.0, 0.0, 0.0};
+  __device__ void add(double x, double w) {
+    s[0] += x * w;
+    s[1] += w * w;
+    s[2] += x * x;
+  }
+  __device__ void get(double& a, double& b, double& c) const {
+    a = s[0];
+    b = s[1];
+    c = s[2];
+  }
+};
+template <>
+struct Partial3<float> {
+  float s[3] = {0.f, 0.f, 0.f}, k[3] = {0.f, 0.f, 0.f};
+  __device__ void add1(int i, float v) {
+    const float y = v - k[i];
+    const float t = s[i] + y;
+    k[i] = (t - s[i]) - y;
+    s[i] = t;
+  }
+  __device__ void add(float x, float w) {
+    add1(0, x * w);
+    add1(1, w * w);
+    add1(2, x * x);
+  }
+  __device__ void get(double& a, double& b, double& c) const {
+    a = (double)s[0] - (double)k[0];
+    b = (double)s[1] - (double)k[1];
+    c = (double)s[2] - (double)k[2];
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kRowThreads) k_down_rows(SectorView sv, HopParams hp, const T* __restrict__ X0,
+                                                   T* __restrict__ O0, int64_t vstride, const double* __restrict__ beta,
+                                                   int beta_stride, int n_step, const int* __restrict__ active) {
+  using RV = typename Vec<T>::t;
+  constexpr int R = Vec<T>::n;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  RV* sx = reinterpret_cast<RV*>(smem_raw);
+  T* sval = reinterpret_cast<T*>(sx + sv.d_dn);
+  T* sU = sval + kMaxVals;
+  const int run = blockIdx.y;
+  if (active && !active[run]) return;
+  for (int i = threadIdx.x; i < kMaxVals; i += blockDim.x) sval[i] = Prec<T>::val(hp, i);
+  for (int i = threadIdx.x; i < kMaxOrb; i += blockDim.x) sU[i] = Prec<T>::U(hp, i);
+  const T* X = X0 + run * vstride;
+  T* O = O0 + run * vstride;
+  const T b = beta ? (T)beta[(int64_t)run * beta_stride + n_step] : T(0);
+  const int64_t du = sv.d_up, dd = sv.d_dn, ld = sv.ld;
+  const T* eup = Prec<T>::e_up(sv);
+  const T* edn = Prec<T>::e_dn(sv);
+  for (int64_t u0 = (int64_t)blockIdx.x * R; u0 < du; u0 += (int64_t)gridDim.x * R) {
+    __syncthreads();
+    for (int64_t d = threadIdx.x; d < dd; d += blockDim.x) {
+      T v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = (u0 + r < du) ? X[(u0 + r) * ld + d] : T(0);
+      sx[d] = Vec<T>::make(v);
+    }
+    __syncthreads();
+    uint32_t bu[R];
+    T eu[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      bool ok = u0 + r < du;
+      bu[r] = ok ? sv.B_up[u0 + r] : 0u;
+      eu[r] = ok ? eup[u0 + r] : T(0);
+    }
+    for (int64_t d = threadIdx.x; d < dd; d += blockDim.x) {
+      const uint32_t bd = sv.B_dn[d];
+      const T ed = edn[d];
+      const RV xv = sx[d];
+      RV acc;
+      {
+        T a[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          T diag = eu[r] + ed;
+          uint32_t dbl = bu[r] & bd & hp.umask;
+          while (dbl) {
+            diag += sU[__ffs(dbl) - 1];
+            dbl &= dbl - 1u;
+          }
+          a[r] = diag * Vec<T>::get(xv, r);
+        }
+        acc = Vec<T>::make(a);
+      }
+      const int32_t nz = sv.ptr_dn[d + 1] - sv.ptr_dn[d];
+      for (int32_t k = 0; k < nz; ++k) {
+        const uint32_t e = __ldg(sv.ell_dn + (int64_t)k * dd + d);
+        T v = sval[ent_vidx(e)];
+        v = ent_neg(e) ? -v : v;
+        Vec<T>::fma(acc, v, sx[ent_col(e)]);
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (u0 + r >= du) continue;
+        const int64_t o = (u0 + r) * ld + d;
+        T out = Vec<T>::get(acc, r);
+        if (beta) out -= b * O[o];
+        O[o] = out;
+      }
+    }
+  }
+}
+
+template <typename T, bool FUSED>
+__global__ void __launch_bounds__(kThreads) k_up_cols(SectorView sv, HopParams hp, const T* __restrict__ X0,
+                                                      T* __restrict__ O0, int64_t vstride, int rows_per_cta, int n,
+                                                      LanczosScalars ls) {
+  using RV = typename Vec<T>::t;
+  constexpr int NV = Vec<T>::n;
+  __shared__ T sval[kMaxVals];
+  __shared__ bool s_last;
+  const int run = blockIdx.z;
+  if (FUSED && !ls.active[run]) return;
+  for (int i = threadIdx.x; i < kMaxVals; i += blockDim.x) sval[i] = Prec<T>::val(hp, i);
+  __syncthreads();
+  const T* X = X0 + run * vstride;
+  T* O = O0 + run * vstride;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int64_t ld = sv.ld;
+  const int64_t c0 = (int64_t)blockIdx.y * (32 * NV) + lane * NV;
+  const int64_t ub = (int64_t)blockIdx.x * rows_per_cta;
+  const int64_t ue = ub + rows_per_cta < sv.d_up ? ub + rows_per_cta : sv.d_up;
+  Partial3<T> part3;
+  for (int64_t u = ub + warp; u < ue; u += nwarp) {
+    RV* op = reinterpret_cast<RV*>(O + u * ld + c0);
+    RV acc = *op;
+    const int32_t p0 = sv.ptr_up[u], p1 = sv.ptr_up[u + 1];
+    for (int32_t k = p0; k < p1; ++k) {
+      const uint32_t e = __ldg(sv.ent_up + k);
+      T v = sval[ent_vidx(e)];
+      v = ent_neg(e) ? -v : v;
+      const RV xv = __ldg(reinterpret_cast<const RV*>(X + (int64_t)ent_col(e) * ld + c0));
+      Vec<T>::fma(acc, v, xv);
+    }
+    *op = acc;
+    if (FUSED) {
+      const RV xs = __ldg(reinterpret_cast<const RV*>(X + u * ld + c0));
+#pragma unroll
+      for (int j = 0; j < NV; ++j)
+        if (c0 + j < sv.d_dn) part3.add(Vec<T>::get(xs, j), Vec<T>::get(acc, j));
+    }
+  }
+  if (!FUSED) return;
+  double sxw, sww, sxx;
+  part3.get(sxw, sww, sxx);
+  block_sum3(sxw, sww, sxx);
+  const unsigned nblk = gridDim.x * gridDim.y;
+  const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
+  double* part = ls.partial + ((int64_t)run * nblk) * 3;
+  if (threadIdx.x == 0) {
+    part[bid * 3 + 0] = sxw;
+    part[bid * 3 + 1] = sww;
+    part[bid * 3 + 2] = sxx;
+    __threadfence();
+    unsigned t = atomicAdd(ls.counter + run, 1u);
+    s_last = (t == nblk - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (unsigned i = threadIdx.x; i < nblk; i += blockDim.x) {
+    a += __ldcg(part + i * 3 + 0);
+    b += __ldcg(part + i * 3 + 1);
+    c += __ldcg(part + i * 3 + 2);
+  }
+  block_sum3(a, b, c);
+  if (threadIdx.x == 0) {
+    double alpha = c > 0.0 ? a / c : 0.0;
+    double b2 = c > 0.0 ? b - a * a / c : 0.0;
+    double bnext = b2 > 0.0 ? sqrt(b2) : 0.0;
+    ls.alpha[(int64_t)run * ls.mstride + n] = alpha;
+    ls.beta[(int64_t)run * (ls.mstride + 1) + n + 1] = bnext;
+    if (ls.nsteps) ls.nsteps[run] = n + 1;
+    if (!(bnext > ls.btol * ls.beta0[run]) || n + 1 >= ls.mstride) ls.active[run] = 0;
+    ls.counter[run] = 0u;
+  }
+}
+
+constexpr int kRowsPerCta = 64;
+static int g_smem_optin = -1;
+
+static size_t down_rows_smem(const SectorView& sv, int dtype) {
+  const size_t es = dtype == ED_FP64 ? 8 : 4;
+  return (size_t)sv.d_dn * 16 + (kMaxVals + kMaxOrb) * es;
+}
+
+// The two-pass form applies when the vector does not fit L2 comfortably and the layout allows
+// 16-byte vector access.
+static bool use_two_pass(const SectorView& sv, int dtype, const void* X, const void* O, int64_t vstride) {
+  const int64_t es = dtype == ED_FP64 ? 8 : 4, NV = dtype == ED_FP64 ? 2 : 4;
+  if (sv.d_up * sv.d_dn * es < (int64_t(32) << 20)) return false;
+  const int64_t need = (sv.d_dn + 32 * NV - 1) / (32 * NV) * (32 * NV);
+  if (sv.ld < need || sv.ld % NV != 0) return false;
+  if (((uintptr_t)X | (uintptr_t)O) % 16 != 0 || (vstride * es) % 16 != 0) return false;
+  if (g_smem_optin < 0) {
+    int dev = 0, v = 0;
+    ED_CUDA(cudaGetDevice(&dev));
+    ED_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    g_smem_optin = v;
+  }
+  return down_rows_smem(sv, dtype) <= (size_t)g_smem_optin;
+}
+
+template <typename T>
+static void launch_two_pass(const SectorView& sv, const HopParams& hp, const T* X, T* O, int64_t vstride, int runs,
+                            const double* beta, int beta_stride, int n, const LanczosScalars* ls, cudaStream_t s) {
+  const double es = sizeof(T);
+  const double dim = (double)sv.d_up * sv.d_dn;
+  const size_t smem = down_rows_smem(sv, sizeof(T) == 8 ? ED_FP64 : ED_FP32);
+  ED_CUDA(cudaFuncSetAttribute(k_down_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int64_t groups = (sv.d_up + Vec<T>::n - 1) / Vec<T>::n;
+  dim3 g1((unsigned)std::min<int64_t>(groups, 152), runs);
+  dim3 g2((unsigned)((sv.d_up + kRowsPerCta - 1) / kRowsPerCta), (unsigned)((sv.d_dn + 32 * Vec<T>::n - 1) / (32 * Vec<T>::n)),
+          runs);
+  // one timed unit per step: both passes (the second launch is counted separately)
+  ProfScope ps_(ls ? K_LANCZOS_STEP : K_HPSI, s, (beta ? 3.0 : 2.0) * es * dim * runs);
+  k_down_rows<T><<<g1, kRowThreads, smem, s>>>(sv, hp, X, O, vstride, beta, beta_stride, n, ls ? ls->active : nullptr);
+  ED_CHECK_LAUNCH();
+  note_launch();
+  if (ls)
+    k_up_cols<T, true><<<g2, kThreads, 0, s>>>(sv, hp, X, O, vstride, kRowsPerCta, n, *ls);
+  else
+    k_up_cols<T, false><<<g2, kThreads, 0, s>>>(sv, hp, X, O, vstride, kRowsPerCta, n, LanczosScalars{});
+  ED_CHECK_LAUNCH();
+}
+
+int two_pass_blocks(const SectorView& sv, int dtype) {
+  const int NV = dtype == ED_FP64 ? 2 : 4;
+  return (int)(((sv.d_up + kRowsPerCta - 1) / kRowsPerCta) * ((sv.d_dn + 32 * NV - 1) / (32 * NV)));
+}
+
 static int grid_for(int64_t dim) {
   int64_t b = (dim + kThreads - 1) / kThreads;
   const int64_t cap = 152 * 8;
   return (int)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
-int lanczos_blocks(const SectorView& sv) { return grid_for(sv.d_up * sv.d_dn); }
+int lanczos_blocks(const SectorView& sv) {
+  // capacity for either form (the two-pass column kernel has more blocks on large sectors)
+  return std::max(grid_for(sv.d_up * sv.d_dn), two_pass_blocks(sv, ED_FP64));
+}
 
 void launch_hpsi(const SectorView& sv, const HopParams& hp, int dtype, const void* x, void* y, cudaStream_t s) {
+  if (use_two_pass(sv, dtype, x, y, 0)) {
+    if (dtype == ED_FP64)
+      launch_two_pass<double>(sv, hp, (const double*)x, (double*)y, 0, 1, nullptr, 0, 0, nullptr, s);
+    else
+      launch_two_pass<float>(sv, hp, (const float*)x, (float*)y, 0, 1, nullptr, 0, 0, nullptr, s);
+    return;
+  }
   int g = grid_for(sv.d_up * sv.d_dn);
   const double es = dtype == ED_FP64 ? 8.0 : 4.0;
   ProfScope ps_(K_HPSI, s, 2.0 * es * (double)(sv.d_up * sv.d_dn));
@@ -198,6 +490,14 @@ void launch_hpsi(const SectorView& sv, const HopParams& hp, int dtype, const voi
 
 void launch_lanczos_step(const SectorView& sv, const HopParams& hp, int dtype, const void* X, void* XP,
                          int64_t vstride, int runs, int n, const LanczosScalars& ls, int nblk_cap, cudaStream_t s) {
+  if (use_two_pass(sv, dtype, X, XP, vstride)) {
+    if (two_pass_blocks(sv, dtype) > nblk_cap) throw Error(ED_ERR_INVALID, "partial buffer too small");
+    if (dtype == ED_FP64)
+      launch_two_pass<double>(sv, hp, (const double*)X, (double*)XP, vstride, runs, ls.beta, ls.mstride + 1, n, &ls, s);
+    else
+      launch_two_pass<float>(sv, hp, (const float*)X, (float*)XP, vstride, runs, ls.beta, ls.mstride + 1, n, &ls, s);
+    return;
+  }
   int g = grid_for(sv.d_up * sv.d_dn);
   if (g > nblk_cap) throw Error(ED_ERR_INVALID, "partial buffer too small");
   dim3 grid(g, runs);

@@ -38,7 +38,7 @@ static int vgrid(int64_t n) {
 template <typename T>
 __global__ void __launch_bounds__(kVT) k_lanczos_next(T* __restrict__ W0, const T* __restrict__ X0, int64_t d_up, int64_t d_dn,
                                                       int64_t ld, int64_t vstride, int n, LanczosScalars ls,
-                                                      double* __restrict__ omega, const double* __restrict__ coef) {
+                                                      T* __restrict__ omega, const double* __restrict__ coef) {
   const int run = blockIdx.y;
   if (!ls.active[run]) return;
   T* W = W0 + run * vstride;
@@ -46,16 +46,15 @@ __global__ void __launch_bounds__(kVT) k_lanczos_next(T* __restrict__ W0, const 
   const double a = ls.alpha[(int64_t)run * ls.mstride + n];
   const double b = ls.beta[(int64_t)run * (ls.mstride + 1) + n + 1];
   const double ib = 1.0 / b;
-  const double cf = omega ? coef[n + 1] : 0.0;
+  const T cf = omega ? (T)coef[n + 1] : T(0);
+  const T aT = (T)a, ibT = (T)ib;
   const int64_t dim = d_up * d_dn;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < dim; idx += (int64_t)gridDim.x * blockDim.x) {
-    int64_t u = idx / d_dn, d = idx - u * d_dn;
+  for_each_element(d_up, d_dn, [&](int64_t u, int64_t d, int64_t idx) {
     int64_t o = u * ld + d;
-    double v = ((double)W[o] - a * (double)X[o]) * ib;
-    T vt = (T)v;
+    const T vt = (W[o] - aT * X[o]) * ibT;
     W[o] = vt;
-    if (omega) omega[idx] += cf * (double)vt;
-  }
+    if (omega) omega[idx] += cf * vt;
+    });
 }
 
 void launch_lanczos_next(int dtype, void* W, const void* X, int64_t d_up, int64_t d_dn, int64_t ld, int64_t vstride,
@@ -68,7 +67,7 @@ void launch_lanczos_next(int dtype, void* W, const void* X, int64_t d_up, int64_
                                               (double*)omega, coef);
   else
     k_lanczos_next<float><<<g, kVT, 0, s>>>((float*)W, (const float*)X, d_up, d_dn, ld, vstride, n, ls,
-                                             (double*)omega, coef);
+                                             (float*)omega, coef);
   ED_CHECK_LAUNCH();
 }
 
@@ -82,11 +81,10 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 
 __global__ void k_start_vector(int dt, void* v, int64_t d_up, int64_t d_dn, int64_t ld, uint64_t seed) {
   const int64_t dim = d_up * d_dn;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < dim; idx += (int64_t)gridDim.x * blockDim.x) {
-    int64_t u = idx / d_dn, d = idx - u * d_dn;
+  for_each_element(d_up, d_dn, [&](int64_t u, int64_t d, int64_t idx) {
     double r = (double)(splitmix64(seed ^ (uint64_t)idx) >> 11) * (1.0 / 9007199254740992.0);
     stv(dt, v, u * ld + d, 2.0 * r - 1.0);
-  }
+    });
 }
 
 void launch_start_vector(int dtype, void* v, int64_t d_up, int64_t d_dn, int64_t ld, uint64_t seed, cudaStream_t s) {
@@ -113,11 +111,10 @@ __global__ void k_dot_partial(int dta, const void* a, int dtb, const void* b, in
                               double* __restrict__ partial) {
   const int64_t dim = d_up * d_dn;
   double s = 0.0;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < dim; idx += (int64_t)gridDim.x * blockDim.x) {
-    int64_t u = idx / d_dn, d = idx - u * d_dn;
+  for_each_element(d_up, d_dn, [&](int64_t u, int64_t d, int64_t idx) {
     int64_t o = u * ld + d;
     s += ldv(dta, a, o) * ldv(dtb, b, o);
-  }
+    });
   s = block_sum(s);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
@@ -153,20 +150,35 @@ __global__ void k_axpby(int dty, void* y, int dta, const void* a, const double* 
   }
   if (cb) sb = neg_b ? -*cb : *cb;
   const int64_t dim = d_up * d_dn;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < dim; idx += (int64_t)gridDim.x * blockDim.x) {
-    int64_t u = idx / d_dn, d = idx - u * d_dn;
+  for_each_element(d_up, d_dn, [&](int64_t u, int64_t d, int64_t idx) {
     int64_t o = u * ld + d;
     double v = 0.0;
     if (ca) v += sa * ldv(dta, a, o);
     if (cb) v += sb * ldv(dtb, b, o);
     stv(dty, y, o, v);
-  }
+    });
 }
 
 static void axpby(int dty, void* y, int dta, const void* a, const double* ca, int dtb, const void* b, const double* cb,
                   int64_t d_up, int64_t d_dn, int64_t ld, cudaStream_t s, int inv_sqrt_a = 0, int neg_b = 0) {
   ProfScope ps_(K_VECTOR, s, 0.0);
   k_axpby<<<vgrid(d_up * d_dn), kVT, 0, s>>>(dty, y, dta, a, ca, dtb, b, cb, d_up, d_dn, ld, inv_sqrt_a, neg_b);
+  ED_CHECK_LAUNCH();
+}
+
+__global__ void k_copy_ld(int dty, void* y, int64_t ld_y, int dta, const void* a, int64_t ld_a,
+                          const double* __restrict__ scale, int64_t d_up, int64_t d_dn) {
+  const double f = scale ? *scale : 1.0;
+  const int64_t dim = d_up * d_dn;
+  for_each_element(d_up, d_dn, [&](int64_t u, int64_t d, int64_t idx) {
+    stv(dty, y, u * ld_y + d, f * ldv(dta, a, u * ld_a + d));
+    });
+}
+
+void launch_copy_ld(int dty, void* y, int64_t ld_y, int dta, const void* a, int64_t ld_a, const double* scale,
+                    int64_t d_up, int64_t d_dn, cudaStream_t s) {
+  ProfScope ps_(K_VECTOR, s, 0.0);
+  k_copy_ld<<<vgrid(d_up * d_dn), kVT, 0, s>>>(dty, y, ld_y, dta, a, ld_a, scale, d_up, d_dn);
   ED_CHECK_LAUNCH();
 }
 

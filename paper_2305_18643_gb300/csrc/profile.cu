@@ -41,6 +41,8 @@ void drain_locked() {
 }
 }  // namespace
 
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
 const char* kernel_name(int kid) { return (kid >= 0 && kid < K_COUNT) ? kNames[kid] : "?"; }
 
 ProfScope::ProfScope(int kid_, cudaStream_t s_, double bytes_) : kid(kid_), s(s_), bytes(bytes_) {

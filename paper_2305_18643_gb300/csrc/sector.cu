@@ -114,6 +114,23 @@ __global__ void k_hop_fill(int64_t dim, const uint32_t* __restrict__ basis, Rank
   }
 }
 
+__global__ void k_max_int(const int32_t* __restrict__ v, int64_t n, int* __restrict__ out) {
+  int m = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, v[i]);
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+// Slot-major copy of the CSR table: ell[k * dim + r] = k-th entry of row r (0 past its end).
+__global__ void k_ell_fill(int64_t dim, const int32_t* __restrict__ ptr, const uint32_t* __restrict__ ent, int zmax,
+                           uint32_t* __restrict__ ell) {
+  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= dim) return;
+  const int32_t p0 = ptr[r], n = ptr[r + 1] - p0;
+  for (int k = 0; k < zmax; ++k) ell[(int64_t)k * dim + r] = k < n ? ent[p0 + k] : 0u;
+}
+
 // Exclusive scan of cnt[0..n) into ptr[0..n] by one block (one-time table construction).
 __global__ void k_scan_one_block(const int32_t* __restrict__ cnt, int64_t n, int32_t* __restrict__ ptr) {
   __shared__ int64_t sums[1024];
@@ -209,6 +226,21 @@ std::unique_ptr<SpinTables> build_spin_tables(const ModelHost& m, int N, cudaStr
   if (dim > 0 && nnz > 0) {
     { ProfScope ps_(K_TABLES, s, 0.0); k_hop_fill<<<nblocks(dim, bs), bs, 0, s>>>(dim, t->basis.p, rv, dpairs.p, npairs, t->ptr.p, t->ent.p); }
     ED_CHECK_LAUNCH();
+  }
+  {
+    DevBuf<int> dz(1);
+    ED_CUDA(cudaMemsetAsync(dz.p, 0, sizeof(int), s));
+    if (dim > 0) {
+      { ProfScope ps_(K_TABLES, s, 0.0); k_max_int<<<std::min<unsigned>(nblocks(dim, bs), 1024), bs, 0, s>>>(cnt.p, dim, dz.p); }
+      ED_CHECK_LAUNCH();
+    }
+    ED_CUDA(cudaMemcpyAsync(&t->zmax, dz.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ED_CUDA(cudaStreamSynchronize(s));
+    t->ell.alloc(std::max<int64_t>((int64_t)t->zmax * dim, 1));
+    if (dim > 0 && t->zmax > 0) {
+      { ProfScope ps_(K_TABLES, s, 0.0); k_ell_fill<<<nblocks(dim, bs), bs, 0, s>>>(dim, t->ptr.p, t->ent.p, t->zmax, t->ell.p); }
+      ED_CHECK_LAUNCH();
+    }
   }
   Diag32 hd;
   for (int a = 0; a < kMaxOrb; ++a) hd.h[a] = a < m.L ? m.h[a * m.L + a] : 0.0;

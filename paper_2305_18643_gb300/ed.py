@@ -69,6 +69,7 @@ def lib():
             "ed_profile_read": (i32, [i32, C.POINTER(i64), _dp, _dp]),
             "ed_profile_kernel_name": (C.c_char_p, [i32]),
             "ed_launch_count": (i64, []),
+            "ed_set_option": (i32, [vp, i32, C.c_double]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -155,6 +156,13 @@ def ed_green(h, omega, eta, n_sites, axis=ED_AXIS_REAL, spin=0, out_ptr=None):
     return st, G
 
 
+ED_OPT_BAND_MAX_DIM, ED_OPT_CF_MAX_STEPS, ED_OPT_GF_TOL = 1, 2, 3
+
+
+def ed_set_option(h, option, value):
+    _check(lib().ed_set_option(h, int(option), float(value)))
+
+
 def ed_green_stats(h):
     tot, mx = C.c_int64(), C.c_int()
     _check(lib().ed_green_stats(h, C.byref(tot), C.byref(mx)))
@@ -184,7 +192,7 @@ def ed_hop_table(h, N, L):
 
 
 def ed_hpsi(h, n_up, n_dn, dtype, x_ptr, y_ptr, ld=0, stream=0):
-    """y = H x on device pointers (FP64 or FP32), asynchronous on `stream` (0 = the cluster's)."""
+    """y = H x on device pointers (FP64 or FP32), asynchronous on `stream` (0 = the CUDA default stream)."""
     _check(lib().ed_hpsi(h, int(n_up), int(n_dn), int(dtype), C.c_void_p(x_ptr), C.c_void_p(y_ptr), int(ld),
                          C.c_void_p(stream) if stream else None))
 
