@@ -55,36 +55,93 @@ struct GAcc<float> {
 };
 
 // blockIdx.y selects a block of X (X + blockIdx.y * xbstride); partial sums per CTA.
+// Gram partial sums, register-tiled: each thread owns a 4 x 4 tile of pairs (i, j) and a slice
+// of the kTile elements staged in shared memory, so 8 shared loads feed 16 multiply-adds.  The
+// slices are added in a fixed order at the end (deterministic).  X blocks: X0 + b * xbstride,
+// or (xbstride == 0) X0 for b = 0 and X1 for b = 1.
 template <typename T>
-__global__ void __launch_bounds__(kGT2) k_gram_partial(const T* __restrict__ X0, int64_t xbstride, int px,
-                                                       const T* __restrict__ Y, int py, int64_t vstride, int64_t n,
-                                                       double* __restrict__ P) {
-  __shared__ T sx[kBP][kTile + 1];
-  __shared__ T sy[kBP][kTile + 1];
-  const T* X = X0 + blockIdx.y * xbstride;
-  const int npair = px * py;
-  GAcc<T> acc[kBP * kBP / kGT2];
-  for (int64_t o0 = (int64_t)blockIdx.x * kTile; o0 < n; o0 += (int64_t)gridDim.x * kTile) {
+__global__ void __launch_bounds__(kGT2) k_gram_partial(const T* __restrict__ X0, const T* __restrict__ X1,
+                                                       int64_t xbstride, int px, const T* __restrict__ Y, int py,
+                                                       int64_t vstride, int64_t n, double* __restrict__ P) {
+  extern __shared__ __align__(16) unsigned char gsm[];
+  T(*sx)[kTile + 1] = reinterpret_cast<T(*)[kTile + 1]>(gsm);
+  T(*sy)[kTile + 1] = reinterpret_cast<T(*)[kTile + 1]>(gsm + sizeof(T) * kBP * (kTile + 1));
+  double* red = reinterpret_cast<double*>(gsm);  // reused after the element loop: [kGT2][16]
+  const T* X = xbstride ? X0 + blockIdx.y * xbstride : (blockIdx.y == 0 ? X0 : X1);
+  const int TI = (px + 3) / 4, TJ = (py + 3) / 4, ntile = TI * TJ;
+  const int nslice = kGT2 / ntile;
+  const int q = threadIdx.x % ntile, sl = threadIdx.x / ntile;
+  const bool worker = sl < nslice;
+  const int ti = q / TJ, tj = q - ti * TJ;
+  GAcc<T> acc[4][4];
+  // thread t stages element e = t % kTile of rows i = t / kTile + 4 m, m < 8 (kGT2 = 4 kTile);
+  // the next tile is fetched into registers while the current one is multiplied.
+  constexpr int kRowsPerPass = kGT2 / kTile;
+  constexpr int kPasses = kBP / kRowsPerPass;
+  const int e_ld = threadIdx.x % kTile, i_ld = threadIdx.x / kTile;
+  T rx[kPasses], ry[kPasses];
+  auto fetch = [&](int64_t o0) {
+    const int64_t o = o0 + e_ld;
+    const bool ok = o < n;
+#pragma unroll
+    for (int m = 0; m < kPasses; ++m) {
+      const int i = i_ld + kRowsPerPass * m;
+      rx[m] = (ok && i < px) ? X[i * vstride + o] : T(0);
+      ry[m] = (ok && i < py) ? Y[i * vstride + o] : T(0);
+    }
+  };
+  int64_t o0 = (int64_t)blockIdx.x * kTile;
+  if (o0 < n) fetch(o0);
+  for (; o0 < n; o0 += (int64_t)gridDim.x * kTile) {
     __syncthreads();
-    for (int t = threadIdx.x; t < kBP * kTile; t += blockDim.x) {
-      const int i = t / kTile, e = t - i * kTile;
-      const int64_t o = o0 + e;
-      if (i < px) sx[i][e] = o < n ? X[i * vstride + o] : T(0);
-      if (i < py) sy[i][e] = o < n ? Y[i * vstride + o] : T(0);
+#pragma unroll
+    for (int m = 0; m < kPasses; ++m) {
+      sx[i_ld + kRowsPerPass * m][e_ld] = rx[m];
+      sy[i_ld + kRowsPerPass * m][e_ld] = ry[m];
     }
     __syncthreads();
-    int q = 0;
-    for (int t = threadIdx.x; t < npair; t += blockDim.x, ++q) {
-      const int i = t / py, j = t - i * py;
-      T s = T(0);
-#pragma unroll 8
-      for (int e = 0; e < kTile; ++e) s += sx[i][e] * sy[j][e];
-      acc[q].add(s);
+    if (o0 + (int64_t)gridDim.x * kTile < n) fetch(o0 + (int64_t)gridDim.x * kTile);
+    if (worker) {
+      T part[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) part[a][b] = T(0);
+      for (int e = sl; e < kTile; e += nslice) {
+        T xv[4], yv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          xv[a] = 4 * ti + a < px ? sx[4 * ti + a][e] : T(0);
+          yv[a] = 4 * tj + a < py ? sy[4 * tj + a][e] : T(0);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) part[a][b] += xv[a] * yv[b];
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b].add(part[a][b]);
     }
   }
-  int q = 0;
+  __syncthreads();
+  if (worker) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) red[threadIdx.x * 16 + a * 4 + b] = acc[a][b].get();
+  }
+  __syncthreads();
+  const int npair = px * py;
   const int64_t base = ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * npair;
-  for (int t = threadIdx.x; t < npair; t += blockDim.x, ++q) P[base + t] = acc[q].get();
+  for (int t = threadIdx.x; t < npair; t += blockDim.x) {
+    const int i = t / py, j = t - i * py;
+    const int qq = (i / 4) * TJ + (j / 4), ab = (i % 4) * 4 + (j % 4);
+    double v = 0.0;
+    for (int k = 0; k < nslice; ++k) v += red[(k * ntile + qq) * 16 + ab];
+    P[base + t] = v;
+  }
 }
 
 __global__ void k_gram_finish(const double* __restrict__ P, int nchunk, int npair, double* __restrict__ G) {
@@ -97,100 +154,148 @@ __global__ void k_gram_finish(const double* __restrict__ P, int nchunk, int npai
   }
 }
 
-// Y_j[o] (mode 0: =, 1: -=) sum over X blocks b < nb and i < px of X_{b,i}[o] C[b][i][j].
 template <typename T>
-__global__ void __launch_bounds__(kGT2) k_block_axpy(T* __restrict__ Y, int py, const T* __restrict__ X0,
+struct VE;
+template <>
+struct VE<float> {
+  using v = float4;
+  static constexpr int n = 4;
+};
+template <>
+struct VE<double> {
+  using v = double2;
+  static constexpr int n = 2;
+};
+
+// Y_j[o] (mode 0: =, 1: -=) sum_k X_k[o] C[k][j] for k < K = nb * px, j < py <= PY.  Each thread
+// owns one 16-byte group of elements and all PY outputs in registers; the coefficients are
+// broadcast from shared memory.  Reads of X at the thread's elements all precede its writes,
+// so Y may alias a block of X.  X blocks: X0 + b * xbstride, or X0 / X1 (xbstride == 0).
+template <typename T, int PY>
+__global__ void __launch_bounds__(kGT2) k_block_axpy(T* __restrict__ Y, int py, const T* X0, const T* X1,
                                                      int64_t xbstride, int nb, int px, const double* __restrict__ C,
                                                      int64_t vstride, int64_t n, int mode) {
-  extern __shared__ unsigned char smraw[];
-  T* sc = reinterpret_cast<T*>(smraw);  // [nb][px][py]
-  const int nc = nb * px * py;
-  for (int t = threadIdx.x; t < nc; t += blockDim.x) sc[t] = (T)C[t];
+  using V = typename VE<T>::v;
+  constexpr int NE = VE<T>::n;
+  extern __shared__ __align__(16) unsigned char asm_[];
+  T* sc = reinterpret_cast<T*>(asm_);  // [K][PY], zero beyond py
+  const int K = nb * px;
+  for (int t = threadIdx.x; t < K * PY; t += blockDim.x) {
+    const int k = t / PY, j = t - k * PY;
+    sc[t] = j < py ? (T)C[k * py + j] : T(0);
+  }
   __syncthreads();
-  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
-    T out[kBP];
+  const int64_t ng = n / NE;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = g * NE;
+    T acc[NE][PY];
 #pragma unroll
-    for (int j = 0; j < kBP; ++j) out[j] = T(0);
-    for (int b = 0; b < nb; ++b) {
-      const T* X = X0 + b * xbstride;
-      for (int i = 0; i < px; ++i) {
-        const T x = X[i * vstride + o];
-        const T* c = sc + (b * px + i) * py;
+    for (int e = 0; e < NE; ++e)
 #pragma unroll
-        for (int j = 0; j < kBP; ++j)
-          if (j < py) out[j] += x * c[j];
+      for (int j = 0; j < PY; ++j) acc[e][j] = T(0);
+    for (int k0 = 0; k0 < K; k0 += 4) {
+      V xv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int k = k0 + u;
+        if (k < K) {
+          const int b = k / px, i = k - b * px;
+          const T* X = xbstride ? X0 + b * xbstride : (b == 0 ? X0 : X1);
+          xv[u] = *reinterpret_cast<const V*>(X + i * vstride + o);
+        } else {
+          xv[u] = V{};
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (k0 + u >= K) break;
+        const T* xs = reinterpret_cast<const T*>(&xv[u]);
+        const T* c = sc + (k0 + u) * PY;
+#pragma unroll
+        for (int j = 0; j < PY; ++j) {
+          const T cj = c[j];
+#pragma unroll
+          for (int e = 0; e < NE; ++e) acc[e][j] += xs[e] * cj;
+        }
       }
     }
 #pragma unroll
-    for (int j = 0; j < kBP; ++j) {
+    for (int j = 0; j < PY; ++j) {
       if (j >= py) break;
-      T* y = Y + j * vstride + o;
-      *y = mode ? *y - out[j] : out[j];
+      V* yp = reinterpret_cast<V*>(Y + j * vstride + o);
+      V yv = mode ? *yp : V{};
+      T* ys = reinterpret_cast<T*>(&yv);
+#pragma unroll
+      for (int e = 0; e < NE; ++e) ys[e] = mode ? ys[e] - acc[e][j] : acc[e][j];
+      *yp = yv;
     }
   }
 }
 
 // ---- small dense work of one block step (one thread block) ---------------------------------
-// Cyclic Jacobi eigen-decomposition of a symmetric p x p matrix (p <= 32) in place: a -> diag,
-// v -> eigenvectors (columns).
-__device__ void jacobi_eig(double* a, double* v, int p) {
-  for (int i = 0; i < p; ++i)
-    for (int j = 0; j < p; ++j) v[i * p + j] = i == j ? 1.0 : 0.0;
-  for (int sweep = 0; sweep < 60; ++sweep) {
-    double off = 0.0, tot = 0.0;
-    for (int i = 0; i < p; ++i)
-      for (int j = 0; j < p; ++j) {
-        tot += a[i * p + j] * a[i * p + j];
-        if (i != j) off += a[i * p + j] * a[i * p + j];
-      }
-    if (off <= 1e-30 * tot || off == 0.0) break;
-    for (int r = 0; r < p; ++r)
-      for (int q = r + 1; q < p; ++q) {
-        const double arq = a[r * p + q];
-        if (fabs(arq) < 1e-300) continue;
-        const double theta = (a[q * p + q] - a[r * p + r]) / (2.0 * arq);
-        const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-        for (int k = 0; k < p; ++k) {
-          const double akr = a[k * p + r], akq = a[k * p + q];
-          a[k * p + r] = c * akr - s * akq;
-          a[k * p + q] = s * akr + c * akq;
-        }
-        for (int k = 0; k < p; ++k) {
-          const double ark = a[r * p + k], aqk = a[q * p + k];
-          a[r * p + k] = c * ark - s * aqk;
-          a[q * p + k] = s * ark + c * aqk;
-        }
-        for (int k = 0; k < p; ++k) {
-          const double vkr = v[k * p + r], vkq = v[k * p + q];
-          v[k * p + r] = c * vkr - s * vkq;
-          v[k * p + q] = s * vkr + c * vkq;
-        }
-      }
-  }
-}
-
 // SVQB of a block with Gram G: Cout = U l^{-1/2} (new basis = W Cout), Bout = l^{1/2} U^T
 // (W = new basis * Bout); directions with l <= thr are dropped (zero columns / rows).  Writes
-// the number of kept directions to *rank.  One thread does the work (p <= 32).
-__global__ void k_svqb(const double* __restrict__ G, int p, double thr, double* __restrict__ Cout,
-                       double* __restrict__ Bout, int* __restrict__ rank) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double a[kBP * kBP], v[kBP * kBP];
-  for (int i = 0; i < p * p; ++i) a[i] = 0.5 * (G[i] + G[(i % p) * p + i / p]);
-  jacobi_eig(a, v, p);
-  int r = 0;
-  for (int k = 0; k < p; ++k) {
-    const double l = a[k * p + k];
-    const bool keep = l > thr;
-    r += keep;
-    const double f = keep ? 1.0 / sqrt(l) : 0.0, g = keep ? sqrt(l) : 0.0;
-    for (int i = 0; i < p; ++i) {
-      Cout[i * p + k] = v[i * p + k] * f;  // column k of C
-      Bout[k * p + i] = v[i * p + k] * g;  // row k of B
-    }
+// the number of kept directions to *rank.  Cyclic Jacobi on one warp (lane k updates row and
+// column k of each rotation), stopped when the off-diagonal norm is below 1e-26 of the total.
+__global__ void __launch_bounds__(32) k_svqb(const double* __restrict__ G, int p, double thr,
+                                             double* __restrict__ Cout, double* __restrict__ Bout,
+                                             int* __restrict__ rank) {
+  __shared__ double a[kBP][kBP + 1], v[kBP][kBP + 1];
+  const int lane = threadIdx.x;
+  for (int t = lane; t < p * p; t += 32) {
+    const int i = t / p, j = t - i * p;
+    a[i][j] = 0.5 * (G[i * p + j] + G[j * p + i]);
+    v[i][j] = i == j ? 1.0 : 0.0;
   }
-  *rank = r;
+  __syncwarp();
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int t = lane; t < p * p; t += 32) {
+      const int i = t / p, j = t - i * p;
+      tot += a[i][j] * a[i][j];
+      if (i != j) off += a[i][j] * a[i][j];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    }
+    if (!(off > 1e-26 * tot)) break;
+    for (int r = 0; r < p; ++r)
+      for (int q = r + 1; q < p; ++q) {
+        __syncwarp();
+        const double arq = a[r][q];
+        if (fabs(arq) < 1e-300) continue;
+        const double theta = (a[q][q] - a[r][r]) / (2.0 * arq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+        __syncwarp();
+        if (lane < p) {  // columns r, q
+          const double akr = a[lane][r], akq = a[lane][q];
+          a[lane][r] = c * akr - sn * akq;
+          a[lane][q] = sn * akr + c * akq;
+          const double vkr = v[lane][r], vkq = v[lane][q];
+          v[lane][r] = c * vkr - sn * vkq;
+          v[lane][q] = sn * vkr + c * vkq;
+        }
+        __syncwarp();
+        if (lane < p) {  // rows r, q
+          const double ark = a[r][lane], aqk = a[q][lane];
+          a[r][lane] = c * ark - sn * aqk;
+          a[q][lane] = sn * ark + c * aqk;
+        }
+      }
+  }
+  __syncwarp();
+  int r = 0;
+  for (int k = 0; k < p; ++k) r += a[k][k] > thr;
+  for (int t = lane; t < p * p; t += 32) {
+    const int i = t / p, k = t - i * p;
+    const double l = a[k][k];
+    const bool keep = l > thr;
+    Cout[i * p + k] = keep ? v[i][k] / sqrt(l) : 0.0;
+    Bout[k * p + i] = keep ? v[i][k] * sqrt(l) : 0.0;
+  }
+  if (lane == 0) *rank = r;
 }
 
 // out = a * b (p x p), optionally transposing b: used to chain the two SVQB factors and to form
@@ -205,10 +310,23 @@ __global__ void k_small_gemm(const double* __restrict__ a, const double* __restr
   }
 }
 
-__global__ void k_small_copy(const double* __restrict__ a, int n, double* __restrict__ out, int sym) {
+// out = a + beta * out (p x p)
+__global__ void k_small_axpy(const double* __restrict__ a, int n, double* __restrict__ out, double beta) {
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) out[t] = a[t] + (beta != 0.0 ? beta * out[t] : 0.0);
+}
+
+// out = a, or its symmetric part (sym); each unordered pair is read and written by one thread,
+// so out may alias a.
+__global__ void k_small_copy(const double* a, int n, double* out, int sym) {
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
     const int i = t / n, j = t - i * n;
-    out[t] = sym ? 0.5 * (a[t] + a[j * n + i]) : a[t];
+    if (!sym) {
+      out[t] = a[t];
+    } else if (i <= j) {
+      const double v = 0.5 * (a[i * n + j] + a[j * n + i]);
+      out[i * n + j] = v;
+      out[j * n + i] = v;
+    }
   }
 }
 
@@ -322,18 +440,19 @@ __global__ void __launch_bounds__(256) k_band_cf(BandCoeffs bc, const double2* _
 // ---- driver -----------------------------------------------------------------------------------
 static int g_grid(int64_t n, int per) {
   int64_t b = (n + per - 1) / per;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 4));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
 }
 
 template <typename T>
-static void gram(const T* X, int64_t xbstride, int nb, int px, const T* Y, int py, int64_t vstride, int64_t n,
-                 DevBuf<double>& P, double* G, cudaStream_t s) {
-  const int nchunk = std::min<int64_t>((n + kTile - 1) / kTile, 304);
+static void gram(const T* X, const T* X1, int64_t xbstride, int nb, int px, const T* Y, int py, int64_t vstride,
+                 int64_t n, DevBuf<double>& P, double* G, cudaStream_t s) {
+  const int nchunk = (int)std::min<int64_t>((n + kTile - 1) / kTile, 152 * 8);
   const int npair = px * py;
   if (P.n < (size_t)nb * nchunk * npair) P.alloc((size_t)nb * nchunk * npair);
+  const size_t smem = std::max(2 * sizeof(T) * kBP * (kTile + 1), sizeof(double) * kGT2 * 16);
   {
     ProfScope ps_(K_BAND, s, 0.0);
-    k_gram_partial<T><<<dim3(nchunk, nb), kGT2, 0, s>>>(X, xbstride, px, Y, py, vstride, n, P.p);
+    k_gram_partial<T><<<dim3(nchunk, nb), kGT2, smem, s>>>(X, X1, xbstride, px, Y, py, vstride, n, P.p);
     ED_CHECK_LAUNCH();
   }
   ProfScope ps_(K_BAND, s, 0.0);
@@ -341,19 +460,35 @@ static void gram(const T* X, int64_t xbstride, int nb, int px, const T* Y, int p
   ED_CHECK_LAUNCH();
 }
 
+template <typename T, int PY>
+static void block_axpy_launch(T* Y, int py, const T* X, const T* X1, int64_t xbstride, int nb, int px, const double* C,
+                              int64_t vstride, int64_t n, int mode, cudaStream_t s) {
+  const size_t smem = (size_t)nb * px * PY * sizeof(T);
+  ProfScope ps_(K_BAND, s, 0.0);
+  k_block_axpy<T, PY><<<g_grid(n / VE<T>::n, kGT2), kGT2, smem, s>>>(Y, py, X, X1, xbstride, nb, px, C, vstride, n, mode);
+  ED_CHECK_LAUNCH();
+}
+
+// Y -= / = X C over nb blocks of X; n is a multiple of the 16-byte element group (padded rows).
 template <typename T>
-static void block_axpy(T* Y, int py, const T* X, int64_t xbstride, int nb, int px, const double* C, int64_t vstride,
-                       int64_t n, int mode, cudaStream_t s) {
-  // coefficients of at most `per` blocks are staged in 48 KB of shared memory per launch
-  const int per = std::max(1, (int)((48 * 1024) / ((size_t)px * py * sizeof(T))));
+static void block_axpy(T* Y, int py, const T* X, const T* X1, int64_t xbstride, int nb, int px, const double* C,
+                       int64_t vstride, int64_t n, int mode, cudaStream_t s) {
+  if (py > 16) throw Error(ED_ERR_INVALID, "band Lanczos block width above 16 is not supported");
+  const int PYs = py <= 4 ? 4 : py <= 8 ? 8 : 16;
+  // at most 64 coefficient rows per launch (one pass over the X blocks they touch)
+  const int per = std::max(1, 64 / px);
   for (int b0 = 0; b0 < nb; b0 += per) {
     const int m = std::min(per, nb - b0);
-    const size_t smem = (size_t)m * px * py * sizeof(T);
     if (mode == 0 && b0 > 0) throw Error(ED_ERR_INVALID, "block_axpy: assignment over several chunks");
-    ProfScope ps_(K_BAND, s, 0.0);
-    k_block_axpy<T><<<g_grid(n, kGT2), kGT2, smem, s>>>(Y, py, X + (int64_t)b0 * xbstride, xbstride, m, px,
-                                                        C + (int64_t)b0 * px * py, vstride, n, mode);
-    ED_CHECK_LAUNCH();
+    const T* xa = xbstride ? X + (int64_t)b0 * xbstride : (b0 == 0 ? X : X1);
+    const T* xb = xbstride ? nullptr : X1;
+    const double* cb = C + (int64_t)b0 * px * py;
+    if (PYs == 4)
+      block_axpy_launch<T, 4>(Y, py, xa, xb, xbstride, m, px, cb, vstride, n, mode, s);
+    else if (PYs == 8)
+      block_axpy_launch<T, 8>(Y, py, xa, xb, xbstride, m, px, cb, vstride, n, mode, s);
+    else
+      block_axpy_launch<T, 16>(Y, py, xa, xb, xbstride, m, px, cb, vstride, n, mode, s);
   }
 }
 
@@ -413,14 +548,14 @@ static bool band_part(ed_cluster& c, int spin, bool electron, const DevBuf<doubl
   auto orthonormalize = [&](double scale2, double* Bfinal) -> int {
     // two SVQB passes: W = X (B2 B1)
     int r = 0;
-    gram<T>(Wb.p, 0, 1, p, Wb.p, p, vstride, n, P, G.p, s);
+    gram<T>(Wb.p, nullptr, 0, 1, p, Wb.p, p, vstride, n, P, G.p, s);
     { ProfScope ps_(K_BAND, s, 0.0); k_svqb<<<1, 32, 0, s>>>(G.p, p, eps_rel * eps_rel * scale2, Cm.p, Bm.p, rank.p); }
     ED_CHECK_LAUNCH();
-    block_axpy<T>(Wb.p, p, Wb.p, 0, 1, p, Cm.p, vstride, n, 0, s);
-    gram<T>(Wb.p, 0, 1, p, Wb.p, p, vstride, n, P, G.p, s);
+    block_axpy<T>(Wb.p, p, Wb.p, nullptr, 0, 1, p, Cm.p, vstride, n, 0, s);
+    gram<T>(Wb.p, nullptr, 0, 1, p, Wb.p, p, vstride, n, P, G.p, s);
     { ProfScope ps_(K_BAND, s, 0.0); k_svqb<<<1, 32, 0, s>>>(G.p, p, 0.25, C2.p, B2.p, rank.p); }
     ED_CHECK_LAUNCH();
-    block_axpy<T>(Wb.p, p, Wb.p, 0, 1, p, C2.p, vstride, n, 0, s);
+    block_axpy<T>(Wb.p, p, Wb.p, nullptr, 0, 1, p, C2.p, vstride, n, 0, s);
     { ProfScope ps_(K_BAND, s, 0.0); k_small_gemm<<<1, 256, 0, s>>>(B2.p, Bm.p, p, 0, Bfinal, 1.0); }
     ED_CHECK_LAUNCH();
     ED_CUDA(cudaMemcpyAsync(&r, rank.p, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -448,30 +583,30 @@ static bool band_part(ed_cluster& c, int spin, bool electron, const DevBuf<doubl
   for (int j = 0; j < kmax; ++j) {
     // W = H X_j
     for (int i = 0; i < p; ++i) launch_hpsi(sv, c.hp, dtype, Xb(j) + i * vstride, Wb.p + i * vstride, s);
-    // A_j = X_j^T W ; W -= X_j A_j
-    gram<T>(Xb(j), 0, 1, p, Wb.p, p, vstride, n, P, A.p + (int64_t)j * pp, s);
+    // project W on the previous blocks and remove the projection: on every stored block twice
+    // (classical Gram-Schmidt twice), or once on [X_{j-1}, X_j] (the three-term block recurrence,
+    // as the band method of Sec. 4.4 orthogonalizes only against the band).  The X_j components
+    // give A_j.
+    for (int pass = 0; pass < (full ? 2 : 1); ++pass) {
+      int nbk;
+      if (full) {
+        nbk = j + 1;
+        gram<T>(Xb(0), nullptr, blk, nbk, p, Wb.p, p, vstride, n, P, G.p, s);
+        block_axpy<T>(Wb.p, p, Xb(0), nullptr, blk, nbk, p, G.p, vstride, n, 1, s);
+      } else if (j > 0) {
+        nbk = 2;
+        gram<T>(Xb(j - 1), Xb(j), 0, 2, p, Wb.p, p, vstride, n, P, G.p, s);
+        block_axpy<T>(Wb.p, p, Xb(j - 1), Xb(j), 0, 2, p, G.p, vstride, n, 1, s);
+      } else {
+        nbk = 1;
+        gram<T>(Xb(0), nullptr, 0, 1, p, Wb.p, p, vstride, n, P, G.p, s);
+        block_axpy<T>(Wb.p, p, Xb(0), nullptr, 0, 1, p, G.p, vstride, n, 1, s);
+      }
+      { ProfScope ps_(K_BAND, s, 0.0); k_small_axpy<<<1, 256, 0, s>>>(G.p + (int64_t)(nbk - 1) * pp, p, A.p + (int64_t)j * pp, pass ? 1.0 : 0.0); }
+      ED_CHECK_LAUNCH();
+    }
     { ProfScope ps_(K_BAND, s, 0.0); k_small_copy<<<1, 256, 0, s>>>(A.p + (int64_t)j * pp, p, A.p + (int64_t)j * pp, 1); }
     ED_CHECK_LAUNCH();
-    block_axpy<T>(Wb.p, p, Xb(j), 0, 1, p, A.p + (int64_t)j * pp, vstride, n, 1, s);
-    if (j > 0) {
-      // W -= X_{j-1} B_{j-1}^T via the Gram with X_{j-1} (equal to B_{j-1}^T up to rounding)
-      gram<T>(Xb(j - 1), 0, 1, p, Wb.p, p, vstride, n, P, tmp.p, s);
-      block_axpy<T>(Wb.p, p, Xb(j - 1), 0, 1, p, tmp.p, vstride, n, 1, s);
-    }
-    // reorthogonalization: twice against every stored block, or once against the last two
-    for (int pass = 0; pass < (full ? 2 : 1); ++pass) {
-      const int first = full ? 0 : std::max(0, j - 1);
-      const int nbk = j - first + 1;
-      if (full) {
-        gram<T>(Xb(first), blk, nbk, p, Wb.p, p, vstride, n, P, G.p, s);
-        block_axpy<T>(Wb.p, p, Xb(first), blk, nbk, p, G.p, vstride, n, 1, s);
-      } else {
-        for (int b = first; b <= j; ++b) {
-          gram<T>(Xb(b), 0, 1, p, Wb.p, p, vstride, n, P, G.p, s);
-          block_axpy<T>(Wb.p, p, Xb(b), 0, 1, p, G.p, vstride, n, 1, s);
-        }
-      }
-    }
     // W = X_{j+1} B_j
     const int r = orthonormalize(scale2, B.p + (int64_t)j * pp);
     k = j + 1;
