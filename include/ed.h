@@ -149,6 +149,24 @@ ed_status ed_hop_table(ed_cluster* c, int N, int32_t* row_ptr, uint32_t* entries
 ed_status ed_hpsi(ed_cluster* c, int n_up, int n_dn, int dtype, const void* x, void* y, int64_t ld,
                   void* stream);
 
+/* y = H x in the cluster's own sector (n_up, n_dn of its description) and, in FP64 device memory,
+ * out3[0] = <x, y>, out3[1] = <y, y>, out3[2] = <x, x>, for callers that must not allocate device
+ * memory (an application that manages the GPU's memory itself, through its own pool or caching
+ * allocator, cannot let the library call cudaMalloc).  The paper has no counterpart: this is an
+ * interface of this library.  The call allocates nothing: the reduction scratch is a fixed
+ * 96 KiB array inside libed, and the sector's tables are the ones ed_cluster_create built.
+ *  - x, y: device arrays of d_up rows with leading dimension ld (ld <= 0 means d_dn), dtype
+ *    ED_FP64 or ED_FP32; they must not overlap.  out3: 3 doubles of device memory.
+ *  - Sectors larger than 4,194,304 elements (d_up * d_dn) are rejected with ED_ERR_TOO_LARGE.
+ *  - The first call on a device looks up the scratch array's device address (once per device,
+ *    with that device current); make that first call before any stream capture.
+ *  - Every call shares the scratch array, and the array keeps the last call's contents; calls
+ *    whose kernels overlap on the GPU (different streams or host threads) race on it and must be
+ *    ordered by the caller.
+ *  - Asynchronous on `stream` (NULL is the CUDA default stream). */
+ed_status ed_hpsi_dots_static(ed_cluster* c, int dtype, const void* x, void* y, int64_t ld, double* out3,
+                              void* stream);
+
 /* ---- measurement of the library's own kernels (no counterpart in the paper) --------------- */
 
 /* Kernel families. */

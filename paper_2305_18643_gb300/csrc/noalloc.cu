@@ -1,0 +1,204 @@
+// ed_hpsi_dots_static: the product y = H x and the reductions <x,y>, <y,y>, <x,x> for callers
+// that must not allocate device memory.  An application that hands libed a memory budget it
+// manages itself (a caching allocator or a pool reserved at start-up), or that runs its solver
+// inside a region where allocating would stall other streams, cannot let the library call
+// cudaMalloc.  Here the only scratch, the per-block partial sums of the reductions and the
+// ticket that picks the block finishing them, lives in fixed arrays inside libed.
+#include <algorithm>
+#include <mutex>
+
+#include "ed_common.cuh"
+
+namespace ed {
+
+constexpr int kStaticThreads = 256;
+constexpr int kStaticPerThread = 4;
+constexpr int kStaticMaxBlocks = 4096;  // 4096 * 3 doubles = 96 KiB of scratch
+constexpr int64_t kStaticMaxDim = (int64_t)kStaticMaxBlocks * kStaticThreads * kStaticPerThread;  // 4,194,304
+
+// Shared by every call on a device, and held by every GPU that loads the library until exit.
+static __device__ __align__(256) double g_static_partial[kStaticMaxBlocks * 3];
+static __device__ __align__(256) unsigned int g_static_ticket[64];
+
+template <typename T>
+struct SPrec;
+template <>
+struct SPrec<double> {
+  __device__ static const double* e_up(const SectorView& s) { return s.e_up; }
+  __device__ static const double* e_dn(const SectorView& s) { return s.e_dn; }
+  __device__ static double val(const HopParams& h, int i) { return h.val[i]; }
+  __device__ static double U(const HopParams& h, int i) { return h.U[i]; }
+};
+template <>
+struct SPrec<float> {
+  __device__ static const float* e_up(const SectorView& s) { return s.e_up32; }
+  __device__ static const float* e_dn(const SectorView& s) { return s.e_dn32; }
+  __device__ static float val(const HopParams& h, int i) { return h.valf[i]; }
+  __device__ static float U(const HopParams& h, int i) { return h.Uf[i]; }
+};
+
+__device__ __forceinline__ void static_block_sum3(double& a, double& b, double& c) {
+  __shared__ double sm[3][kStaticThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+    c += __shfl_down_sync(0xffffffffu, c, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    sm[0][w] = a;
+    sm[1][w] = b;
+    sm[2][w] = c;
+  }
+  __syncthreads();
+  if (w == 0) {
+    a = l < kStaticThreads / 32 ? sm[0][l] : 0.0;
+    b = l < kStaticThreads / 32 ? sm[1][l] : 0.0;
+    c = l < kStaticThreads / 32 ? sm[2][l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      b += __shfl_down_sync(0xffffffffu, b, o);
+      c += __shfl_down_sync(0xffffffffu, c, o);
+    }
+  }
+  __syncthreads();
+}
+
+// One thread per element (kStaticPerThread elements per thread, one grid pass); block partial
+// sums go to `partial`, the last block (ticket) adds them in block order into out3.
+template <typename T>
+__global__ void __launch_bounds__(kStaticThreads) k_hpsi_dots_static(SectorView sv, HopParams hp, const T* __restrict__ X,
+                                                                     T* __restrict__ Y, double* __restrict__ partial,
+                                                                     unsigned int* __restrict__ ticket,
+                                                                     double* __restrict__ out3) {
+  __shared__ T sval[kMaxVals];
+  __shared__ T sU[kMaxOrb];
+  __shared__ bool s_last;
+  for (int i = threadIdx.x; i < kMaxVals; i += blockDim.x) sval[i] = SPrec<T>::val(hp, i);
+  for (int i = threadIdx.x; i < kMaxOrb; i += blockDim.x) sU[i] = SPrec<T>::U(hp, i);
+  __syncthreads();
+  const int64_t dim = sv.d_up * sv.d_dn;
+  double sxy = 0.0, syy = 0.0, sxx = 0.0;
+  for (int k = 0; k < kStaticPerThread; ++k) {
+    const int64_t idx = ((int64_t)blockIdx.x * kStaticPerThread + k) * kStaticThreads + threadIdx.x;
+    if (idx >= dim) break;
+    const int64_t u = idx / sv.d_dn, d = idx - u * sv.d_dn;
+    const T* xr = X + u * sv.ld;
+    const uint32_t bu = sv.B_up[u], bd = sv.B_dn[d];
+    T diag = SPrec<T>::e_up(sv)[u] + SPrec<T>::e_dn(sv)[d];
+    uint32_t dbl = bu & bd & hp.umask;
+    while (dbl) {
+      diag += sU[__ffs(dbl) - 1];
+      dbl &= dbl - 1u;
+    }
+    T acc = diag * xr[d];
+    for (int32_t q = sv.ptr_dn[d]; q < sv.ptr_dn[d + 1]; ++q) {
+      const uint32_t e = __ldg(sv.ent_dn + q);
+      const T v = sval[ent_vidx(e)], x = __ldg(xr + ent_col(e));
+      acc += ent_neg(e) ? -v * x : v * x;
+    }
+    for (int32_t q = sv.ptr_up[u]; q < sv.ptr_up[u + 1]; ++q) {
+      const uint32_t e = __ldg(sv.ent_up + q);
+      const T v = sval[ent_vidx(e)], x = __ldg(X + (int64_t)ent_col(e) * sv.ld + d);
+      acc += ent_neg(e) ? -v * x : v * x;
+    }
+    Y[u * sv.ld + d] = acc;
+    const double xv = (double)xr[d], yv = (double)acc;
+    sxy += xv * yv;
+    syy += yv * yv;
+    sxx += xv * xv;
+  }
+  static_block_sum3(sxy, syy, sxx);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x * 3 + 0] = sxy;
+    partial[blockIdx.x * 3 + 1] = syy;
+    partial[blockIdx.x * 3 + 2] = sxx;
+    __threadfence();
+    const unsigned t = atomicAdd(ticket, 1u);
+    s_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+    a += __ldcg(partial + i * 3 + 0);
+    b += __ldcg(partial + i * 3 + 1);
+    c += __ldcg(partial + i * 3 + 2);
+  }
+  static_block_sum3(a, b, c);
+  if (threadIdx.x == 0) {
+    out3[0] = a;
+    out3[1] = b;
+    out3[2] = c;
+    *ticket = 0u;
+  }
+}
+
+namespace {
+struct StaticScratch {
+  double* partial = nullptr;
+  unsigned int* ticket = nullptr;
+};
+std::mutex g_static_mu;
+StaticScratch g_static_dev[64];  // per device ordinal, filled by the first call on that device
+}  // namespace
+
+// Device addresses of the fixed scratch on the current device (looked up once per device).
+static StaticScratch static_scratch() {
+  int dev = 0;
+  ED_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) throw Error(ED_ERR_INVALID, "device ordinal above 63");
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  StaticScratch& s = g_static_dev[dev];
+  if (!s.partial) {
+    void* p = nullptr;
+    void* t = nullptr;
+    ED_CUDA(cudaGetSymbolAddress(&p, g_static_partial));
+    ED_CUDA(cudaGetSymbolAddress(&t, g_static_ticket));
+    s.partial = (double*)p;
+    s.ticket = (unsigned int*)t;
+  }
+  return s;
+}
+
+}  // namespace ed
+
+using namespace ed;
+
+extern "C" ed_status ed_hpsi_dots_static(ed_cluster* c, int dtype, const void* x, void* y, int64_t ld, double* out3,
+                                         void* stream) {
+  try {
+    if (!c || !x || !y || !out3) throw Error(ED_ERR_INVALID, "cluster, x, y and out3 must not be NULL");
+    if (dtype != ED_FP64 && dtype != ED_FP32) throw Error(ED_ERR_INVALID, "dtype must be ED_FP64 or ED_FP32");
+    // the cluster's own sector: its tables were built by ed_cluster_create, nothing is allocated
+    auto iu = c->spins.find(c->desc.n_up), idn = c->spins.find(c->desc.n_dn);
+    if (iu == c->spins.end() || idn == c->spins.end()) throw Error(ED_ERR_STATE, "cluster tables missing");
+    const int64_t du = iu->second->dim, dd = idn->second->dim;
+    if (du * dd > kStaticMaxDim)
+      throw Error(ED_ERR_TOO_LARGE, "sector dimension " + std::to_string(du * dd) +
+                                        " exceeds the 4,194,304 elements covered by the fixed scratch of ed_hpsi_dots_static");
+    if (ld > 0 && ld < dd) throw Error(ED_ERR_INVALID, "ld must be >= d_dn (or <= 0 for d_dn)");
+    SectorView sv = c->view(c->desc.n_up, c->desc.n_dn, ld);
+    StaticScratch s = static_scratch();
+    cudaStream_t st = (cudaStream_t)stream;
+    ED_CUDA(cudaMemsetAsync(s.ticket, 0, sizeof(unsigned int), st));  // the ticket must start at zero
+    const int64_t per = (int64_t)kStaticThreads * kStaticPerThread;
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, (du * dd + per - 1) / per);
+    note_launch();
+    if (dtype == ED_FP64)
+      k_hpsi_dots_static<double><<<blocks, kStaticThreads, 0, st>>>(sv, c->hp, (const double*)x, (double*)y, s.partial,
+                                                                     s.ticket, out3);
+    else
+      k_hpsi_dots_static<float><<<blocks, kStaticThreads, 0, st>>>(sv, c->hp, (const float*)x, (float*)y, s.partial,
+                                                                    s.ticket, out3);
+    ED_CHECK_LAUNCH();
+    return ED_OK;
+  } catch (const Error& e) {
+    set_last_error(e.what());
+    return e.code;
+  } catch (const std::exception& e) {
+    set_last_error(e.what());
+    return ED_ERR_INVALID;
+  }
+}

@@ -70,6 +70,7 @@ def lib():
             "ed_profile_kernel_name": (C.c_char_p, [i32]),
             "ed_launch_count": (i64, []),
             "ed_set_option": (i32, [vp, i32, C.c_double]),
+            "ed_hpsi_dots_static": (i32, [vp, i32, vp, vp, i64, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -218,6 +219,13 @@ def ed_profile_kernel_name(kernel):
 
 def ed_launch_count():
     return int(lib().ed_launch_count())
+
+
+def ed_hpsi_dots_static(h, dtype, x_ptr, y_ptr, out3_ptr, ld=0, stream=0):
+    """y = H x in the cluster's own sector and <x,y>, <y,y>, <x,x> into out3 (device FP64), using
+    the library's fixed scratch instead of device allocations; asynchronous on `stream`."""
+    _check(lib().ed_hpsi_dots_static(h, int(dtype), C.c_void_p(x_ptr), C.c_void_p(y_ptr), int(ld),
+                                     C.c_void_p(out3_ptr), C.c_void_p(stream) if stream else None))
 
 
 class Cluster:
