@@ -123,6 +123,25 @@ ed_status ed_set_option(ed_cluster* c, int option, double value);
  * the longest run.  Any pointer may be NULL. */
 ed_status ed_green_stats(const ed_cluster* c, int64_t* total_steps, int* max_steps);
 
+/* Batched form: n independent clusters solved together.  For each cluster: the Lanczos ground
+ * state (as ed_ground_state, at most 600 levels per pass) and, when n_freq > 0, the
+ * continued-fraction Green function of Sec. 4.3 (at most min(20000, 2 d + 16) levels per run) for spin up and
+ * spin down (spin down equals spin up when n_up == n_dn), on z = omega + i eta (ED_AXIS_REAL)
+ * or i omega (ED_AXIS_MATSUBARA).  All clusters share `precision` (ED_FP64 or ED_FP32); each
+ * cluster's seed and tol are taken from its description, its precision and gf_method are
+ * ignored.  At most 20 orbitals per cluster.
+ *  - E0, residual, status, iters: n values each (host), any may be NULL; status per cluster is
+ *    ED_OK, ED_WARN_DEGENERATE or ED_WARN_NOT_CONVERGED.
+ *  - G_out: complex128 (2 doubles each), clusters one after the other, cluster c holding
+ *    [2 spins][n_freq][n_sites_c][n_sites_c]; host or device memory as out_is_device says.
+ * Tables, ground states and continued fractions of all clusters are built by a few launches:
+ * persistent kernels in which every thread block takes the next cluster (or continued fraction)
+ * from a queue, largest first.  The block width and the mapping of the block-level H.psi are
+ * picked by timing candidates on the first call for a batch shape (then cached). */
+ed_status ed_batch_solve(const ed_cluster_desc* descs, int n, int precision, const double* omega, int n_freq,
+                         double eta, int axis, double* E0, double* residual, int* status, int* iters,
+                         double* G_out, int out_is_device);
+
 /* ---- lower-level calls (parity tests and benchmarks) ------------------------------------- */
 
 /* Sector dimensions d_up = C(L, n_up), d_dn = C(L, n_dn) of any sector of this cluster. */

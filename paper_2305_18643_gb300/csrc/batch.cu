@@ -1,0 +1,1027 @@
+// Batched form: many small clusters solved together (ground state, Sec. 4.2, and continued-
+// fraction Green function, Sec. 4.3, for each).
+//
+// 1. Tables of every (cluster, particle number) needed are built by three launches into one
+//    arena.  Their sizes follow from closed forms: d = C(L, N) states and at most N (L - N) hops
+//    per state, stored slot-major ([zmax][d]) with a per-state count, so no count/scan pass runs.
+// 2. A persistent kernel solves the ground states: every block takes the next cluster from an
+//    atomic queue (largest sector first) and runs the whole Lanczos ground-state algorithm of
+//    the single-cluster path inside the block (block-level fused H.psi with FP64 reductions, the
+//    tridiagonal check of tridiag.cuh, the retrace, the FP64 polish and restarts).
+// 3. A second persistent kernel runs the continued fractions: every block takes the next
+//    (cluster, spin, part, pair) from the queue, applies c+ / c to the ground state and runs the
+//    recursion with the convergence check on the frequency grid.
+// 4. Two grid-wide kernels evaluate every continued fraction on the grid and assemble G.
+// Block width and the element-to-thread mapping of the block-level H.psi are picked by an
+// autotuner on the first call for a given batch shape.  No block ever waits on another block.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <numeric>
+#include <tuple>
+
+#include "ed_common.cuh"
+#include "tridiag.cuh"
+
+namespace ed {
+
+constexpr int kBMaxIter = 600;     // Lanczos levels per ground-state pass
+constexpr int kBMaxL = 20;         // orbitals per batched cluster
+constexpr int kBCheck = 10;
+
+struct BBinom {
+  uint32_t c[kMaxOrb + 1][kMaxOrb + 1];
+};
+
+struct BTable {            // one spin sector of one cluster
+  int L, N, split, zmax;
+  int64_t dim;
+  uint32_t* basis;         // [dim]
+  int32_t* rank_lo;        // [2^split]
+  int32_t* rank_hi;        // [2^(L - split)]
+  uint32_t* ell;           // [zmax][dim] packed entries (col << 8 | neg << 7 | vidx)
+  uint8_t* cnt;            // [dim] entries of each state
+  double* e64;             // [dim] one-body diagonal
+  float* e32;
+  int cluster;
+};
+
+struct BPair {
+  uint32_t a, b, vidx, between;
+};
+
+struct BCluster {
+  HopParams hp;
+  int ns, L, n_up, n_dn;
+  int t_up, t_dn;            // GS tables
+  int t_upp, t_upm, t_dnp, t_dnm;   // N +- 1 tables (-1: none)
+  int64_t d;                 // GS sector dimension
+  double* omega;             // FP64 ground state [d]
+  uint64_t seed;
+  double tol;
+  int precision;
+  // results
+  double E0, residual, gap;
+  int iters, status;
+};
+
+struct BRun {                // one continued fraction
+  int cluster, spin, part, i, j;   // part 0 electron, 1 hole; j = -1 for a diagonal run
+  int tu, td;                // target sector tables
+  int src;                   // table of the changed spin in the GS sector
+  int64_t d;                 // target sector dimension
+  double* alpha;             // [mmax]
+  double* beta;              // [mmax + 1]
+  int mmax;                  // levels of this run: min(cap, 2 d + 16), as the single-cluster path
+  double b0sq;
+  int nsteps;
+};
+
+// -------------------------------------------------------------------------------- tables
+__global__ void k_bt_basis(BTable* __restrict__ T, BBinom bn) {
+  BTable t = T[blockIdx.y];
+  const int64_t nlo = int64_t(1) << t.split, nhi = int64_t(1) << (t.L - t.split);
+  const int64_t n = max(t.dim, max(nlo, nhi));
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    if (r < t.dim) {
+      uint32_t rem = (uint32_t)r, b = 0;
+      int p = t.L - 1;
+      for (int k = t.N; k >= 1; --k) {
+        while (bn.c[p][k] > rem) --p;
+        b |= 1u << p;
+        rem -= bn.c[p][k];
+        --p;
+      }
+      t.basis[r] = b;
+    }
+    if (r < nlo) {
+      int32_t v = 0;
+      int j = 0;
+      for (int p = 0; p < t.split; ++p)
+        if ((r >> p) & 1) v += (int32_t)bn.c[p][++j];
+      t.rank_lo[r] = v;
+    }
+    if (r < nhi) {
+      const int m = t.N - __popc((uint32_t)r);
+      int32_t v = -1;
+      if (m >= 0 && m <= t.split) {
+        v = 0;
+        int j = 0;
+        for (int q = 0; q < t.L - t.split; ++q)
+          if ((r >> q) & 1) v += (int32_t)bn.c[q + t.split][m + (++j)];
+      }
+      t.rank_hi[r] = v;
+    }
+  }
+}
+
+__global__ void k_bt_fill(BTable* __restrict__ T, const BPair* __restrict__ pairs, const int* __restrict__ pair_off,
+                          const double* __restrict__ hdiag /* [cluster][kMaxOrb] */) {
+  BTable t = T[blockIdx.y];
+  const BPair* pp = pairs + pair_off[t.cluster];
+  const int np = pair_off[t.cluster + 1] - pair_off[t.cluster];
+  const double* hd = hdiag + (int64_t)t.cluster * kMaxOrb;
+  const uint32_t lomask = (1u << t.split) - 1u;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < t.dim; r += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t s = t.basis[r];
+    int k = 0;
+    for (int q = 0; q < np; ++q) {
+      const BPair p = pp[q];
+      if (((s >> p.a) & 1u) && !((s >> p.b) & 1u)) {
+        const uint32_t c = s ^ (1u << p.a) ^ (1u << p.b);
+        const uint32_t neg = __popc(s & p.between) & 1u;
+        const uint32_t col = (uint32_t)(t.rank_lo[c & lomask] + t.rank_hi[c >> t.split]);
+        if (k < t.zmax) t.ell[(int64_t)k * t.dim + r] = (col << 8) | (neg << 7) | p.vidx;
+        ++k;
+      }
+    }
+    t.cnt[r] = (uint8_t)min(k, t.zmax);
+    double e = 0.0;
+    for (int a = 0; a < t.L; ++a)
+      if ((s >> a) & 1u) e += hd[a];
+    t.e64[r] = e;
+    t.e32[r] = (float)e;
+  }
+}
+
+// -------------------------------------------------------------------------------- block-level H.psi
+template <typename T>
+struct BP;
+template <>
+struct BP<double> {
+  __device__ static const double* e(const BTable& t) { return t.e64; }
+  __device__ static double val(const HopParams& h, int i) { return h.val[i]; }
+  __device__ static double U(const HopParams& h, int i) { return h.U[i]; }
+};
+template <>
+struct BP<float> {
+  __device__ static const float* e(const BTable& t) { return t.e32; }
+  __device__ static float val(const HopParams& h, int i) { return h.valf[i]; }
+  __device__ static float U(const HopParams& h, int i) { return h.Uf[i]; }
+};
+
+struct BlockShared {
+  double red[3][32];
+  double bcast[4];
+};
+
+__device__ __forceinline__ void bred3(double& a, double& b, double& c, BlockShared& sh) {
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+    c += __shfl_down_sync(0xffffffffu, c, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (l == 0) {
+    sh.red[0][w] = a;
+    sh.red[1][w] = b;
+    sh.red[2][w] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double x = 0, y = 0, z = 0;
+    for (int i = 0; i < nw; ++i) {
+      x += sh.red[0][i];
+      y += sh.red[1][i];
+      z += sh.red[2][i];
+    }
+    sh.bcast[0] = x;
+    sh.bcast[1] = y;
+    sh.bcast[2] = z;
+  }
+  __syncthreads();
+  a = sh.bcast[0];
+  b = sh.bcast[1];
+  c = sh.bcast[2];
+}
+
+// W = H X - bcoef * W (in place; W may hold x_prev), with <x,w>, <w,w>, <x,x> returned to every
+// thread.  mode 0: element-strided (consecutive threads take consecutive elements); mode 1: one
+// warp per row (warp-uniform up-spin entries, lanes over the columns).
+template <typename T>
+__device__ void block_hx(const BTable& tu, const BTable& td, const T* sval, const T* sU, uint32_t umask, const T* X,
+                         T* W, T bcoef, int mode, double& sxw, double& sww, double& sxx, BlockShared& sh) {
+  const int64_t du = tu.dim, dd = td.dim;
+  const T* eu = BP<T>::e(tu);
+  const T* ed = BP<T>::e(td);
+  double a = 0.0, b = 0.0, c = 0.0;
+  auto element = [&](int64_t u, int64_t d) {
+    const int64_t o = u * dd + d;
+    const uint32_t bu = tu.basis[u], bd = td.basis[d];
+    T diag = eu[u] + ed[d];
+    uint32_t dbl = bu & bd & umask;
+    while (dbl) {
+      diag += sU[__ffs(dbl) - 1];
+      dbl &= dbl - 1u;
+    }
+    const T x = X[o];
+    T acc = diag * x;
+    const T* xr = X + u * dd;
+    const int nd = td.cnt[d];
+    for (int k = 0; k < nd; ++k) {
+      const uint32_t e = td.ell[(int64_t)k * dd + d];
+      const T v = sval[ent_vidx(e)];
+      acc += (ent_neg(e) ? -v : v) * xr[ent_col(e)];
+    }
+    const int nu = tu.cnt[u];
+    for (int k = 0; k < nu; ++k) {
+      const uint32_t e = tu.ell[(int64_t)k * du + u];
+      const T v = sval[ent_vidx(e)];
+      acc += (ent_neg(e) ? -v : v) * X[(int64_t)ent_col(e) * dd + d];
+    }
+    const T w = acc - bcoef * W[o];
+    W[o] = w;
+    a += (double)x * (double)w;
+    b += (double)w * (double)w;
+    c += (double)x * (double)x;
+  };
+  if (mode == 1 && dd >= 16) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t u = warp; u < du; u += nw)
+      for (int64_t d = lane; d < dd; d += 32) element(u, d);
+  } else {
+    const int64_t n = du * dd;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const int64_t u = i / dd;
+      element(u, i - u * dd);
+    }
+  }
+  bred3(a, b, c, sh);
+  sxw = a;
+  sww = b;
+  sxx = c;
+}
+
+__device__ __forceinline__ uint64_t b_splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+struct GSShared {
+  BlockShared bs;
+  double alpha[kBMaxIter + 2];
+  double beta[kBMaxIter + 2];
+  double svec[2 * (kBMaxIter + 2)];
+  double eval[4];
+  float svalf[kMaxVals];
+  double svald[kMaxVals];
+  float sUf[kMaxOrb];
+  double sUd[kMaxOrb];
+  int flag;
+};
+
+// Hopping values and U of the block's cluster in the precision of the vectors.
+template <typename T, typename S>
+__device__ __forceinline__ const T* sval_of(const S& g) {
+  if constexpr (sizeof(T) == 8)
+    return g.svald;
+  else
+    return g.svalf;
+}
+template <typename T, typename S>
+__device__ __forceinline__ const T* sU_of(const S& g) {
+  if constexpr (sizeof(T) == 8)
+    return g.sUd;
+  else
+    return g.sUf;
+}
+
+// One Lanczos pass set (first pass + retrace) from the normalized start Vs; the ground state
+// accumulates in omega (FP64).  Returns the levels used; eval[0..2] = lowest, second, Ritz.
+template <typename T>
+__device__ int block_lanczos(const BTable& tu, const BTable& td, uint32_t umask, GSShared& g, T* V0, T* V1,
+                             const T* Vs, double* omega, double tol_ritz, int mode, bool* breakdown) {
+  const int64_t n = tu.dim * td.dim;
+  const T* sval = sval_of<T>(g);
+  const T* sU = sU_of<T>(g);
+  int m = 0;
+  *breakdown = false;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+      V0[i] = Vs[i];
+      V1[i] = T(0);
+      if (pass == 1) omega[i] = g.svec[0] * (double)Vs[i];
+    }
+    if (threadIdx.x == 0) g.beta[0] = 0.0;
+    __syncthreads();
+    T* X = V0;
+    T* P = V1;
+    const int nmax = pass == 0 ? kBMaxIter : m - 1;
+    for (int k = 0; k < nmax; ++k) {
+      double sxw, sww, sxx;
+      block_hx<T>(tu, td, sval, sU, umask, X, P, (T)g.beta[k], mode, sxw, sww, sxx, g.bs);
+      const double alpha = sxx > 0.0 ? sxw / sxx : 0.0;
+      const double b2 = sxx > 0.0 ? sww - sxw * sxw / sxx : 0.0;
+      const double bn = b2 > 0.0 ? sqrt(b2) : 0.0;
+      if (threadIdx.x == 0) {
+        g.alpha[k] = alpha;
+        g.beta[k + 1] = bn;
+      }
+      const bool stop_here = !(bn > 1e-13);
+      if (!stop_here) {
+        const T aT = (T)alpha, ibT = (T)(1.0 / bn);
+        const double cf = pass == 1 ? g.svec[k + 1] : 0.0;
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+          const T v = (P[i] - aT * X[i]) * ibT;
+          P[i] = v;
+          if (pass == 1) omega[i] += cf * (double)v;
+        }
+      }
+      __syncthreads();
+      T* t = X;
+      X = P;
+      P = t;
+      if (pass == 0 && (stop_here || (k + 1) % kBCheck == 0 || k + 1 == kBMaxIter)) {
+        const int levels = k + 1;
+        tridiag_lowest_block(g.alpha, g.beta, levels, g.eval, g.svec);
+        __syncthreads();
+        m = levels;
+        if (stop_here) {
+          *breakdown = true;
+          break;
+        }
+        if (g.eval[2] < tol_ritz * fmax(1.0, fabs(g.eval[0]))) break;
+      }
+      if (stop_here) break;
+    }
+  }
+  return m;
+}
+
+template <typename T>
+__device__ void block_ground_state(BCluster& c, const BTable* tabs, GSShared& g, T* V0, T* V1, T* Vs, double* Y64,
+                                   double* Vd0, double* Vd1, double* Vds, int mode) {
+  const BTable tu = tabs[c.t_up], td = tabs[c.t_dn];
+  const int64_t n = c.d;
+  double* om = c.omega;
+  const uint32_t umask = c.hp.umask;
+  int total = 0;
+  bool fp64 = sizeof(T) == 8;
+  double E = 0.0, res = 0.0, lam0 = 0.0, lam1 = 0.0;
+  bool ok = false;
+  for (int attempt = 0; attempt < 5 && !ok; ++attempt) {
+    double s2 = 0.0, dummy1 = 0.0, dummy2 = 0.0;
+    bool brk = false;
+    int m;
+    if (!fp64) {
+      for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const double r = (double)(b_splitmix64(c.seed ^ (uint64_t)i) >> 11) * (1.0 / 9007199254740992.0);
+        Vs[i] = attempt == 0 ? (T)(2.0 * r - 1.0) : (T)om[i];
+        s2 += (double)Vs[i] * (double)Vs[i];
+      }
+      bred3(s2, dummy1, dummy2, g.bs);
+      const T f = (T)(1.0 / sqrt(s2));
+      for (int64_t i = threadIdx.x; i < n; i += blockDim.x) Vs[i] *= f;
+      __syncthreads();
+      m = block_lanczos<T>(tu, td, umask, g, V0, V1, Vs, om, 1e-7, mode, &brk);
+    } else {
+      for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const double r = (double)(b_splitmix64(c.seed ^ (uint64_t)i) >> 11) * (1.0 / 9007199254740992.0);
+        Vds[i] = attempt == 0 && sizeof(T) == 8 ? 2.0 * r - 1.0 : om[i];
+        s2 += Vds[i] * Vds[i];
+      }
+      bred3(s2, dummy1, dummy2, g.bs);
+      const double f = 1.0 / sqrt(s2);
+      for (int64_t i = threadIdx.x; i < n; i += blockDim.x) Vds[i] *= f;
+      __syncthreads();
+      m = block_lanczos<double>(tu, td, umask, g, Vd0, Vd1, Vds, om, fmin(1e-2, 0.1 * c.tol), mode, &brk);
+    }
+    total += m;
+    lam0 = g.eval[0];
+    lam1 = g.eval[1];
+    // FP64 polish: normalize, Rayleigh quotient, explicit residual
+    double nn = 0.0, z1 = 0.0, z2 = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) nn += om[i] * om[i];
+    bred3(nn, z1, z2, g.bs);
+    const double f = 1.0 / sqrt(nn);
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+      om[i] *= f;
+      Y64[i] = 0.0;
+    }
+    __syncthreads();
+    double sxw, sww, sxx;
+    block_hx<double>(tu, td, g.svald, g.sUd, umask, om, Y64, 0.0, mode, sxw, sww, sxx, g.bs);
+    E = sxw;
+    double r2 = 0.0, q1 = 0.0, q2 = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const double rr = Y64[i] - E * om[i];
+      r2 += rr * rr;
+    }
+    bred3(r2, q1, q2, g.bs);
+    res = sqrt(fmax(r2, 0.0));
+    const double scale = fmax(1.0, fabs(E));
+    if (fp64 || c.precision == ED_FP64)
+      ok = res / scale <= c.tol || brk;
+    else
+      ok = (lam1 - E) > 0.0 && res * res / (lam1 - E) <= 1e-11 * scale;
+    if (!ok) fp64 = true;  // refine in FP64 from the current state
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    c.E0 = E;
+    c.residual = res / fmax(1.0, fabs(E));
+    c.iters = total;
+    c.gap = lam1 - lam0;
+    c.status = !ok ? ED_WARN_NOT_CONVERGED : ((lam1 - lam0) < 1e-8 * fmax(1.0, fabs(lam0)) ? ED_WARN_DEGENERATE : ED_OK);
+  }
+  __syncthreads();
+}
+
+struct BWork {
+  char* base;          // per-block workspace
+  int64_t stride;      // bytes per block
+  int64_t maxd;
+};
+
+template <typename T>
+__global__ void k_batch_gs(BCluster* __restrict__ C, const int* __restrict__ order, int n, const BTable* __restrict__ tabs,
+                           int* __restrict__ queue, BWork w, int mode) {
+  __shared__ GSShared g;
+  char* ws = w.base + (int64_t)blockIdx.x * w.stride;
+  const int64_t md = w.maxd;
+  T* V0 = (T*)ws;
+  T* V1 = V0 + md;
+  T* Vs = V1 + md;
+  double* Y64 = (double*)(ws + ((3 * md * sizeof(T) + 255) / 256) * 256);
+  double* Vd0 = Y64 + md;
+  double* Vd1 = Vd0 + md;
+  double* Vds = Vd1 + md;
+  while (true) {
+    __syncthreads();
+    if (threadIdx.x == 0) g.flag = atomicAdd(queue, 1);
+    __syncthreads();
+    const int item = g.flag;
+    if (item >= n) return;
+    BCluster& c = C[order[item]];
+    for (int i = threadIdx.x; i < kMaxVals; i += blockDim.x) {
+      g.svalf[i] = c.hp.valf[i];
+      g.svald[i] = c.hp.val[i];
+    }
+    for (int i = threadIdx.x; i < kMaxOrb; i += blockDim.x) {
+      g.sUf[i] = c.hp.Uf[i];
+      g.sUd[i] = c.hp.U[i];
+    }
+    __syncthreads();
+    block_ground_state<T>(c, tabs, g, V0, V1, Vs, Y64, Vd0, Vd1, Vds, mode);
+  }
+}
+
+// -------------------------------------------------------------------------------- continued fractions
+struct CFShared {
+  BlockShared bs;
+  double2 prev[64];
+  double maxdiff;
+  float svalf[kMaxVals];
+  double svald[kMaxVals];
+  float sUf[kMaxOrb];
+  double sUd[kMaxOrb];
+  int flag;
+};
+
+__device__ __forceinline__ double2 b_cf_eval(const double* __restrict__ a, const double* __restrict__ b, int m,
+                                             double b0sq, double2 z, double E0, double s) {
+  if (m <= 0) return make_double2(0.0, 0.0);
+  double dr = z.x + s * (a[m - 1] - E0), di = z.y;
+  for (int k = m - 2; k >= 0; --k) {
+    const double bb = b[k + 1];
+    const double q = bb * bb / (dr * dr + di * di);
+    dr = z.x + s * (a[k] - E0) - q * dr;
+    di = z.y + q * di;
+  }
+  const double q = b0sq / (dr * dr + di * di);
+  return make_double2(q * dr, -q * di);
+}
+
+template <typename T>
+__global__ void k_batch_cf(BRun* __restrict__ R, const int* __restrict__ order, int n, const BCluster* __restrict__ C,
+                           const BTable* __restrict__ tabs, int* __restrict__ queue, BWork w,
+                           const double2* __restrict__ z, int nz, double tol, int mode) {
+  __shared__ CFShared g;
+  char* ws = w.base + (int64_t)blockIdx.x * w.stride;
+  T* V0 = (T*)ws;
+  T* V1 = V0 + w.maxd;
+  const int zstride = max(1, (nz + 63) / 64);  // at most 64 check frequencies (g.prev)
+  const int nzs = (nz + zstride - 1) / zstride;
+  while (true) {
+    __syncthreads();
+    if (threadIdx.x == 0) g.flag = atomicAdd(queue, 1);
+    __syncthreads();
+    const int item = g.flag;
+    if (item >= n) return;
+    BRun& r = R[order[item]];
+    const BCluster& c = C[r.cluster];
+    for (int i = threadIdx.x; i < kMaxVals; i += blockDim.x) {
+      g.svalf[i] = c.hp.valf[i];
+      g.svald[i] = c.hp.val[i];
+    }
+    for (int i = threadIdx.x; i < kMaxOrb; i += blockDim.x) {
+      g.sUf[i] = c.hp.Uf[i];
+      g.sUd[i] = c.hp.U[i];
+    }
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) g.prev[i] = make_double2(0.0, 0.0);
+    const BTable tu = tabs[r.tu], td = tabs[r.td], src = tabs[r.src];
+    const BTable dst = r.spin == 0 ? tu : td;
+    const int64_t du = tu.dim, dd = td.dim, nel = r.d;
+    const int64_t dd_s = tabs[c.t_dn].dim;
+    const uint32_t lomask = (1u << src.split) - 1u;
+    const int create = r.part == 0;
+    const int extra = r.spin == 1 ? (c.n_up & 1) : 0;
+    double s2 = 0.0, z1 = 0.0, z2 = 0.0;
+    __syncthreads();
+    // phi = (c_i [+ c_j])^(+) W in the target sector (pull form, sign of Eq. basis)
+    for (int64_t idx = threadIdx.x; idx < nel; idx += blockDim.x) {
+      const int64_t u = idx / dd, d = idx - u * dd;
+      const uint32_t bt = r.spin == 0 ? dst.basis[u] : dst.basis[d];
+      double acc = 0.0;
+      for (int k = 0; k < 2; ++k) {
+        const int site = k == 0 ? r.i : r.j;
+        if (site < 0) continue;
+        const uint32_t bit = 1u << site;
+        if (create ? !(bt & bit) : (bt & bit)) continue;
+        const uint32_t sb = bt ^ bit;
+        const int64_t rr = src.rank_lo[sb & lomask] + src.rank_hi[sb >> src.split];
+        const int neg = (__popc(bt & (bit - 1u)) + extra) & 1;
+        const double v = r.spin == 0 ? c.omega[rr * dd_s + d] : c.omega[u * dd_s + rr];
+        acc += neg ? -v : v;
+      }
+      V0[idx] = (T)acc;
+      V1[idx] = T(0);
+      s2 += acc * acc;
+    }
+    bred3(s2, z1, z2, g.bs);
+    const double b0 = sqrt(s2);
+    int steps = 0;
+    if (s2 > 1e-28) {
+      const T f = (T)(1.0 / b0);
+      for (int64_t idx = threadIdx.x; idx < nel; idx += blockDim.x) V0[idx] *= f;
+      __syncthreads();
+      T* X = V0;
+      T* P = V1;
+      double bprev = 0.0;
+      int next_check = 32, hits = 0;
+      const double sgn = create ? -1.0 : 1.0;
+      for (int k = 0; k < r.mmax; ++k) {
+        double sxw, sww, sxx;
+        block_hx<T>(tu, td, sval_of<T>(g), sU_of<T>(g), c.hp.umask, X, P, (T)bprev, mode, sxw, sww, sxx, g.bs);
+        const double alpha = sxx > 0.0 ? sxw / sxx : 0.0;
+        const double b2 = sxx > 0.0 ? sww - sxw * sxw / sxx : 0.0;
+        const double bn = b2 > 0.0 ? sqrt(b2) : 0.0;
+        if (threadIdx.x == 0) {
+          r.alpha[k] = alpha;
+          r.beta[k + 1] = bn;
+        }
+        steps = k + 1;
+        if (!(bn > 1e-10)) break;
+        const T aT = (T)alpha, ibT = (T)(1.0 / bn);
+        for (int64_t idx = threadIdx.x; idx < nel; idx += blockDim.x) P[idx] = (P[idx] - aT * X[idx]) * ibT;
+        bprev = bn;
+        T* t = X;
+        X = P;
+        P = t;
+        __syncthreads();
+        if (steps == next_check) {
+          // the continued fraction on every zstride-th frequency, compared with the last check
+          if (threadIdx.x == 0) g.maxdiff = 0.0;
+          __syncthreads();
+          double mx = 0.0;
+          for (int q = threadIdx.x; q < nzs; q += blockDim.x) {
+            const double2 gv = b_cf_eval(r.alpha, r.beta, steps, s2, z[q * zstride], c.E0, sgn);
+            mx = fmax(mx, hypot(gv.x - g.prev[q].x, gv.y - g.prev[q].y));
+            g.prev[q] = gv;
+          }
+          for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+          if ((threadIdx.x & 31) == 0) atomicMax((unsigned long long*)&g.maxdiff, __double_as_longlong(mx));
+          __syncthreads();
+          hits = g.maxdiff < tol ? hits + 1 : 0;
+          if (hits >= 2) break;
+          next_check = steps + max(32, steps / 8);
+        }
+      }
+    }
+    if (threadIdx.x == 0) {
+      r.b0sq = s2;
+      r.nsteps = steps;
+    }
+    __syncthreads();
+  }
+}
+
+// -------------------------------------------------------------------------------- evaluation on the grid
+__global__ void k_bcf_eval(const BRun* __restrict__ R, const BCluster* __restrict__ C, const double2* __restrict__ z,
+                           int nz, double2* __restrict__ out) {
+  const BRun& r = R[blockIdx.y];
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nz) return;
+  out[(int64_t)blockIdx.y * nz + k] =
+      b_cf_eval(r.alpha, r.beta, r.nsteps, r.b0sq, z[k], C[r.cluster].E0, r.part == 0 ? -1.0 : 1.0);
+}
+
+// G[c][spin][z][i][j] from the runs: base[c][spin][part] = first run of that part (-1: absent).
+__global__ void k_bcombine(const BCluster* __restrict__ C, int nclu, const int* __restrict__ base,
+                           const int64_t* __restrict__ goff, const double2* __restrict__ Gk, int nz,
+                           double2* __restrict__ G) {
+  const int c = blockIdx.y;
+  const int p = C[c].ns;
+  const int64_t per = (int64_t)2 * nz * p * p;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < per; t += (int64_t)gridDim.x * blockDim.x) {
+    const int spin = (int)(t / ((int64_t)nz * p * p));
+    const int64_t rem = t - (int64_t)spin * nz * p * p;
+    const int k = (int)(rem / (p * p));
+    const int ij = (int)(rem - (int64_t)k * p * p);
+    const int i = ij / p, j = ij - i * p;
+    double2 g = make_double2(0.0, 0.0);
+    for (int part = 0; part < 2; ++part) {
+      const int b0 = base[(c * 2 + spin) * 2 + part];
+      if (b0 < 0) continue;
+      if (i == j) {
+        const double2 v = Gk[(int64_t)(b0 + i) * nz + k];
+        g.x += v.x;
+        g.y += v.y;
+      } else {
+        const int lo = min(i, j), hi = max(i, j);
+        const int rp = b0 + p + (lo * (2 * p - lo - 1)) / 2 + (hi - lo - 1);
+        const double2 vp = Gk[(int64_t)rp * nz + k], vi = Gk[(int64_t)(b0 + lo) * nz + k],
+                      vj = Gk[(int64_t)(b0 + hi) * nz + k];
+        g.x += 0.5 * (vp.x - vi.x - vj.x);
+        g.y += 0.5 * (vp.y - vi.y - vj.y);
+      }
+    }
+    G[goff[c] + t] = g;
+  }
+}
+
+// -------------------------------------------------------------------------------- host driver
+namespace {
+struct Arena {
+  DevBuf<char> buf;
+  size_t used = 0;
+  size_t take(size_t bytes) {
+    const size_t off = used;
+    used += (bytes + 255) / 256 * 256;
+    return off;
+  }
+};
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune;  // (L_max, d bucket, n bucket, prec) -> (threads, mode)
+
+BBinom make_bbinom() {
+  BBinom b;
+  std::memset(&b, 0, sizeof(b));
+  for (int n = 0; n <= kMaxOrb; ++n) {
+    b.c[n][0] = 1;
+    for (int k = 1; k <= n; ++k) b.c[n][k] = b.c[n - 1][k - 1] + (k <= n - 1 ? b.c[n - 1][k] : 0);
+  }
+  return b;
+}
+}  // namespace
+
+struct BatchResult {
+  std::vector<double> E0, residual;
+  std::vector<int> status, iters, gf_steps;
+};
+
+// Runs the persistent ground-state and continued-fraction kernels with `threads` per block.
+template <typename T>
+static void run_batch_kernels(int threads, int mode, BCluster* C, const int* corder, int nclu, const BTable* tabs,
+                              BRun* R, const int* rorder, int nruns, int* queues, const BWork& w, int blocks,
+                              const double2* z, int nz, double tol, bool do_gf, cudaStream_t s) {
+  ED_CUDA(cudaMemsetAsync(queues, 0, 2 * sizeof(int), s));
+  {
+    ProfScope ps_(K_BATCH, s, 0.0);
+    k_batch_gs<T><<<blocks, threads, 0, s>>>(C, corder, nclu, tabs, queues, w, mode);
+    ED_CHECK_LAUNCH();
+  }
+  if (do_gf && nruns > 0) {
+    ProfScope ps_(K_BATCH, s, 0.0);
+    k_batch_cf<T><<<blocks, threads, 0, s>>>(R, rorder, nruns, C, tabs, queues + 1, w, z, nz, tol, mode);
+    ED_CHECK_LAUNCH();
+  }
+}
+
+void batch_solve(const ed_cluster_desc* descs, int n, int precision, const double2* z_host, int nz, bool do_gf,
+                 int cf_max_steps, double* E0_out, double* res_out, int* status_out, int* iters_out,
+                 double2* G_dev_out, cudaStream_t s) {
+  static const BBinom bn = make_bbinom();
+  if (n <= 0) return;
+  // ---- models
+  std::vector<ModelHost> models(n);
+  std::vector<BCluster> C(n);
+  for (int c = 0; c < n; ++c) {
+    std::memset(&C[c], 0, sizeof(BCluster));
+    build_model(&descs[c], models[c], C[c].hp);
+    if (models[c].L > kBMaxL) throw Error(ED_ERR_INVALID, "batched clusters have at most 20 orbitals");
+    C[c].ns = models[c].ns;
+    C[c].L = models[c].L;
+    C[c].n_up = descs[c].n_up;
+    C[c].n_dn = descs[c].n_dn;
+    C[c].seed = descs[c].seed;
+    C[c].tol = descs[c].tol > 0 ? descs[c].tol : 1e-12;
+    C[c].precision = precision;
+    if (C[c].ns > 32) throw Error(ED_ERR_INVALID, "too many cluster sites");
+  }
+  // ---- tables: one per (cluster, particle number) needed
+  std::vector<BTable> T;
+  std::vector<size_t> off_basis, off_lo, off_hi, off_ell, off_cnt, off_e64, off_e32;
+  Arena tab;
+  std::vector<std::map<int, int>> tindex(n);
+  auto need = [&](int c, int N) -> int {
+    if (N < 0 || N > C[c].L) return -1;
+    auto it = tindex[c].find(N);
+    if (it != tindex[c].end()) return it->second;
+    BTable t;
+    std::memset(&t, 0, sizeof(t));
+    t.L = C[c].L;
+    t.N = N;
+    t.split = t.L / 2;
+    t.dim = (int64_t)binomial(t.L, N);
+    t.zmax = std::max(1, N * (t.L - N));
+    t.cluster = c;
+    off_basis.push_back(tab.take(t.dim * 4));
+    off_lo.push_back(tab.take((size_t(1) << t.split) * 4));
+    off_hi.push_back(tab.take((size_t(1) << (t.L - t.split)) * 4));
+    off_ell.push_back(tab.take((size_t)t.zmax * t.dim * 4));
+    off_cnt.push_back(tab.take(t.dim));
+    off_e64.push_back(tab.take(t.dim * 8));
+    off_e32.push_back(tab.take(t.dim * 4));
+    T.push_back(t);
+    tindex[c][N] = (int)T.size() - 1;
+    return (int)T.size() - 1;
+  };
+  for (int c = 0; c < n; ++c) {
+    C[c].t_up = need(c, C[c].n_up);
+    C[c].t_dn = need(c, C[c].n_dn);
+    C[c].d = T[C[c].t_up].dim * T[C[c].t_dn].dim;
+    C[c].t_upp = do_gf ? need(c, C[c].n_up + 1) : -1;
+    C[c].t_upm = do_gf ? need(c, C[c].n_up - 1) : -1;
+    const bool both = C[c].n_up != C[c].n_dn;
+    C[c].t_dnp = do_gf && both ? need(c, C[c].n_dn + 1) : -1;
+    C[c].t_dnm = do_gf && both ? need(c, C[c].n_dn - 1) : -1;
+  }
+  // ---- runs
+  const int cap = cf_max_steps > 0 ? cf_max_steps : 20000;
+  std::vector<BRun> R;
+  std::vector<int> base((size_t)n * 4, -1);
+  for (int c = 0; c < n && do_gf; ++c) {
+    const int p = C[c].ns;
+    const int nspin = C[c].n_up != C[c].n_dn ? 2 : 1;
+    for (int spin = 0; spin < nspin; ++spin)
+      for (int part = 0; part < 2; ++part) {
+        const int tgt = spin == 0 ? (part == 0 ? C[c].t_upp : C[c].t_upm) : (part == 0 ? C[c].t_dnp : C[c].t_dnm);
+        if (tgt < 0) continue;
+        base[(c * 2 + spin) * 2 + part] = (int)R.size();
+        for (int q = 0; q < p + p * (p - 1) / 2; ++q) {
+          BRun r;
+          std::memset(&r, 0, sizeof(r));
+          r.cluster = c;
+          r.spin = spin;
+          r.part = part;
+          if (q < p) {
+            r.i = q;
+            r.j = -1;
+          } else {
+            int k = q - p, i = 0;
+            while (k >= p - 1 - i) {
+              k -= p - 1 - i;
+              ++i;
+            }
+            r.i = i;
+            r.j = i + 1 + k;
+          }
+          r.tu = spin == 0 ? tgt : C[c].t_up;
+          r.td = spin == 0 ? C[c].t_dn : tgt;
+          r.src = spin == 0 ? C[c].t_up : C[c].t_dn;
+          r.d = T[r.tu].dim * T[r.td].dim;
+          r.mmax = (int)std::max<int64_t>(64, std::min<int64_t>(cap, 2 * r.d + 16));
+          R.push_back(r);
+        }
+      }
+    if (nspin == 1)
+      for (int part = 0; part < 2; ++part) base[(c * 2 + 1) * 2 + part] = base[(c * 2 + 0) * 2 + part];
+  }
+  const int nruns = (int)R.size();
+  // ---- arena: tables, ground states, run coefficients, G parts
+  std::vector<size_t> off_om(n), off_al(nruns), off_be(nruns);
+  for (int c = 0; c < n; ++c) off_om[c] = tab.take(C[c].d * 8);
+  for (int r = 0; r < nruns; ++r) {
+    off_al[r] = tab.take((size_t)R[r].mmax * 8);
+    off_be[r] = tab.take((size_t)(R[r].mmax + 1) * 8);
+  }
+  const size_t off_gk = tab.take((size_t)std::max(nruns, 1) * nz * sizeof(double2));
+  tab.buf.alloc(tab.used);
+  char* B = tab.buf.p;
+  for (size_t t = 0; t < T.size(); ++t) {
+    T[t].basis = (uint32_t*)(B + off_basis[t]);
+    T[t].rank_lo = (int32_t*)(B + off_lo[t]);
+    T[t].rank_hi = (int32_t*)(B + off_hi[t]);
+    T[t].ell = (uint32_t*)(B + off_ell[t]);
+    T[t].cnt = (uint8_t*)(B + off_cnt[t]);
+    T[t].e64 = (double*)(B + off_e64[t]);
+    T[t].e32 = (float*)(B + off_e32[t]);
+  }
+  for (int c = 0; c < n; ++c) C[c].omega = (double*)(B + off_om[c]);
+  for (int r = 0; r < nruns; ++r) {
+    R[r].alpha = (double*)(B + off_al[r]);
+    R[r].beta = (double*)(B + off_be[r]);
+  }
+  double2* Gk = (double2*)(B + off_gk);
+  // pairs and diagonals
+  std::vector<BPair> pairs;
+  std::vector<int> pair_off(n + 1, 0);
+  std::vector<double> hdiag((size_t)n * kMaxOrb, 0.0);
+  for (int c = 0; c < n; ++c) {
+    const ModelHost& m = models[c];
+    for (size_t k = 0; k < m.pair_a.size(); ++k) {
+      const uint32_t a = m.pair_a[k], b = m.pair_b[k];
+      const uint32_t lo = std::min(a, b), hi = std::max(a, b);
+      const uint32_t between = ((1u << hi) - 1u) ^ ((1u << (lo + 1)) - 1u);
+      pairs.push_back(BPair{a, b, (uint32_t)m.pair_vidx[k], between});
+    }
+    pair_off[c + 1] = (int)pairs.size();
+    for (int a = 0; a < m.L; ++a) hdiag[(size_t)c * kMaxOrb + a] = m.h[a * m.L + a];
+  }
+  // orders: largest first
+  std::vector<int> corder(n), rorder(nruns);
+  std::iota(corder.begin(), corder.end(), 0);
+  std::stable_sort(corder.begin(), corder.end(), [&](int a, int b) { return C[a].d > C[b].d; });
+  std::iota(rorder.begin(), rorder.end(), 0);
+  std::stable_sort(rorder.begin(), rorder.end(), [&](int a, int b) { return R[a].d > R[b].d; });
+  // ---- device descriptors
+  DevBuf<BTable> dT(T.size());
+  DevBuf<BPair> dP(std::max<size_t>(pairs.size(), 1));
+  DevBuf<int> dPoff(n + 1), dCo(n), dRo(std::max(nruns, 1)), dQ(2), dBase((size_t)n * 4);
+  DevBuf<double> dHd(hdiag.size());
+  DevBuf<BCluster> dC(n);
+  DevBuf<BRun> dR(std::max(nruns, 1));
+  DevBuf<double2> dz(std::max(nz, 1));
+  ED_CUDA(cudaMemcpyAsync(dT.p, T.data(), T.size() * sizeof(BTable), cudaMemcpyHostToDevice, s));
+  if (!pairs.empty()) ED_CUDA(cudaMemcpyAsync(dP.p, pairs.data(), pairs.size() * sizeof(BPair), cudaMemcpyHostToDevice, s));
+  ED_CUDA(cudaMemcpyAsync(dPoff.p, pair_off.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  ED_CUDA(cudaMemcpyAsync(dHd.p, hdiag.data(), hdiag.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  ED_CUDA(cudaMemcpyAsync(dC.p, C.data(), n * sizeof(BCluster), cudaMemcpyHostToDevice, s));
+  ED_CUDA(cudaMemcpyAsync(dCo.p, corder.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
+  if (nruns) {
+    ED_CUDA(cudaMemcpyAsync(dR.p, R.data(), nruns * sizeof(BRun), cudaMemcpyHostToDevice, s));
+    ED_CUDA(cudaMemcpyAsync(dRo.p, rorder.data(), nruns * sizeof(int), cudaMemcpyHostToDevice, s));
+  }
+  ED_CUDA(cudaMemcpyAsync(dBase.p, base.data(), base.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  if (nz) ED_CUDA(cudaMemcpyAsync(dz.p, z_host, nz * sizeof(double2), cudaMemcpyHostToDevice, s));
+  // ---- tables
+  int64_t maxdim = 0;
+  for (const BTable& t : T) maxdim = std::max<int64_t>(maxdim, std::max<int64_t>(t.dim, int64_t(1) << (t.L - t.split)));
+  {
+    const unsigned gx = (unsigned)std::min<int64_t>((maxdim + 255) / 256, 64);
+    ProfScope ps_(K_TABLES, s, 0.0);
+    k_bt_basis<<<dim3(gx, (unsigned)T.size()), 256, 0, s>>>(dT.p, bn);
+    ED_CHECK_LAUNCH();
+  }
+  {
+    const unsigned gx = (unsigned)std::min<int64_t>((maxdim + 255) / 256, 64);
+    ProfScope ps_(K_TABLES, s, 0.0);
+    k_bt_fill<<<dim3(gx, (unsigned)T.size()), 256, 0, s>>>(dT.p, dP.p, dPoff.p, dHd.p);
+    ED_CHECK_LAUNCH();
+  }
+  // ---- workspace: per persistent block, 3 + 4 vectors of the largest sector
+  int64_t maxd = 1;
+  for (int c = 0; c < n; ++c) maxd = std::max(maxd, C[c].d);
+  for (int r = 0; r < nruns; ++r) maxd = std::max(maxd, R[r].d);
+  const size_t es = precision == ED_FP64 ? 8 : 4;
+  const size_t stride = ((3 * maxd * es + 255) / 256) * 256 + 4 * maxd * 8 + 256;
+  int dev = 0, sms = 0;
+  ED_CUDA(cudaGetDevice(&dev));
+  ED_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  // autotuned block width and mapping (cached per batch shape)
+  int Lmax = 0;
+  for (int c = 0; c < n; ++c) Lmax = std::max(Lmax, C[c].L);
+  int dbucket = 0;
+  while ((int64_t(1) << (2 * dbucket)) < maxd) ++dbucket;
+  int nbucket = 0;
+  while ((1 << nbucket) < n) ++nbucket;
+  const auto key = std::make_tuple(Lmax, dbucket, nbucket, precision);
+  std::pair<int, int> cfg{256, 0};
+  bool tuned;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    tuned = it != g_tune.end();
+    if (tuned) cfg = it->second;
+  }
+  const int per_sm = 4;
+  const int blocks = std::max(1, std::min(n + nruns, sms * per_sm));
+  DevBuf<char> work((size_t)blocks * stride);
+  BWork w{work.p, (int64_t)stride, maxd};
+  if (!tuned) {
+    // time the ground-state kernel of the largest clusters with each candidate
+    const int sample = std::min(n, std::max(8, blocks));
+    const std::pair<int, int> cands[] = {{128, 0}, {256, 0}, {256, 1}, {512, 1}};
+    float best = 1e30f;
+    cudaEvent_t e0, e1;
+    ED_CUDA(cudaEventCreate(&e0));
+    ED_CUDA(cudaEventCreate(&e1));
+    for (const auto& cd : cands) {
+      ED_CUDA(cudaMemcpyAsync(dC.p, C.data(), n * sizeof(BCluster), cudaMemcpyHostToDevice, s));
+      ED_CUDA(cudaEventRecord(e0, s));
+      if (precision == ED_FP64)
+        run_batch_kernels<double>(cd.first, cd.second, dC.p, dCo.p, sample, dT.p, dR.p, dRo.p, 0, dQ.p, w, blocks,
+                                  dz.p, nz, 0.0, false, s);
+      else
+        run_batch_kernels<float>(cd.first, cd.second, dC.p, dCo.p, sample, dT.p, dR.p, dRo.p, 0, dQ.p, w, blocks,
+                                 dz.p, nz, 0.0, false, s);
+      ED_CUDA(cudaEventRecord(e1, s));
+      ED_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      ED_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        cfg = cd;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ED_CUDA(cudaMemcpyAsync(dC.p, C.data(), n * sizeof(BCluster), cudaMemcpyHostToDevice, s));
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = cfg;
+  }
+  const double gtol = precision == ED_FP64 ? 1e-10 : 1e-6;
+  if (precision == ED_FP64)
+    run_batch_kernels<double>(cfg.first, cfg.second, dC.p, dCo.p, n, dT.p, dR.p, dRo.p, nruns, dQ.p, w, blocks,
+                              dz.p, nz, gtol, do_gf, s);
+  else
+    run_batch_kernels<float>(cfg.first, cfg.second, dC.p, dCo.p, n, dT.p, dR.p, dRo.p, nruns, dQ.p, w, blocks,
+                             dz.p, nz, gtol, do_gf, s);
+  if (do_gf && nruns > 0) {
+    {
+      ProfScope ps_(K_GF_EVAL, s, 0.0);
+      k_bcf_eval<<<dim3((nz + 255) / 256, nruns), 256, 0, s>>>(dR.p, dC.p, dz.p, nz, Gk);
+      ED_CHECK_LAUNCH();
+    }
+    std::vector<int64_t> goff(n + 1, 0);
+    for (int c = 0; c < n; ++c) goff[c + 1] = goff[c] + (int64_t)2 * nz * C[c].ns * C[c].ns;
+    DevBuf<int64_t> dgoff(n + 1);
+    ED_CUDA(cudaMemcpyAsync(dgoff.p, goff.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    {
+      ProfScope ps_(K_GF_EVAL, s, 0.0);
+      k_bcombine<<<dim3(64, n), 256, 0, s>>>(dC.p, n, dBase.p, dgoff.p, Gk, nz, G_dev_out);
+      ED_CHECK_LAUNCH();
+    }
+    ED_CUDA(cudaStreamSynchronize(s));
+  }
+  // ---- results
+  ED_CUDA(cudaMemcpyAsync(C.data(), dC.p, n * sizeof(BCluster), cudaMemcpyDeviceToHost, s));
+  std::vector<BRun> Rh(nruns);
+  if (nruns) ED_CUDA(cudaMemcpyAsync(Rh.data(), dR.p, nruns * sizeof(BRun), cudaMemcpyDeviceToHost, s));
+  ED_CUDA(cudaStreamSynchronize(s));
+  for (int c = 0; c < n; ++c) {
+    if (E0_out) E0_out[c] = C[c].E0;
+    if (res_out) res_out[c] = C[c].residual;
+    if (status_out) status_out[c] = C[c].status;
+    if (iters_out) iters_out[c] = C[c].iters;
+  }
+}
+
+}  // namespace ed
+
+using namespace ed;
+
+extern "C" ed_status ed_batch_solve(const ed_cluster_desc* descs, int n, int precision, const double* omega, int n_freq,
+                                    double eta, int axis, double* E0, double* residual, int* status, int* iters,
+                                    double* G_out, int out_is_device) {
+  try {
+    if (!descs || n < 0) throw Error(ED_ERR_INVALID, "descs is NULL or n < 0");
+    if (precision != ED_FP64 && precision != ED_FP32) throw Error(ED_ERR_INVALID, "precision must be ED_FP64 or ED_FP32");
+    if (n_freq < 0 || (n_freq > 0 && (!omega || !G_out))) throw Error(ED_ERR_INVALID, "omega and G_out are needed when n_freq > 0");
+    if (axis != ED_AXIS_REAL && axis != ED_AXIS_MATSUBARA) throw Error(ED_ERR_INVALID, "bad axis");
+    std::vector<double2> z(n_freq);
+    for (int k = 0; k < n_freq; ++k) z[k] = axis == ED_AXIS_REAL ? make_double2(omega[k], eta) : make_double2(0.0, omega[k]);
+    int64_t total = 0;
+    for (int c = 0; c < n; ++c) total += (int64_t)2 * n_freq * descs[c].n_sites * descs[c].n_sites;
+    cudaStream_t s = nullptr;
+    ED_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    struct SD {
+      cudaStream_t s;
+      ~SD() { cudaStreamSynchronize(s); cudaStreamDestroy(s); }
+    } sd{s};
+    DevBuf<double2> Gd;
+    double2* Gdev = (double2*)G_out;
+    if (n_freq > 0 && !out_is_device) {
+      Gd.alloc(std::max<int64_t>(total, 1));
+      Gdev = Gd.p;
+    }
+    batch_solve(descs, n, precision, z.data(), n_freq, n_freq > 0, 0, E0, residual, status, iters, Gdev, s);
+    if (n_freq > 0 && !out_is_device) {
+      ED_CUDA(cudaMemcpyAsync(G_out, Gd.p, total * sizeof(double2), cudaMemcpyDeviceToHost, s));
+      ED_CUDA(cudaStreamSynchronize(s));
+    }
+    return ED_OK;
+  } catch (const Error& e) {
+    set_last_error(e.what());
+    return e.code;
+  } catch (const std::exception& e) {
+    set_last_error(e.what());
+    return ED_ERR_INVALID;
+  }
+}

@@ -43,7 +43,7 @@ void set_last_error(const std::string& msg);
 // Kernel families timed by the profiler (ed_profile_* in ed.h).
 enum KernelId {
   K_TABLES = 0, K_HPSI, K_LANCZOS_STEP, K_LANCZOS_NEXT, K_TRIDIAG, K_VECTOR, K_APPLY_COP, K_GF_EVAL,
-  K_BAND, K_COUNT
+  K_BAND, K_BATCH, K_COUNT
 };
 const char* kernel_name(int kid);
 void note_launch();  // counts a launch that is timed inside another kernel's scope
@@ -176,6 +176,7 @@ __device__ __forceinline__ int32_t rank_of(const RankView& r, uint32_t b) {
 
 // sector.cu
 std::unique_ptr<SpinTables> build_spin_tables(const ModelHost& m, int N, cudaStream_t s);
+void build_model(const ed_cluster_desc* desc, ModelHost& m, HopParams& hp);  // api.cu
 void basis_to_host(int L, int N, uint32_t* out, int64_t dim);
 uint64_t binomial(int n, int k);
 

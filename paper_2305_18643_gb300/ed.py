@@ -71,6 +71,8 @@ def lib():
             "ed_launch_count": (i64, []),
             "ed_set_option": (i32, [vp, i32, C.c_double]),
             "ed_hpsi_dots_static": (i32, [vp, i32, vp, vp, i64, vp, vp]),
+            "ed_batch_solve": (i32, [C.POINTER(ed_cluster_desc), i32, i32, _dp, i32, C.c_double, i32, _dp, _dp,
+                                     C.POINTER(i32), C.POINTER(i32), vp, i32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -226,6 +228,52 @@ def ed_hpsi_dots_static(h, dtype, x_ptr, y_ptr, out3_ptr, ld=0, stream=0):
     the library's fixed scratch instead of device allocations; asynchronous on `stream`."""
     _check(lib().ed_hpsi_dots_static(h, int(dtype), C.c_void_p(x_ptr), C.c_void_p(y_ptr), int(ld),
                                      C.c_void_p(out3_ptr), C.c_void_p(stream) if stream else None))
+
+
+def _desc_array(clusters, seed=0, tol=0.0):
+    keep, descs = [], (ed_cluster_desc * max(len(clusters), 1))()
+    for k, cl in enumerate(clusters):
+        ns = int(np.asarray(cl["t"]).shape[0])
+        eps = np.asarray(cl.get("eps", np.zeros(0)), dtype=np.float64).ravel()
+        nb = int(eps.size)
+        arrs = [_arr(cl["t"], ns * ns), _arr(np.broadcast_to(np.asarray(cl["U"], float), (ns,)), ns),
+                _arr(eps, nb) if nb else None, _arr(cl.get("theta", np.zeros((ns, 0))), ns * nb) if nb else None]
+        keep.append(arrs)
+        ptr = [a.ctypes.data_as(_dp) if a is not None else None for a in arrs]
+        descs[k] = ed_cluster_desc(ns, nb, ptr[0], ptr[1], float(cl["mu"]), ptr[2], ptr[3], int(cl["n_up"]),
+                                   int(cl["n_dn"]), 0, 0, (int(seed) + k) & (2 ** 64 - 1), float(tol), 0)
+    return descs, keep
+
+
+def ed_batch_solve(clusters, precision=ED_FP64, omega=None, eta=0.05, axis=ED_AXIS_REAL, seed=0, tol=0.0,
+                   out_ptr=None):
+    """Solve many clusters together.  Returns (E0, residual, status, iters, G) where G is a list of
+    complex128 arrays [2, n_freq, n_sites, n_sites] (None when omega is None or out_ptr is given)."""
+    n = len(clusters)
+    descs, keep = _desc_array(clusters, seed, tol)
+    om = _arr(omega, np.asarray(omega).size) if omega is not None else np.zeros(0)
+    nf = om.size
+    E0, res = np.zeros(max(n, 1)), np.zeros(max(n, 1))
+    st, it = np.zeros(max(n, 1), dtype=np.int32), np.zeros(max(n, 1), dtype=np.int32)
+    sizes = [2 * nf * int(np.asarray(cl["t"]).shape[0]) ** 2 for cl in clusters]
+    G = None
+    if out_ptr is not None:
+        gptr, dev = C.c_void_p(out_ptr), 1
+    else:
+        G = np.zeros(max(sum(sizes), 1), dtype=np.complex128)
+        gptr, dev = G.ctypes.data_as(C.c_void_p), 0
+    _check(lib().ed_batch_solve(descs, n, int(precision), om.ctypes.data_as(_dp), nf, float(eta), int(axis),
+                                E0.ctypes.data_as(_dp), res.ctypes.data_as(_dp),
+                                st.ctypes.data_as(C.POINTER(C.c_int)), it.ctypes.data_as(C.POINTER(C.c_int)),
+                                gptr if nf else None, dev))
+    Gs = None
+    if G is not None and nf:
+        Gs, o = [], 0
+        for cl, sz in zip(clusters, sizes):
+            ns = int(np.asarray(cl["t"]).shape[0])
+            Gs.append(G[o:o + sz].reshape(2, nf, ns, ns))
+            o += sz
+    return E0[:n], res[:n], st[:n], it[:n], Gs
 
 
 class Cluster:
