@@ -125,13 +125,16 @@ ed_status ed_green_stats(const ed_cluster* c, int64_t* total_steps, int* max_ste
 
 /* Batched form: n independent clusters solved together.  For each cluster: the Lanczos ground
  * state (as ed_ground_state, at most 600 levels per pass) and, when n_freq > 0, the
- * continued-fraction Green function of Sec. 4.3 (at most min(20000, 2 d + 16) levels per run) for spin up and
+ * continued-fraction Green function of Sec. 4.3 for spin up and
  * spin down (spin down equals spin up when n_up == n_dn), on z = omega + i eta (ED_AXIS_REAL)
- * or i omega (ED_AXIS_MATSUBARA).  All clusters share `precision` (ED_FP64 or ED_FP32); each
+ * or i omega (ED_AXIS_MATSUBARA); each continued fraction stops when it converges on the grid (as
+ * in ed_green) or at the preset maximum of min(cf_max_levels, 2 d + 16) levels (cf_max_levels <= 0
+ * selects 400; Sec. 4.3 stops at a preset maximum).  All clusters share `precision` (ED_FP64 or ED_FP32); each
  * cluster's seed and tol are taken from its description, its precision and gf_method are
  * ignored.  At most 20 orbitals per cluster.
- *  - E0, residual, status, iters: n values each (host), any may be NULL; status per cluster is
- *    ED_OK, ED_WARN_DEGENERATE or ED_WARN_NOT_CONVERGED.
+ *  - E0, residual, status, iters (ground-state levels), gf_steps (continued-fraction levels over
+ *    all runs): n values each (host), any may be NULL; status per cluster is ED_OK,
+ *    ED_WARN_DEGENERATE or ED_WARN_NOT_CONVERGED.
  *  - G_out: complex128 (2 doubles each), clusters one after the other, cluster c holding
  *    [2 spins][n_freq][n_sites_c][n_sites_c]; host or device memory as out_is_device says.
  * Tables, ground states and continued fractions of all clusters are built by a few launches:
@@ -139,8 +142,8 @@ ed_status ed_green_stats(const ed_cluster* c, int64_t* total_steps, int* max_ste
  * from a queue, largest first.  The block width and the mapping of the block-level H.psi are
  * picked by timing candidates on the first call for a batch shape (then cached). */
 ed_status ed_batch_solve(const ed_cluster_desc* descs, int n, int precision, const double* omega, int n_freq,
-                         double eta, int axis, double* E0, double* residual, int* status, int* iters,
-                         double* G_out, int out_is_device);
+                         double eta, int axis, int cf_max_levels, double* E0, double* residual, int* status, int* iters,
+                         int64_t* gf_steps, double* G_out, int out_is_device);
 
 /* ---- lower-level calls (parity tests and benchmarks) ------------------------------------- */
 
@@ -199,7 +202,8 @@ enum {
   ED_K_APPLY_COP = 6,     /* c+ / c applied to the ground state */
   ED_K_GF_EVAL = 7,       /* Green-function evaluation and assembly on the grid */
   ED_K_BAND = 8,          /* band-Lanczos orthogonalization */
-  ED_K_COUNT = 9
+  ED_K_BATCH = 9,         /* persistent kernels of the batched form */
+  ED_K_COUNT = 10
 };
 
 /* Turns per-family timing on (1) or off (0) and clears the totals.  While on, each launch of a

@@ -612,46 +612,49 @@ __global__ void k_batch_cf(BRun* __restrict__ R, const int* __restrict__ order, 
 }
 
 // -------------------------------------------------------------------------------- evaluation on the grid
-__global__ void k_bcf_eval(const BRun* __restrict__ R, const BCluster* __restrict__ C, const double2* __restrict__ z,
-                           int nz, double2* __restrict__ out) {
-  const BRun& r = R[blockIdx.y];
+__global__ void k_bcf_eval(const BRun* __restrict__ R, int nruns, const BCluster* __restrict__ C,
+                           const double2* __restrict__ z, int nz, double2* __restrict__ out) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nz) return;
-  out[(int64_t)blockIdx.y * nz + k] =
-      b_cf_eval(r.alpha, r.beta, r.nsteps, r.b0sq, z[k], C[r.cluster].E0, r.part == 0 ? -1.0 : 1.0);
+  for (int q = blockIdx.y; q < nruns; q += gridDim.y) {  // grid.y is capped at 65535
+    const BRun& r = R[q];
+    out[(int64_t)q * nz + k] =
+        b_cf_eval(r.alpha, r.beta, r.nsteps, r.b0sq, z[k], C[r.cluster].E0, r.part == 0 ? -1.0 : 1.0);
+  }
 }
 
 // G[c][spin][z][i][j] from the runs: base[c][spin][part] = first run of that part (-1: absent).
 __global__ void k_bcombine(const BCluster* __restrict__ C, int nclu, const int* __restrict__ base,
                            const int64_t* __restrict__ goff, const double2* __restrict__ Gk, int nz,
                            double2* __restrict__ G) {
-  const int c = blockIdx.y;
-  const int p = C[c].ns;
-  const int64_t per = (int64_t)2 * nz * p * p;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < per; t += (int64_t)gridDim.x * blockDim.x) {
-    const int spin = (int)(t / ((int64_t)nz * p * p));
-    const int64_t rem = t - (int64_t)spin * nz * p * p;
-    const int k = (int)(rem / (p * p));
-    const int ij = (int)(rem - (int64_t)k * p * p);
-    const int i = ij / p, j = ij - i * p;
-    double2 g = make_double2(0.0, 0.0);
-    for (int part = 0; part < 2; ++part) {
-      const int b0 = base[(c * 2 + spin) * 2 + part];
-      if (b0 < 0) continue;
-      if (i == j) {
-        const double2 v = Gk[(int64_t)(b0 + i) * nz + k];
-        g.x += v.x;
-        g.y += v.y;
-      } else {
-        const int lo = min(i, j), hi = max(i, j);
-        const int rp = b0 + p + (lo * (2 * p - lo - 1)) / 2 + (hi - lo - 1);
-        const double2 vp = Gk[(int64_t)rp * nz + k], vi = Gk[(int64_t)(b0 + lo) * nz + k],
-                      vj = Gk[(int64_t)(b0 + hi) * nz + k];
-        g.x += 0.5 * (vp.x - vi.x - vj.x);
-        g.y += 0.5 * (vp.y - vi.y - vj.y);
+  for (int c = blockIdx.y; c < nclu; c += gridDim.y) {  // grid.y is capped at 65535
+    const int p = C[c].ns;
+    const int64_t per = (int64_t)2 * nz * p * p;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < per; t += (int64_t)gridDim.x * blockDim.x) {
+      const int spin = (int)(t / ((int64_t)nz * p * p));
+      const int64_t rem = t - (int64_t)spin * nz * p * p;
+      const int k = (int)(rem / (p * p));
+      const int ij = (int)(rem - (int64_t)k * p * p);
+      const int i = ij / p, j = ij - i * p;
+      double2 g = make_double2(0.0, 0.0);
+      for (int part = 0; part < 2; ++part) {
+        const int b0 = base[(c * 2 + spin) * 2 + part];
+        if (b0 < 0) continue;
+        if (i == j) {
+          const double2 v = Gk[(int64_t)(b0 + i) * nz + k];
+          g.x += v.x;
+          g.y += v.y;
+        } else {
+          const int lo = min(i, j), hi = max(i, j);
+          const int rp = b0 + p + (lo * (2 * p - lo - 1)) / 2 + (hi - lo - 1);
+          const double2 vp = Gk[(int64_t)rp * nz + k], vi = Gk[(int64_t)(b0 + lo) * nz + k],
+                        vj = Gk[(int64_t)(b0 + hi) * nz + k];
+          g.x += 0.5 * (vp.x - vi.x - vj.x);
+          g.y += 0.5 * (vp.y - vi.y - vj.y);
+        }
       }
+      G[goff[c] + t] = g;
     }
-    G[goff[c] + t] = g;
   }
 }
 
@@ -705,7 +708,7 @@ static void run_batch_kernels(int threads, int mode, BCluster* C, const int* cor
 
 void batch_solve(const ed_cluster_desc* descs, int n, int precision, const double2* z_host, int nz, bool do_gf,
                  int cf_max_steps, double* E0_out, double* res_out, int* status_out, int* iters_out,
-                 double2* G_dev_out, cudaStream_t s) {
+                 int64_t* gf_steps_out, double2* G_dev_out, cudaStream_t s) {
   static const BBinom bn = make_bbinom();
   if (n <= 0) return;
   // ---- models
@@ -956,7 +959,7 @@ void batch_solve(const ed_cluster_desc* descs, int n, int precision, const doubl
   if (do_gf && nruns > 0) {
     {
       ProfScope ps_(K_GF_EVAL, s, 0.0);
-      k_bcf_eval<<<dim3((nz + 255) / 256, nruns), 256, 0, s>>>(dR.p, dC.p, dz.p, nz, Gk);
+      k_bcf_eval<<<dim3((nz + 255) / 256, std::min(nruns, 32768)), 256, 0, s>>>(dR.p, nruns, dC.p, dz.p, nz, Gk);
       ED_CHECK_LAUNCH();
     }
     std::vector<int64_t> goff(n + 1, 0);
@@ -965,7 +968,7 @@ void batch_solve(const ed_cluster_desc* descs, int n, int precision, const doubl
     ED_CUDA(cudaMemcpyAsync(dgoff.p, goff.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     {
       ProfScope ps_(K_GF_EVAL, s, 0.0);
-      k_bcombine<<<dim3(64, n), 256, 0, s>>>(dC.p, n, dBase.p, dgoff.p, Gk, nz, G_dev_out);
+      k_bcombine<<<dim3(64, std::min(n, 32768)), 256, 0, s>>>(dC.p, n, dBase.p, dgoff.p, Gk, nz, G_dev_out);
       ED_CHECK_LAUNCH();
     }
     ED_CUDA(cudaStreamSynchronize(s));
@@ -975,6 +978,10 @@ void batch_solve(const ed_cluster_desc* descs, int n, int precision, const doubl
   std::vector<BRun> Rh(nruns);
   if (nruns) ED_CUDA(cudaMemcpyAsync(Rh.data(), dR.p, nruns * sizeof(BRun), cudaMemcpyDeviceToHost, s));
   ED_CUDA(cudaStreamSynchronize(s));
+  if (gf_steps_out) {
+    for (int c = 0; c < n; ++c) gf_steps_out[c] = 0;
+    for (int r = 0; r < nruns; ++r) gf_steps_out[Rh[r].cluster] += Rh[r].nsteps;
+  }
   for (int c = 0; c < n; ++c) {
     if (E0_out) E0_out[c] = C[c].E0;
     if (res_out) res_out[c] = C[c].residual;
@@ -988,8 +995,9 @@ void batch_solve(const ed_cluster_desc* descs, int n, int precision, const doubl
 using namespace ed;
 
 extern "C" ed_status ed_batch_solve(const ed_cluster_desc* descs, int n, int precision, const double* omega, int n_freq,
-                                    double eta, int axis, double* E0, double* residual, int* status, int* iters,
-                                    double* G_out, int out_is_device) {
+                                    double eta, int axis, int cf_max_levels, double* E0, double* residual, int* status,
+                                    int* iters,
+                                    int64_t* gf_steps, double* G_out, int out_is_device) {
   try {
     if (!descs || n < 0) throw Error(ED_ERR_INVALID, "descs is NULL or n < 0");
     if (precision != ED_FP64 && precision != ED_FP32) throw Error(ED_ERR_INVALID, "precision must be ED_FP64 or ED_FP32");
@@ -1011,7 +1019,8 @@ extern "C" ed_status ed_batch_solve(const ed_cluster_desc* descs, int n, int pre
       Gd.alloc(std::max<int64_t>(total, 1));
       Gdev = Gd.p;
     }
-    batch_solve(descs, n, precision, z.data(), n_freq, n_freq > 0, 0, E0, residual, status, iters, Gdev, s);
+    batch_solve(descs, n, precision, z.data(), n_freq, n_freq > 0, cf_max_levels > 0 ? cf_max_levels : 400, E0,
+                residual, status, iters, gf_steps, Gdev, s);
     if (n_freq > 0 && !out_is_device) {
       ED_CUDA(cudaMemcpyAsync(G_out, Gd.p, total * sizeof(double2), cudaMemcpyDeviceToHost, s));
       ED_CUDA(cudaStreamSynchronize(s));

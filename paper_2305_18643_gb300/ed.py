@@ -71,8 +71,8 @@ def lib():
             "ed_launch_count": (i64, []),
             "ed_set_option": (i32, [vp, i32, C.c_double]),
             "ed_hpsi_dots_static": (i32, [vp, i32, vp, vp, i64, vp, vp]),
-            "ed_batch_solve": (i32, [C.POINTER(ed_cluster_desc), i32, i32, _dp, i32, C.c_double, i32, _dp, _dp,
-                                     C.POINTER(i32), C.POINTER(i32), vp, i32]),
+            "ed_batch_solve": (i32, [C.POINTER(ed_cluster_desc), i32, i32, _dp, i32, C.c_double, i32, i32, _dp, _dp,
+                                     C.POINTER(i32), C.POINTER(i32), C.POINTER(i64), vp, i32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -201,7 +201,7 @@ def ed_hpsi(h, n_up, n_dn, dtype, x_ptr, y_ptr, ld=0, stream=0):
 
 
 ED_K_TABLES, ED_K_HPSI, ED_K_LANCZOS_STEP, ED_K_LANCZOS_NEXT, ED_K_TRIDIAG = 0, 1, 2, 3, 4
-ED_K_VECTOR, ED_K_APPLY_COP, ED_K_GF_EVAL, ED_K_BAND, ED_K_COUNT = 5, 6, 7, 8, 9
+ED_K_VECTOR, ED_K_APPLY_COP, ED_K_GF_EVAL, ED_K_BAND, ED_K_BATCH, ED_K_COUNT = 5, 6, 7, 8, 9, 10
 
 
 def ed_profile_enable(on):
@@ -246,15 +246,18 @@ def _desc_array(clusters, seed=0, tol=0.0):
 
 
 def ed_batch_solve(clusters, precision=ED_FP64, omega=None, eta=0.05, axis=ED_AXIS_REAL, seed=0, tol=0.0,
-                   out_ptr=None):
+                   out_ptr=None, cf_max_levels=0):
     """Solve many clusters together.  Returns (E0, residual, status, iters, G) where G is a list of
-    complex128 arrays [2, n_freq, n_sites, n_sites] (None when omega is None or out_ptr is given)."""
+    complex128 arrays [2, n_freq, n_sites, n_sites] (None when omega is None or out_ptr is given).
+    cf_max_levels caps every continued fraction (<= 0: the library's preset, 400 levels); the
+    continued-fraction levels of each cluster are left in ed_batch_solve.gf_steps."""
     n = len(clusters)
     descs, keep = _desc_array(clusters, seed, tol)
     om = _arr(omega, np.asarray(omega).size) if omega is not None else np.zeros(0)
     nf = om.size
     E0, res = np.zeros(max(n, 1)), np.zeros(max(n, 1))
     st, it = np.zeros(max(n, 1), dtype=np.int32), np.zeros(max(n, 1), dtype=np.int32)
+    gs = np.zeros(max(n, 1), dtype=np.int64)
     sizes = [2 * nf * int(np.asarray(cl["t"]).shape[0]) ** 2 for cl in clusters]
     G = None
     if out_ptr is not None:
@@ -263,9 +266,9 @@ def ed_batch_solve(clusters, precision=ED_FP64, omega=None, eta=0.05, axis=ED_AX
         G = np.zeros(max(sum(sizes), 1), dtype=np.complex128)
         gptr, dev = G.ctypes.data_as(C.c_void_p), 0
     _check(lib().ed_batch_solve(descs, n, int(precision), om.ctypes.data_as(_dp), nf, float(eta), int(axis),
-                                E0.ctypes.data_as(_dp), res.ctypes.data_as(_dp),
+                                int(cf_max_levels), E0.ctypes.data_as(_dp), res.ctypes.data_as(_dp),
                                 st.ctypes.data_as(C.POINTER(C.c_int)), it.ctypes.data_as(C.POINTER(C.c_int)),
-                                gptr if nf else None, dev))
+                                gs.ctypes.data_as(C.POINTER(C.c_int64)), gptr if nf else None, dev))
     Gs = None
     if G is not None and nf:
         Gs, o = [], 0
@@ -273,6 +276,7 @@ def ed_batch_solve(clusters, precision=ED_FP64, omega=None, eta=0.05, axis=ED_AX
             ns = int(np.asarray(cl["t"]).shape[0])
             Gs.append(G[o:o + sz].reshape(2, nf, ns, ns))
             o += sz
+    ed_batch_solve.gf_steps = gs[:n]
     return E0[:n], res[:n], st[:n], it[:n], Gs
 
 

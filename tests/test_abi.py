@@ -53,3 +53,57 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(ed._build, "LIB", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         ed.lib()
+
+
+def declared_signatures():
+    """{name: [parameter type strings]} of every function declared in include/*.h."""
+    sigs = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"(ed_[A-Za-z0-9_]+)\s*\(([^;{]*?)\)\s*;", src, re.S):
+            params = [p.strip() for p in m.group(2).split(",")]
+            if params == ["void"] or params == [""]:
+                params = []
+            sigs[m.group(1)] = params
+    return sigs
+
+
+def _kind(ctype):
+    """'ptr', 'f64', 'i64', 'i32' for a ctypes type; the same classes for a C parameter string."""
+    import ctypes as C
+    if ctype in (C.c_double,):
+        return "f64"
+    if ctype in (C.c_int64, C.c_uint64):
+        return "i64"
+    if ctype in (C.c_int, C.c_uint32, C.c_int32):
+        return "i32"
+    return "ptr"
+
+
+def _ckind(param):
+    if "*" in param:
+        return "ptr"
+    if param.startswith("double"):
+        return "f64"
+    if re.match(r"(u?int64_t|size_t|long)", param):
+        return "i64"
+    return "i32"
+
+
+def test_binding_signatures_match_header(libpath):
+    """Every entry point the Python binding declares has the header's parameter count and, slot by
+    slot, the same class of type (pointer, double, 64-bit or 32-bit integer)."""
+    from paper_2305_18643_gb300 import ed
+    ed._lib = None
+    lib = ed.lib()
+    sigs = declared_signatures()
+    checked = 0
+    for name, params in sigs.items():
+        f = getattr(lib, name)
+        if f.argtypes is None:
+            continue
+        got = [_kind(t) for t in f.argtypes]
+        want = [_ckind(p) for p in params]
+        assert got == want, (name, got, want)
+        checked += 1
+    assert checked >= 15

@@ -313,7 +313,7 @@ def test_batch_matches_oracle(precision):
     exact Lehmann sum."""
     fam = _small_family(24)
     om = W.real_grid(201)
-    E0, res, st, it, G = ed.ed_batch_solve(fam, precision=precision, omega=om, eta=0.05)
+    E0, res, st, it, G = ed.ed_batch_solve(fam, precision=precision, omega=om, eta=0.05, cf_max_levels=20000)
     for k, c in enumerate(fam):
         m = _model(c)
         Gu, _, _, Eref, gap = O.green_exact(m, c["n_up"], c["n_dn"], om + 0.05j, spin=0)
@@ -330,8 +330,9 @@ def test_batch_same_alone_and_in_the_mix():
     """A cluster solved alone (batch of one) and inside a batch of others gives the same E0 and G."""
     fam = _small_family(16, max_orb=10, instance=1)
     om = W.real_grid(101)
-    E0, _, _, _, G = ed.ed_batch_solve(fam, precision=ed.ED_FP64, omega=om, seed=77)
+    E0, _, _, _, G = ed.ed_batch_solve(fam, precision=ed.ED_FP64, omega=om, seed=77, cf_max_levels=20000)
     for k in (0, 5, 11):
-        E1, _, _, _, G1 = ed.ed_batch_solve([fam[k]], precision=ed.ED_FP64, omega=om, seed=77 + k)
+        E1, _, _, _, G1 = ed.ed_batch_solve([fam[k]], precision=ed.ED_FP64, omega=om, seed=77 + k,
+                                             cf_max_levels=20000)
         assert abs(E1[0] - E0[k]) <= 1e-12 * max(1.0, abs(E0[k]))
         assert np.max(np.abs(G1[0] - G[k])) <= 1e-10
