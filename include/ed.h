@@ -145,6 +145,107 @@ ed_status ed_batch_solve(const ed_cluster_desc* descs, int n, int precision, con
                          double eta, int axis, int cf_max_levels, double* E0, double* residual, int* status, int* iters,
                          int64_t* gf_steps, double* G_out, int out_is_device);
 
+/* ---- served form: continuous batching of cluster solves --------------------------------- */
+
+/* A server solves cluster requests (ground state and, if asked, G of both spins) as they arrive,
+ * the way a quantum-cluster code issues one impurity solve per VCA / CDMFT iteration (Sec. 5).
+ * It owns max_slots lanes: each lane is a host thread with a CUDA stream of its own.  A request
+ * is admitted when a lane is free and its device memory (sector tables, Lanczos vectors,
+ * Green-function vectors and G, from closed forms of the sector dimensions) fits what is left
+ * of mem_budget_bytes; admission is first-come first-served, and a later request that fits may
+ * pass a waiting larger one at most 8 times.  Admitted requests run at the same time on their
+ * lanes' streams.  Requests whose sectors (ground-state and N +- 1) hold at most
+ * ED_SRV_BATCH_MAX_DIM elements, with at most 20 orbitals, the continued-fraction method and the
+ * same precision, frequency grid and level cap, are taken together by one lane and solved by the
+ * persistent kernels of ed_batch_solve with a fixed block configuration; larger ones run the
+ * single-cluster path (ed_cluster_create, ed_ground_state, ed_green for each spin).  Which path
+ * a request takes depends on the request alone, and neither path's arithmetic depends on the
+ * other requests, so a request gives the same result alone and among others.
+ * Every request and server call is host-side; no device wait is unbounded. */
+typedef struct ed_server ed_server;
+
+typedef struct ed_request_opts {
+  const double* omega;   /* n_freq frequencies (copied at submit); NULL when n_freq == 0 */
+  int n_freq;            /* 0: ground state only */
+  double eta;            /* broadening of ED_AXIS_REAL */
+  int axis;              /* ED_AXIS_REAL or ED_AXIS_MATSUBARA */
+  int cf_max_levels;     /* preset maximum of every continued fraction; <= 0 selects 400 */
+  double* G_out;         /* host, complex128 [2 spins][n_freq][n_sites][n_sites]; written before
+                            ed_poll / ed_wait report completion; the caller keeps it alive until
+                            then (NULL allowed when n_freq == 0) */
+} ed_request_opts;
+
+typedef struct ed_result {
+  int status;            /* the request's final status (ED_OK, a warning or an error code) */
+  int path;              /* 0 single-cluster path, 1 batched persistent kernels */
+  double E0, residual;   /* as ed_ground_state */
+  int iters;             /* ground-state Lanczos levels */
+  int batch_size;        /* requests solved together with this one (1 on the single path) */
+  int64_t gf_steps;      /* Green-function Lanczos levels */
+  double queued_ms;      /* submit -> start on a lane */
+  double run_ms;         /* start -> results written */
+  double latency_ms;     /* submit -> results written */
+  size_t device_bytes;   /* device memory reserved for it at admission */
+} ed_result;
+
+/* Creates a server on the current device.  mem_budget_bytes > 0, 1 <= max_slots <= 64.
+ * ED_ERR_INVALID, ED_ERR_CUDA. */
+ed_status ed_server_create(size_t mem_budget_bytes, int max_slots, ed_server** out);
+
+/* Stops admitting, cancels queued requests, lets running ones reach their next check point
+ * (they end with ED_ERR_CANCELLED), joins the lanes and frees everything.  NULL is a no-op. */
+void ed_server_destroy(ed_server* srv);
+
+/* Server options: ED_SRV_BATCH_MAX_DIM (largest sector dimension of the batched path; 0 turns it
+ * off; default 100000), ED_SRV_BATCH_MAX_REQUESTS (requests per batched solve; default 64),
+ * ED_SRV_GF_BUDGET_FRACTION (share of mem_budget_bytes that one request's Green-function
+ * vectors may take; default 0.5), ED_SRV_PAUSE (1: lanes take no new request, submitted ones
+ * stay queued; 0: admission resumes; default 0).  ED_ERR_INVALID for an unknown option or a
+ * bad value. */
+enum { ED_SRV_BATCH_MAX_DIM = 1, ED_SRV_BATCH_MAX_REQUESTS = 2, ED_SRV_GF_BUDGET_FRACTION = 3, ED_SRV_PAUSE = 4 };
+ed_status ed_server_set_option(ed_server* srv, int option, double value);
+
+/* Device bytes a request would reserve on the single-cluster path with the given Green-function
+ * budget (gf_budget_bytes <= 0: unlimited), from closed forms only: no CUDA call, no allocation.
+ * ED_ERR_INVALID for a bad description. */
+ed_status ed_request_bytes(const ed_cluster_desc* desc, const ed_request_opts* opts, size_t gf_budget_bytes,
+                           size_t* bytes);
+
+/* Queues one request (desc and opts are copied; desc->precision, gf_method, seed, tol and
+ * max_iter apply).  *req_id receives its id.  ED_ERR_TOO_LARGE if even its smallest device
+ * footprint exceeds the server's budget; ED_ERR_INVALID for a bad description or options;
+ * ED_ERR_STATE after ed_server_destroy has begun. */
+ed_status ed_submit(ed_server* srv, const ed_cluster_desc* desc, const ed_request_opts* opts, uint64_t* req_id);
+
+/* Non-blocking: ED_PENDING while the request is queued or running; otherwise ED_OK with *out
+ * filled (out->status is the request's own status) and the id forgotten; ED_ERR_NOT_FOUND for
+ * an unknown or already collected id. */
+ed_status ed_poll(ed_server* srv, uint64_t req_id, ed_result* out);
+
+/* As ed_poll, but waits up to timeout_s seconds; ED_ERR_TIMEOUT if the request is still pending
+ * then (it keeps running). */
+ed_status ed_wait(ed_server* srv, uint64_t req_id, double timeout_s, ed_result* out);
+
+/* Cancels a request: a queued one ends at once, a running one at its next check point (after
+ * the ground state, between spins); its final status is ED_ERR_CANCELLED.  ED_ERR_NOT_FOUND for
+ * an unknown id. */
+ed_status ed_cancel(ed_server* srv, uint64_t req_id);
+
+/* Test hook for failure handling, with the failure made on the host: when a lane picks the
+ * request it ends it with `status` (< 0) before any device work, as a failed CUDA call would;
+ * the other requests go on.  ED_ERR_NOT_FOUND if the request is not queued. */
+ed_status ed_server_inject_failure(ed_server* srv, uint64_t req_id, int status);
+
+typedef struct ed_server_stats {
+  int64_t submitted, completed, failed, cancelled;
+  int queued, running;            /* now */
+  int max_running;                /* most requests on lanes at once so far */
+  size_t reserved_bytes;          /* device memory reserved now */
+  size_t peak_reserved_bytes;
+  int64_t batched_solves;         /* batched-path solves (each of one or more requests) */
+} ed_server_stats;
+ed_status ed_server_stats_get(ed_server* srv, ed_server_stats* out);
+
 /* ---- lower-level calls (parity tests and benchmarks) ------------------------------------- */
 
 /* Sector dimensions d_up = C(L, n_up), d_dn = C(L, n_dn) of any sector of this cluster. */

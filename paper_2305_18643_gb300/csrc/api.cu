@@ -10,6 +10,22 @@
 namespace ed {
 
 static thread_local std::string g_last_error;
+thread_local cudaStream_t g_alloc_stream = nullptr;
+
+namespace {
+struct PinnedScratch {
+  double* p = nullptr;
+  ~PinnedScratch() {
+    if (p) cudaFreeHost(p);
+  }
+};
+thread_local PinnedScratch t_pinned;
+}  // namespace
+
+double* pinned_scratch() {
+  if (!t_pinned.p) ED_CUDA(cudaMallocHost(&t_pinned.p, kPinnedSlots * sizeof(double)));
+  return t_pinned.p;
+}
 
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 
@@ -113,6 +129,27 @@ void build_model(const ed_cluster_desc* desc, ModelHost& m, HopParams& hp) {
     }
 }
 
+// A cluster whose work runs on `stream` (owned by the caller) or, when stream is nullptr, on a
+// stream of its own.  Throws ed::Error.
+std::unique_ptr<ed_cluster> cluster_create_on(const ed_cluster_desc* desc, cudaStream_t stream) {
+  auto c = std::make_unique<ed_cluster>();
+  build_model(desc, c->model, c->hp);
+  c->desc = *desc;
+  c->desc.t = c->desc.U = c->desc.eps = c->desc.theta = nullptr;
+  if (!(c->desc.tol > 0.0)) c->desc.tol = 1e-12;
+  if (c->desc.max_iter <= 0) c->desc.max_iter = 600;
+  ED_CUDA(cudaGetDevice(&c->device));
+  if (stream) {
+    c->stream = stream;
+    c->owns_stream = false;
+  } else {
+    ED_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+  }
+  c->tables(desc->n_up);
+  c->tables(desc->n_dn);
+  return c;
+}
+
 }  // namespace ed
 
 using namespace ed;
@@ -156,17 +193,7 @@ ed_status ed_cluster_create(const ed_cluster_desc* desc, ed_cluster** out) {
   return guarded([&]() -> ed_status {
     require(desc != nullptr && out != nullptr, "desc and out must not be NULL");
     *out = nullptr;
-    auto c = std::make_unique<ed_cluster>();
-    build_model(desc, c->model, c->hp);
-    c->desc = *desc;
-    c->desc.t = c->desc.U = c->desc.eps = c->desc.theta = nullptr;
-    if (!(c->desc.tol > 0.0)) c->desc.tol = 1e-12;
-    if (c->desc.max_iter <= 0) c->desc.max_iter = 600;
-    ED_CUDA(cudaGetDevice(&c->device));
-    ED_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
-    c->tables(desc->n_up);
-    c->tables(desc->n_dn);
-    *out = c.release();
+    *out = ed::cluster_create_on(desc, nullptr).release();
     return ED_OK;
   });
 }
@@ -175,7 +202,7 @@ void ed_cluster_destroy(ed_cluster* c) {
   if (!c) return;
   try {
     cudaStreamSynchronize(c->stream);
-    cudaStream_t s = c->stream;
+    cudaStream_t s = c->owns_stream ? c->stream : nullptr;
     delete c;
     if (s) cudaStreamDestroy(s);
   } catch (...) {

@@ -571,12 +571,7 @@ static bool band_part(ed_cluster& c, int spin, bool electron, const DevBuf<doubl
   DevBuf<double2> prev((size_t)nzc * pp);
   ED_CUDA(cudaMemsetAsync(prev.p, 0, (size_t)nzc * pp * sizeof(double2), s));
   DevBuf<double> dmax(1);
-  double* hmax = nullptr;
-  ED_CUDA(cudaMallocHost(&hmax, sizeof(double)));
-  struct HF {
-    double* p;
-    ~HF() { cudaFreeHost(p); }
-  } hf{hmax};
+  double* hmax = pinned_scratch() + 17;
   const double sgn = electron ? 1.0 : -1.0;
   int k = 0, hits = 0, next_check = 2;
   bool conv = false;
@@ -663,7 +658,7 @@ bool run_green_band(ed_cluster& c, int spin, const double2* z_host, int nz, doub
   const int p = c.model.ns;
   const int dtype = c.desc.precision;
   BandOptions opt{c.gf_tol > 0 ? c.gf_tol : (dtype == ED_FP64 ? 1e-10 : 1e-6), c.band_max_dim > 0 ? c.band_max_dim : 20000,
-                  size_t(32) << 30};
+                  c.gf_mem_budget ? c.gf_mem_budget : size_t(32) << 30};
   DevBuf<double2> zd(nz);
   ED_CUDA(cudaMemcpyAsync(zd.p, z_host, nz * sizeof(double2), cudaMemcpyHostToDevice, s));
   DevBuf<double2> Ge((size_t)nz * p * p), Gh((size_t)nz * p * p);

@@ -706,9 +706,57 @@ static void run_batch_kernels(int threads, int mode, BCluster* C, const int* cor
   }
 }
 
+// Device bytes batch_solve allocates for these clusters (tables, ground states, continued-fraction
+// coefficients, evaluated fractions and the per-block workspace; the caller's G not included).
+size_t batch_device_bytes(const ed_cluster_desc* descs, int n, int precision, int nz, int cf_max_steps, int sms) {
+  auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
+  const int cap = cf_max_steps > 0 ? cf_max_steps : 20000;
+  const size_t es = precision == ED_FP64 ? 8 : 4;
+  size_t bytes = 0;
+  int64_t maxd = 1, nruns = 0;
+  for (int c = 0; c < n; ++c) {
+    const int L = descs[c].n_sites + descs[c].n_bath, p = descs[c].n_sites;
+    const int nu = descs[c].n_up, nd = descs[c].n_dn;
+    std::map<int, int64_t> dims;
+    auto table = [&](int N) {
+      if (N < 0 || N > L || dims.count(N)) return;
+      const int64_t d = (int64_t)binomial(L, N);
+      dims[N] = d;
+      const int split = L / 2, zmax = std::max(1, N * (L - N));
+      bytes += r256(d * 4) + r256((size_t(1) << split) * 4) + r256((size_t(1) << (L - split)) * 4) +
+               r256((size_t)zmax * d * 4) + r256(d) + r256(d * 8) + r256(d * 4);
+    };
+    table(nu);
+    table(nd);
+    const int64_t d = dims[nu] * dims[nd];
+    maxd = std::max(maxd, d);
+    bytes += r256(d * 8);
+    if (nz <= 0) continue;
+    for (int dn : {1, -1}) {
+      table(nu + dn);
+      if (nu != nd) table(nd + dn);
+    }
+    for (int spin = 0; spin < (nu != nd ? 2 : 1); ++spin)
+      for (int dn : {1, -1}) {
+        const int nt = (spin == 0 ? nu : nd) + dn;
+        if (nt < 0 || nt > L) continue;
+        const int64_t dt = (int64_t)binomial(L, nt) * (spin == 0 ? dims[nd] : dims[nu]);
+        maxd = std::max(maxd, dt);
+        const int64_t mmax = std::max<int64_t>(64, std::min<int64_t>(cap, 2 * dt + 16));
+        const int runs = p + p * (p - 1) / 2;
+        nruns += runs;
+        bytes += (size_t)runs * (r256(mmax * 8) + r256((mmax + 1) * 8));
+      }
+  }
+  bytes += r256((size_t)std::max<int64_t>(nruns, 1) * std::max(nz, 0) * 16);
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(n + nruns, (int64_t)sms * 4));
+  const size_t stride = ((3 * maxd * es + 255) / 256) * 256 + 4 * maxd * 8 + 256;
+  return bytes + (size_t)blocks * stride + (size_t(1) << 20);
+}
+
 void batch_solve(const ed_cluster_desc* descs, int n, int precision, const double2* z_host, int nz, bool do_gf,
                  int cf_max_steps, double* E0_out, double* res_out, int* status_out, int* iters_out,
-                 int64_t* gf_steps_out, double2* G_dev_out, cudaStream_t s) {
+                 int64_t* gf_steps_out, double2* G_dev_out, cudaStream_t s, int fixed_threads, int fixed_mode) {
   static const BBinom bn = make_bbinom();
   if (n <= 0) return;
   // ---- models
@@ -906,8 +954,10 @@ void batch_solve(const ed_cluster_desc* descs, int n, int precision, const doubl
   while ((1 << nbucket) < n) ++nbucket;
   const auto key = std::make_tuple(Lmax, dbucket, nbucket, precision);
   std::pair<int, int> cfg{256, 0};
-  bool tuned;
-  {
+  bool tuned = fixed_threads > 0;
+  if (tuned) {
+    cfg = {fixed_threads, fixed_mode};
+  } else {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);
     tuned = it != g_tune.end();
@@ -1020,7 +1070,7 @@ extern "C" ed_status ed_batch_solve(const ed_cluster_desc* descs, int n, int pre
       Gdev = Gd.p;
     }
     batch_solve(descs, n, precision, z.data(), n_freq, n_freq > 0, cf_max_levels > 0 ? cf_max_levels : 400, E0,
-                residual, status, iters, gf_steps, Gdev, s);
+                residual, status, iters, gf_steps, Gdev, s, 0, 0);
     if (n_freq > 0 && !out_is_device) {
       ED_CUDA(cudaMemcpyAsync(G_out, Gd.p, total * sizeof(double2), cudaMemcpyDeviceToHost, s));
       ED_CUDA(cudaStreamSynchronize(s));

@@ -63,36 +63,65 @@ struct ProfScope {
   ~ProfScope();
 };
 
-// Device buffer with RAII ownership (cudaMalloc / cudaFree).
+// Stream on which DevBuf allocates and frees in this thread (stream-ordered: cudaMallocAsync /
+// cudaFreeAsync), or nullptr for cudaMalloc / cudaFree.  cudaFree waits for the whole device, so
+// code that shares the GPU with other streams of the same process (the server's lanes) sets it to
+// the one stream its buffers are used on.
+extern thread_local cudaStream_t g_alloc_stream;
+struct AllocStreamScope {
+  cudaStream_t prev;
+  explicit AllocStreamScope(cudaStream_t s) : prev(g_alloc_stream) { g_alloc_stream = s; }
+  ~AllocStreamScope() { g_alloc_stream = prev; }
+  AllocStreamScope(const AllocStreamScope&) = delete;
+  AllocStreamScope& operator=(const AllocStreamScope&) = delete;
+};
+
+// Page-locked host scratch of this thread (kPinnedSlots doubles, allocated on first use and kept
+// for the thread's life), the landing place of small device-to-host reads.  Slots: [0, 16) ground
+// state, 16 continued fractions, 17 band Lanczos.
+constexpr int kPinnedSlots = 32;
+double* pinned_scratch();
+
+// Device buffer with RAII ownership (cudaMalloc / cudaFree, or the stream-ordered pair when
+// g_alloc_stream is set at allocation; the buffer is then freed on that stream).
 template <typename T>
 struct DevBuf {
   T* p = nullptr;
   size_t n = 0;
+  cudaStream_t s = nullptr;  // stream of a stream-ordered allocation
   DevBuf() = default;
   explicit DevBuf(size_t count) { alloc(count); }
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
-  DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n), s(o.s) { o.p = nullptr; o.n = 0; o.s = nullptr; }
   DevBuf& operator=(DevBuf&& o) noexcept {
-    if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    if (this != &o) { release(); p = o.p; n = o.n; s = o.s; o.p = nullptr; o.n = 0; o.s = nullptr; }
     return *this;
   }
   ~DevBuf() { release(); }
   void alloc(size_t count) {
     release();
     if (count == 0) return;
-    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    cudaStream_t as = g_alloc_stream;
+    cudaError_t e = as ? cudaMallocAsync((void**)&p, count * sizeof(T), as) : cudaMalloc(&p, count * sizeof(T));
     if (e != cudaSuccess) {
       cudaGetLastError();
       p = nullptr;
-      throw Error(ED_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
+      throw Error(ED_ERR_OOM, "device allocation of " + std::to_string(count * sizeof(T)) + " bytes failed");
     }
     n = count;
+    s = as;
   }
   void release() {
-    if (p) cudaFree(p);
+    if (p) {
+      if (s)
+        cudaFreeAsync(p, s);
+      else
+        cudaFree(p);
+    }
     p = nullptr;
     n = 0;
+    s = nullptr;
   }
 };
 
@@ -236,6 +265,7 @@ struct ed_cluster {
   ed::HopParams hp;
   ed_cluster_desc desc;  // array pointers inside are cleared
   cudaStream_t stream = nullptr;
+  bool owns_stream = true;     // false: the stream belongs to the caller (a server lane)
   int device = 0;
   std::map<int, std::unique_ptr<ed::SpinTables>> spins;  // by particle number
   // ground state (FP64, contiguous d_up x d_dn)
@@ -247,7 +277,12 @@ struct ed_cluster {
   int cf_max_steps = 0;        // steps per continued fraction (0: default)
   double gf_tol = 0.0;         // |Delta G| between convergence checks (0: default)
   bool gf_converged = true;
+  size_t gf_mem_budget = 0;    // bytes for Green-function Lanczos vectors (0: default)
   int gf_max_steps = 0;
   ed::SpinTables& tables(int N);
   ed::SectorView view(int n_up, int n_dn, int64_t ld);
 };
+
+namespace ed {
+std::unique_ptr<ed_cluster> cluster_create_on(const ed_cluster_desc* desc, cudaStream_t stream);
+}  // namespace ed

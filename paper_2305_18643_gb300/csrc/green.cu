@@ -254,12 +254,7 @@ static bool cf_part(ed_cluster& c, int spin, bool electron, int dtype, const Dev
   const int nzs = (nz + zstride - 1) / zstride;
   DevBuf<int2> druns(R);
   ED_CUDA(cudaMemcpyAsync(druns.p, runs_h.data(), R * sizeof(int2), cudaMemcpyHostToDevice, s));
-  int* host_active = nullptr;
-  ED_CUDA(cudaMallocHost(&host_active, sizeof(int)));
-  struct HostFree {
-    int* p;
-    ~HostFree() { cudaFreeHost(p); }
-  } hf{host_active};
+  int* host_active = (int*)(pinned_scratch() + 16);
   for (int r0 = 0; r0 < R; r0 += Rc) {
     const int rc = std::min(Rc, R - r0);
     DevBuf<char> V0(rc * vstride * es), V1(rc * vstride * es);
@@ -350,7 +345,7 @@ void run_green_cf(ed_cluster& c, int spin, const double2* z_host, int nz, double
   const int R = p + p * (p - 1) / 2;
   const int dtype = c.desc.precision;
   GreenOptions opt{c.gf_tol > 0 ? c.gf_tol : (dtype == ED_FP64 ? 1e-10 : 1e-6), c.cf_max_steps > 0 ? c.cf_max_steps : 20000,
-                   size_t(48) << 30};
+                   c.gf_mem_budget ? c.gf_mem_budget : size_t(48) << 30};
   DevBuf<double2> zd(nz);
   ED_CUDA(cudaMemcpyAsync(zd.p, z_host, nz * sizeof(double2), cudaMemcpyHostToDevice, s));
   DevBuf<double2> Ge((size_t)R * nz), Gh((size_t)R * nz);

@@ -46,11 +46,6 @@ void axpy_neg(double* y, const double* a, const double* x, int64_t n, cudaStream
 }
 
 
-struct PinnedScalars {
-  double* p = nullptr;
-  PinnedScalars() { ED_CUDA(cudaMallocHost(&p, 16 * sizeof(double))); }
-  ~PinnedScalars() { if (p) cudaFreeHost(p); }
-};
 
 // One Lanczos pass set (first pass + retrace) from start vector `v0` (dtype, normalized in
 // place).  Writes the normalized-by-construction sum_n s_n v_n into omega (FP64).
@@ -113,7 +108,8 @@ static int lanczos_pass(ed_cluster& c, const SectorView& sv, int dtype, LanczosR
         if (!act) {
           // the run stopped at the first level whose b_{n+1} vanished: find it on the host
           std::vector<double> b(n + 2);
-          ED_CUDA(cudaMemcpy(b.data(), L.beta.p, (n + 2) * sizeof(double), cudaMemcpyDeviceToHost));
+          ED_CUDA(cudaMemcpyAsync(b.data(), L.beta.p, (n + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
+          ED_CUDA(cudaStreamSynchronize(s));
           levels = 1;
           while (levels < n + 1 && b[levels] > L.ls.btol) ++levels;
           *breakdown = levels < L.M;
@@ -142,8 +138,7 @@ GroundResult run_ground_state(ed_cluster& c, int dtype, double tol, int max_iter
   const int64_t du = sv.d_up, dd = sv.d_dn, dim = du * dd;
   GroundResult R;
   c.omega.alloc(std::max<int64_t>(dim, 1));
-  PinnedScalars hs;
-  double* host = hs.p;
+  double* host = pinned_scratch();  // slots 0..15
   if (dim == 0) throw Error(ED_ERR_INVALID, "empty sector");
 
   const int nblk = lanczos_blocks(sv);

@@ -74,6 +74,7 @@ def lib():
             "ed_batch_solve": (i32, [C.POINTER(ed_cluster_desc), i32, i32, _dp, i32, C.c_double, i32, i32, _dp, _dp,
                                      C.POINTER(i32), C.POINTER(i32), C.POINTER(i64), vp, i32]),
         }
+        sig.update(_server_sigs)
         for name, (res, args) in sig.items():
             f = getattr(L, name)
             f.restype = res
@@ -314,3 +315,144 @@ class Cluster:
 
     def green(self, omega, eta, axis=ED_AXIS_REAL, spin=0):
         return ed_green(self.h, omega, eta, self.ns, axis, spin)[1]
+
+
+# ----------------------------------------------------------------------------- served form
+class ed_request_opts(C.Structure):
+    _fields_ = [("omega", _dp), ("n_freq", C.c_int), ("eta", C.c_double), ("axis", C.c_int),
+                ("cf_max_levels", C.c_int), ("G_out", _dp)]
+
+
+class ed_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("path", C.c_int), ("E0", C.c_double), ("residual", C.c_double),
+                ("iters", C.c_int), ("batch_size", C.c_int), ("gf_steps", C.c_int64), ("queued_ms", C.c_double),
+                ("run_ms", C.c_double), ("latency_ms", C.c_double), ("device_bytes", C.c_size_t)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ed_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("cancelled", C.c_int64), ("queued", C.c_int), ("running", C.c_int), ("max_running", C.c_int),
+                ("reserved_bytes", C.c_size_t), ("peak_reserved_bytes", C.c_size_t),
+                ("batched_solves", C.c_int64)]
+
+
+ED_SRV_BATCH_MAX_DIM, ED_SRV_BATCH_MAX_REQUESTS, ED_SRV_GF_BUDGET_FRACTION, ED_SRV_PAUSE = 1, 2, 3, 4
+
+_server_sigs = {
+    "ed_server_create": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(C.c_void_p)]),
+    "ed_server_destroy": (None, [C.c_void_p]),
+    "ed_server_set_option": (C.c_int, [C.c_void_p, C.c_int, C.c_double]),
+    "ed_request_bytes": (C.c_int, [C.POINTER(ed_cluster_desc), C.POINTER(ed_request_opts), C.c_size_t,
+                                   C.POINTER(C.c_size_t)]),
+    "ed_submit": (C.c_int, [C.c_void_p, C.POINTER(ed_cluster_desc), C.POINTER(ed_request_opts),
+                            C.POINTER(C.c_uint64)]),
+    "ed_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(ed_result)]),
+    "ed_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_double, C.POINTER(ed_result)]),
+    "ed_cancel": (C.c_int, [C.c_void_p, C.c_uint64]),
+    "ed_server_inject_failure": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int]),
+    "ed_server_stats_get": (C.c_int, [C.c_void_p, C.POINTER(ed_server_stats)]),
+}
+
+
+def _slib():
+    return lib()
+
+
+def _one_desc(cluster, precision, gf_method, seed, tol, max_iter=0):
+    descs, keep = _desc_array([cluster], seed, tol)
+    d = descs[0]
+    d.precision, d.gf_method, d.max_iter = int(precision), int(gf_method), int(max_iter)
+    return d, keep
+
+
+def ed_request_bytes(cluster, n_freq=0, precision=ED_FP64, gf_method=ED_GF_CF, cf_max_levels=0, gf_budget=0):
+    """Device bytes of one request on the single-cluster path (host-side closed forms only)."""
+    d, keep = _one_desc(cluster, precision, gf_method, 0, 0.0)
+    om = np.zeros(max(n_freq, 1))
+    G = np.zeros(1, dtype=np.complex128)
+    o = ed_request_opts(om.ctypes.data_as(_dp), int(n_freq), 0.05, ED_AXIS_REAL, int(cf_max_levels),
+                        G.ctypes.data_as(_dp))
+    out = C.c_size_t()
+    _check(_slib().ed_request_bytes(C.byref(d), C.byref(o), int(gf_budget), C.byref(out)))
+    return out.value
+
+
+class Server:
+    """ed_server_* with Python-owned request buffers.  submit() returns the request id; poll() /
+    wait() return (ed_result dict, G [2, n_freq, n_sites, n_sites] or None) once it is done."""
+
+    def __init__(self, mem_budget_bytes, max_slots=4, **options):
+        h = C.c_void_p()
+        _check(_slib().ed_server_create(int(mem_budget_bytes), int(max_slots), C.byref(h)))
+        self.h = h
+        self._live = {}
+        names = {"batch_max_dim": ED_SRV_BATCH_MAX_DIM, "batch_max_requests": ED_SRV_BATCH_MAX_REQUESTS,
+                 "gf_budget_fraction": ED_SRV_GF_BUDGET_FRACTION, "paused": ED_SRV_PAUSE}
+        for k, v in options.items():
+            _check(_slib().ed_server_set_option(self.h, names[k], float(v)))
+
+    def submit(self, cluster, omega=None, eta=0.05, axis=ED_AXIS_REAL, precision=ED_FP64, gf_method=ED_GF_CF,
+               seed=0, tol=0.0, cf_max_levels=0, max_iter=0):
+        d, keep = _one_desc(cluster, precision, gf_method, seed, tol, max_iter)
+        ns = int(np.asarray(cluster["t"]).shape[0])
+        om = _arr(omega, np.asarray(omega).size) if omega is not None else np.zeros(0)
+        nf = om.size
+        G = np.zeros((2, nf, ns, ns), dtype=np.complex128) if nf else None
+        o = ed_request_opts(om.ctypes.data_as(_dp) if nf else None, nf, float(eta), int(axis), int(cf_max_levels),
+                            G.ctypes.data_as(_dp) if nf else None)
+        rid = C.c_uint64()
+        _check(_slib().ed_submit(self.h, C.byref(d), C.byref(o), C.byref(rid)))
+        self._live[rid.value] = (G, om, keep)
+        return rid.value
+
+    def _done(self, rid, st, res):
+        if st == ED_PENDING:
+            return None
+        G = self._live.pop(rid)[0]
+        return res.as_dict(), G
+
+    def poll(self, rid):
+        res = ed_result()
+        st = _check(_slib().ed_poll(self.h, int(rid), C.byref(res)))
+        return self._done(rid, st, res)
+
+    def wait(self, rid, timeout_s=600.0):
+        res = ed_result()
+        st = _check(_slib().ed_wait(self.h, int(rid), float(timeout_s), C.byref(res)))
+        return self._done(rid, st, res)
+
+    def pause(self, on=True):
+        """Stop (on) or resume (off) admission; submitted requests stay queued while paused."""
+        _check(_slib().ed_server_set_option(self.h, ED_SRV_PAUSE, 1.0 if on else 0.0))
+
+    def cancel(self, rid):
+        _check(_slib().ed_cancel(self.h, int(rid)))
+
+    def inject_failure(self, rid, status=ED_ERR_CUDA):
+        _check(_slib().ed_server_inject_failure(self.h, int(rid), int(status)))
+
+    def stats(self):
+        s = ed_server_stats()
+        _check(_slib().ed_server_stats_get(self.h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def close(self):
+        if self.h:
+            _slib().ed_server_destroy(self.h)
+            self.h = None
+            self._live.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
