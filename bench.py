@@ -45,6 +45,10 @@ WORKLOADS = {
     "batch": (lambda instance=0: W.batched_family(512, instance=instance),
               "512 seeded clusters of 4-12 orbitals (chains, 2-leg ladders, 2x2 plaquettes + 0-8 bath), "
               "|t| ~ U[0.5,1.5], U ~ U[2,10], mu = U/2, random fillings; both spins", "fp32", "cf", 512),
+    "served": (None, "stream of solve requests: open 2xW clusters of 8/10/12/14 orbitals (uniform), t=-1, "
+               "t'=+-0.3 seeded per bond, U=8, mu=4, half filling; ground state + G on 2048 Matsubara "
+               "frequencies (beta=50); continued fractions up to 10 orbitals, band Lanczos from 12",
+               "fp32", "mixed", 2048),
 }
 ETA = 0.05
 # Krylov vectors per part of the band Green function: the paper's runs stop at R = 100-500 (Sec. 4.4)
@@ -58,6 +62,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="4x4")
+    ap.add_argument("--requests", type=int, default=32, help="served workload: requests per stream")
+    ap.add_argument("--rates", type=str, default="1,4,16",
+                    help="served workload: Poisson arrival rates as multiples of 1 / (mean sequential FP64 solve time)")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default=None)
     ap.add_argument("--gf", choices=["band", "cf", "none"], default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -160,6 +167,8 @@ def run_ours(args, rank, world, local_rank):
     gf = args.gf or gf_d
     if args.workload == "batch":
         return run_batch(args, rank, world, local_rank, torch, ed)
+    if args.workload == "served":
+        return run_served(args, rank, world, local_rank, torch, ed)
     c = gen(instance=rank)
     ns = c["t"].shape[0]
     omega = W.real_grid(nfreq)
@@ -225,7 +234,7 @@ def run_ours(args, rank, world, local_rank):
     n_step, ms_step, by_step = prof[ed.ED_K_LANCZOS_STEP]
     peak, peak_kind = measured_peak_hbm()
     achieved = (by_step / 1e9) / (ms_step / 1e3) if ms_step > 0 else None
-    traffic = ncu_traffic("hpsi.cu", "lanczos_step_4x4.txt") if args.workload == "4x4" else None
+    traffic = ncu_traffic("hpsi.cu", "lanczos_step_4x4.md") if args.workload == "4x4" else None
     hpsi_per_solve = (prof[ed.ED_K_LANCZOS_STEP][0] + prof[ed.ED_K_HPSI][0]) / max(args.steps, 1)
     result = {
         "metric": "ED solves/s (H.psi HBM GB/s and % roofline in `roofline`)",
@@ -367,6 +376,189 @@ def run_batch(args, rank, world, local_rank, torch, ed):
     return result
 
 
+def served_stream(n, instance):
+    """n requests of the served workload (seeded): (cluster, gf_method name)."""
+    rng = np.random.default_rng(20230529 + 5000 + instance)
+    out = []
+    for _ in range(n):
+        c = W.served_request(rng)
+        out.append((c, "cf" if c["t"].shape[0] <= 10 else "band"))
+    return out
+
+
+def run_served(args, rank, world, local_rank, torch, ed):
+    """Served form: requests through ed_server (FP32 vectors, memory admission, batched small
+    requests, lanes overlapping on the device).  A step is one stream of --requests requests
+    submitted at once (saturation); value = requests completed / s.  Beside it: the same kind of
+    requests solved one after another by the plain FP64 path (ed_cluster_create, ed_ground_state,
+    ed_green, ed_cluster_destroy), and Poisson streams at multiples of that path's rate with their
+    p50 / p99 latency."""
+    import threading
+    nfreq = WORKLOADS["served"][4]
+    om = W.matsubara_grid(nfreq)
+    GB = 1 << 30
+    budget = int(float(os.environ.get("ED_SERVED_BUDGET_GB", "200")) * GB)
+    lanes = 8
+
+    def gfm(name):
+        return ed.ED_GF_CF if name == "cf" else ed.ED_GF_BAND
+
+    # ---- the plain FP64 path, one request after another (calibration of the arrival rates)
+    cal = served_stream(8, 100 + rank)
+    seq_ms, seq_E0 = [], []
+    for k, (c, m) in enumerate([cal[0]] + cal):  # the first solve warms up and is not counted
+        ns = c["t"].shape[0]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = ed.ed_cluster_create(c, precision=ed.ED_FP64, gf_method=gfm(m), seed=77 + max(k - 1, 0))
+        try:
+            _, E0, _, _ = ed.ed_ground_state(h)
+            ed.ed_green(h, om, 0.0, ns, axis=ed.ED_AXIS_MATSUBARA)
+        finally:
+            ed.ed_cluster_destroy(h)
+        if k > 0:
+            seq_ms.append(1e3 * (time.perf_counter() - t0))
+            seq_E0.append(E0)
+    t_seq = float(np.mean(seq_ms))
+
+    srv = ed.Server(budget, max_slots=lanes)
+
+    def run_stream(reqs, gaps_s, seed0):
+        """Submits reqs with the given gaps (seconds before each), waits for all; returns results."""
+        ids = []
+        t0 = time.perf_counter()
+        t_next = t0
+        for k, ((c, m), g) in enumerate(zip(reqs, gaps_s)):
+            t_next += g
+            dt = t_next - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            ids.append(srv.submit(c, omega=om, eta=0.0, axis=ed.ED_AXIS_MATSUBARA, precision=ed.ED_FP32,
+                                  gf_method=gfm(m), seed=seed0 + k))
+        res = [srv.wait(i, timeout_s=1800.0)[0] for i in ids]
+        return res, time.perf_counter() - t0
+
+    # warm-up: the first requests of every size (pool growth, module load)
+    warm = served_stream(max(args.warmup, 4), 200 + rank)
+    run_stream(warm, [0.0] * len(warm), 1)
+    # timed: saturated streams
+    streams = [served_stream(args.requests, 300 + 10 * rank + s) for s in range(args.steps)]
+    ed.ed_profile_enable(1)
+    l0 = ed.ed_launch_count()
+    all_res = []
+    with ClockSampler(local_rank) as clk:
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        for s, reqs in enumerate(streams):
+            res, _ = run_stream(reqs, [0.0] * len(reqs), 1000 * (s + 1))
+            all_res += res
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    launches = ed.ed_launch_count() - l0
+    prof = {k: ed.ed_profile_read(k) for k in range(ed.ED_K_COUNT)}
+    ed.ed_profile_enable(0)
+    if world > 1:
+        t = torch.tensor([wall], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        wall = float(t.item())
+    n_req = args.requests * args.steps
+    value = world * n_req / wall
+    lat = np.array([r["latency_ms"] for r in all_res])
+    # Poisson streams at multiples of the sequential FP64 rate
+    sweep = []
+    rng = np.random.default_rng(20230529 + 5999 + rank)
+    for f in [float(x) for x in args.rates.split(",") if x.strip()]:
+        reqs = served_stream(args.requests, 400 + int(10 * f) + rank)
+        gaps = rng.exponential(t_seq / 1e3 / f, size=len(reqs))
+        gaps[0] = 0.0
+        res, span = run_stream(reqs, gaps, 50000 + int(f * 100))
+        L = np.array([r["latency_ms"] for r in res])
+        sweep.append({"rate_x_seq": f, "arrival_rate_per_s": f * 1e3 / t_seq, "requests": len(reqs),
+                      "p50_ms": float(np.percentile(L, 50)), "p99_ms": float(np.percentile(L, 99)),
+                      "mean_queued_ms": float(np.mean([r["queued_ms"] for r in res])),
+                      "completed_per_s": len(reqs) / span, "max_running": srv.stats()["max_running"]})
+    stats = srv.stats()
+    # accuracy: the calibration requests again through the server (FP32) against their FP64 energies
+    acc_res, _ = run_stream(cal, [0.0] * len(cal), 77)
+    dE = max(abs(r["E0"] - e) / max(1.0, abs(e)) for r, e in zip(acc_res, seq_E0))
+    srv.close()
+    n_s, ms_s, by_s = prof[ed.ED_K_LANCZOS_STEP]
+    peak, peak_kind = measured_peak_hbm()
+    achieved = (by_s / 1e9) / (ms_s / 1e3) if ms_s > 0 else None
+    h2d = int(np.mean([8 * (c["t"].size + c["t"].shape[0] + 1) + 8 * nfreq for reqs in streams for c, _ in reqs]))
+    d2h = int(np.mean([2 * nfreq * c["t"].shape[0] ** 2 * 16 + 64 for reqs in streams for c, _ in reqs]))
+    result = {
+        "metric": "ED solves/s and p50/p99 latency, served form (H.psi GB/s in `roofline`)",
+        "value": value, "unit": "requests/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 vectors, f64 reductions", "data": "synthetic (seeded request stream)",
+        "config": {"workload": "served: " + WORKLOADS["served"][1], "requests_per_step": args.requests,
+                   "lanes": lanes, "memory_budget_gb": budget / GB, "n_freq": nfreq, "axis": "matsubara",
+                   "timing": "host wall clock from the first submit to the last result (requests carry host "
+                             "inputs and host outputs; synchronize on both sides)",
+                   "l2": "L2 flushed by the stream's own traffic (vectors up to 94 MB, several requests at once)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "clocks": clk.summary(),
+        "e2e": {"value": value, "unit": "requests/s", "h2d_bytes_per_step": h2d * args.requests,
+                "d2h_bytes_per_step": d2h * args.requests,
+                "note": "the served form is host-to-host: every request's inputs and G cross PCIe/C2C inside "
+                        "the timed region"},
+        "gpu_launches": int(launches),
+        "latency_ms_saturated": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+        "sequential_fp64": {"value": 1e3 / t_seq, "unit": "requests/s", "mean_ms": t_seq, "requests": len(cal),
+                            "how": "ed_cluster_create, ed_ground_state, ed_green (same method per size), "
+                                   "ed_cluster_destroy, one request after another, FP64"},
+        "speedup_vs_sequential_fp64": value / (1e3 / t_seq),
+        "max_rel_E0_diff_fp32_served_vs_fp64": dE,
+        "poisson": sweep,
+        "server": {k: stats[k] for k in ("completed", "failed", "max_running", "peak_reserved_bytes",
+                                         "batched_solves")},
+        "roofline": {"bound": "hbm", "kernel": "lanczos_step (fused H.psi + Lanczos epilogue), all requests",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None, "peak_source": peak_kind,
+                     "launches": n_s, "note": "event-timed launches overlap with other lanes' kernels"},
+        "kernels_ms": {ed.ed_profile_kernel_name(k): round(v[1], 3) for k, v in prof.items() if v[0]},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline_served(all_res, streams)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return result
+
+
+def cpu_baseline_served(results, streams, target_s=15.0):
+    """Oracle factorized H.psi timed once per request size (bounded rows), times each request's
+    H.psi count in the GPU run (ground state both passes + Green-function Lanczos levels)."""
+    import oracle as O
+    reqs = [c for s in streams for c, _ in s]
+    per_size = {}
+    budget = target_s / 4
+    for c in reqs:
+        n = c["t"].shape[0]
+        if n in per_size:
+            continue
+        m = O.Model(c["t"], c["U"], c["mu"], c["eps"], c["theta"])
+        du = len(O.sector_basis(m.L, c["n_up"]))
+        dd = len(O.sector_basis(m.L, c["n_dn"]))
+        psi = np.random.default_rng(0).standard_normal((du, dd))
+        rows = max(1, min(du, 16))
+        while True:
+            t0 = time.perf_counter()
+            O.apply_h_rows(m, c["n_up"], c["n_dn"], psi, np.arange(rows))
+            dt = time.perf_counter() - t0
+            if dt > budget / 8 or rows == du:
+                break
+            rows = min(du, rows * 4)
+        per_size[n] = dt * du / rows
+    t = [per_size[c["t"].shape[0]] * (2 * r["iters"] + r["gf_steps"]) for c, r in zip(reqs, results)]
+    return {"value": 1.0 / float(np.mean(t)), "unit": "requests/s", "cores": 1, "kind": "oracle",
+            "sample": "oracle apply_h_rows (scipy factorized H.psi, FP64) timed on a block of rows per request "
+                      "size %s, scaled to a full H.psi and multiplied by each request's H.psi count in the GPU run"
+                      % sorted(per_size)}
+
+
 def cpu_baseline_batch(fam, info, target_s=15.0):
     """Oracle factorized H.psi timed on the first clusters of the family, times each cluster's
     H.psi count in the GPU run (ground state both passes + continued-fraction levels)."""
@@ -418,10 +610,18 @@ def cpu_baseline(workload, c, hpsi_per_solve):
                       % hpsi_per_solve}
 
 
+# H.psi per solve of the GPU runs (ground state both passes + Green-function Lanczos vectors), the
+# counts the oracle arm multiplies its timed H.psi by
+HPSI_PER_SOLVE = {"4x4": 1264.0, "cdmft": 2000.0, "2x4": 20000.0}
+
+
 def run_reference(args, rank, world):
     gen, label, prec_d, gf_d, nfreq = WORKLOADS[args.workload]
     c = gen(instance=0)
-    hpsi_per_solve = {"4x4": 1000.0, "cdmft": 2000.0, "2x4": 20000.0}[args.workload]
+    if args.workload not in HPSI_PER_SOLVE:
+        return {"impl": "reference", "unavailable": "the oracle arm covers the single-cluster workloads; the %s "
+                "workload reports its oracle baseline in cpu_baseline of the GPU line" % args.workload}
+    hpsi_per_solve = HPSI_PER_SOLVE[args.workload]
     for _ in range(args.warmup):
         oracle_sample(args.workload, c, rows_target_s=2.0)
     t0 = time.perf_counter()
