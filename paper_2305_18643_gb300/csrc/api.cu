@@ -127,6 +127,15 @@ void build_model(const ed_cluster_desc* desc, ModelHost& m, HopParams& hp) {
       hp.Uf[i] = (float)m.U[i];
       if (m.U[i] != 0.0) hp.umask |= 1u << i;
     }
+    hp.uniform_u = 1;
+    for (int i = 0; i < L; ++i)
+      if (((hp.umask >> i) & 1u) && m.U[i] != hp.u0) {
+        if (hp.u0 == 0.0)
+          hp.u0 = m.U[i];
+        else
+          hp.uniform_u = 0;
+      }
+    hp.u0f = (float)hp.u0;
 }
 
 // A cluster whose work runs on `stream` (owned by the caller) or, when stream is nullptr, on a

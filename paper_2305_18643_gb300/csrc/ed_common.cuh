@@ -23,6 +23,16 @@ constexpr int kMaxPairs = kMaxOrb * (kMaxOrb - 1);
 __host__ __device__ inline uint32_t ent_col(uint32_t e) { return e >> 8; }
 __host__ __device__ inline uint32_t ent_neg(uint32_t e) { return (e >> 7) & 1u; }
 __host__ __device__ inline uint32_t ent_vidx(uint32_t e) { return e & 127u; }
+// Entry of the row kernel's slot-major table: (col << 14) | (((vidx << 1) | neg) << 2), so that
+// e >> 10 is the byte offset of the column's 16-byte group in shared memory and e & 0x3FC that
+// of its signed value in a table of 4-byte values (signed values of one index side by side, so
+// the few distinct values of a warp's loads fall in distinct banks).  col < 2^18.
+__host__ __device__ inline uint32_t row_ell_pack(uint32_t e) {
+  return (ent_col(e) << 14) | (((ent_vidx(e) << 1) | ent_neg(e)) << 2);
+}
+// Slots of zeros after the last slot of the row kernel's table, so that it may load ahead
+// without bounds checks.
+constexpr int kEllPad = 8;
 
 struct Error : public std::runtime_error {
   ed_status code;
@@ -142,6 +152,9 @@ struct HopParams {
   float Uf[kMaxOrb];
   uint32_t umask;   // orbitals with U != 0
   int nvals;
+  int uniform_u;    // 1: every orbital of umask has the same U (u0), so sum_i U_i n_i n_i = u0 popc(...)
+  double u0;
+  float u0f;
 };
 
 // One spin's sector with N particles: basis, two-level rank tables, hopping table, diagonal.

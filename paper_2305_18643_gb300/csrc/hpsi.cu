@@ -255,74 +255,179 @@ struct Partial3<float> {
   }
 };
 
+// ---- accumulators of 16-byte groups: four FP32 rows (packed FMAs, fma.rn.f32x2, on the row
+// pairs (0,1) and (2,3)) or two FP64 rows.
+__device__ __forceinline__ unsigned long long f2_pack(float x, float y) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+  return r;
+}
+__device__ __forceinline__ float2 f2_unpack(unsigned long long r) {
+  float2 v;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+  return v;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b, unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+template <typename T>
+struct Acc16;
+template <>
+struct Acc16<float> {
+  unsigned long long a, b;  // rows (0,1), rows (2,3)
+  __device__ void set(const float* v) {
+    a = f2_pack(v[0], v[1]);
+    b = f2_pack(v[2], v[3]);
+  }
+  // acc += s * (16-byte group x)
+  __device__ void fma(float s, const ulonglong2& x) {
+    const unsigned long long ss = f2_pack(s, s);
+    a = f2_fma(ss, x.x, a);
+    b = f2_fma(ss, x.y, b);
+  }
+  // the same with s given as the pair (s, s)
+  __device__ void fma_pair(unsigned long long ss, const ulonglong2& x) {
+    a = f2_fma(ss, x.x, a);
+    b = f2_fma(ss, x.y, b);
+  }
+  __device__ float get(int r) const {
+    const float2 p = f2_unpack(r < 2 ? a : b);
+    return (r & 1) ? p.y : p.x;
+  }
+  __device__ void set_vec(const float4& v) {
+    a = f2_pack(v.x, v.y);
+    b = f2_pack(v.z, v.w);
+  }
+  __device__ float4 vec() const {
+    const float2 p = f2_unpack(a), q = f2_unpack(b);
+    return make_float4(p.x, p.y, q.x, q.y);
+  }
+};
+template <>
+struct Acc16<double> {
+  double a, b;
+  __device__ void set(const double* v) {
+    a = v[0];
+    b = v[1];
+  }
+  __device__ void fma(double s, const ulonglong2& x) {
+    a = ::fma(s, __longlong_as_double((long long)x.x), a);
+    b = ::fma(s, __longlong_as_double((long long)x.y), b);
+  }
+  __device__ void fma_pair(unsigned long long s, const ulonglong2& x) { fma(__longlong_as_double((long long)s), x); }
+  __device__ double get(int r) const { return r == 0 ? a : b; }
+  __device__ void set_vec(const double2& v) {
+    a = v.x;
+    b = v.y;
+  }
+  __device__ double2 vec() const { return make_double2(a, b); }
+};
+
+// Row pass: O[u][:] = (D + K_dn) X[u][:] - b O[u][:] for R interleaved rows per step.  The rows
+// are staged in shared memory as 16-byte groups (one per column); each thread owns columns d and
+// gathers the groups sx[col] of its hops.  The slot-major entries (row_ell_pack) carry the byte
+// offsets of the group and of the signed hop value, so a hop costs one table load, two shared
+// loads and the FMAs.  Table loads run one chunk of kPre slots ahead of their use (the table
+// has kEllPad zero slots at its end, so the look-ahead needs no bounds check).
 template <typename T>
 __global__ void __launch_bounds__(kRowThreads) k_down_rows(SectorView sv, HopParams hp, const T* __restrict__ X0,
                                                    T* __restrict__ O0, int64_t vstride, const double* __restrict__ beta,
                                                    int beta_stride, int n_step, const int* __restrict__ active) {
-  using RV = typename Vec<T>::t;
   constexpr int R = Vec<T>::n;
+  constexpr int kPre = kEllPad;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  RV* sx = reinterpret_cast<RV*>(smem_raw);
-  T* sval = reinterpret_cast<T*>(sx + sv.d_dn);
-  T* sU = sval + kMaxVals;
+  unsigned char* sxb = smem_raw;                                  // [d_dn] 16-byte groups
+  T* ssv = reinterpret_cast<T*>(smem_raw + sv.d_dn * 16);         // [256] signed values, (vidx << 1) | neg
+  T* sU = ssv + 256;
   const int run = blockIdx.y;
   if (active && !active[run]) return;
-  for (int i = threadIdx.x; i < kMaxVals; i += blockDim.x) sval[i] = Prec<T>::val(hp, i);
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+    const T v = Prec<T>::val(hp, i >> 1);
+    ssv[i] = (i & 1) ? -v : v;
+  }
   for (int i = threadIdx.x; i < kMaxOrb; i += blockDim.x) sU[i] = Prec<T>::U(hp, i);
+  const T u0 = sizeof(T) == 8 ? (T)hp.u0 : (T)hp.u0f;
+  const bool uni = hp.uniform_u != 0;
   const T* X = X0 + run * vstride;
   T* O = O0 + run * vstride;
   const T b = beta ? (T)beta[(int64_t)run * beta_stride + n_step] : T(0);
   const int64_t du = sv.d_up, dd = sv.d_dn, ld = sv.ld;
   const T* eup = Prec<T>::e_up(sv);
   const T* edn = Prec<T>::e_dn(sv);
-  for (int64_t u0 = (int64_t)blockIdx.x * R; u0 < du; u0 += (int64_t)gridDim.x * R) {
+  const unsigned char* ssvb = reinterpret_cast<const unsigned char*>(ssv);
+  auto hop = [&](Acc16<T>& acc, uint32_t e) {
+    const T v = *reinterpret_cast<const T*>(ssvb + (e & 0x3FCu) * (sizeof(T) / 4));
+    acc.fma(v, *reinterpret_cast<const ulonglong2*>(sxb + (e >> 10)));
+  };
+  for (int64_t u0r = (int64_t)blockIdx.x * R; u0r < du; u0r += (int64_t)gridDim.x * R) {
     __syncthreads();
     for (int64_t d = threadIdx.x; d < dd; d += blockDim.x) {
       T v[R];
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[r] = (u0 + r < du) ? X[(u0 + r) * ld + d] : T(0);
-      sx[d] = Vec<T>::make(v);
+      for (int r = 0; r < R; ++r) v[r] = (u0r + r < du) ? X[(u0r + r) * ld + d] : T(0);
+      *reinterpret_cast<typename Vec<T>::t*>(sxb + d * 16) = Vec<T>::make(v);
     }
     __syncthreads();
     uint32_t bu[R];
     T eu[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      bool ok = u0 + r < du;
-      bu[r] = ok ? sv.B_up[u0 + r] : 0u;
-      eu[r] = ok ? eup[u0 + r] : T(0);
+      bool ok = u0r + r < du;
+      bu[r] = ok ? sv.B_up[u0r + r] : 0u;
+      eu[r] = ok ? eup[u0r + r] : T(0);
     }
     for (int64_t d = threadIdx.x; d < dd; d += blockDim.x) {
+      const int32_t nz = sv.ptr_dn[d + 1] - sv.ptr_dn[d];
+      const uint32_t* p = sv.ell_dn + d;
+      uint32_t e[kPre];
+#pragma unroll
+      for (int i = 0; i < kPre; ++i) e[i] = __ldg(p + i * dd);
+      p += kPre * dd;
       const uint32_t bd = sv.B_dn[d];
       const T ed = edn[d];
-      const RV xv = sx[d];
-      RV acc;
+      Acc16<T> acc;
       {
+        const typename Vec<T>::t xv = *reinterpret_cast<const typename Vec<T>::t*>(sxb + d * 16);
         T a[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           T diag = eu[r] + ed;
           uint32_t dbl = bu[r] & bd & hp.umask;
-          while (dbl) {
-            diag += sU[__ffs(dbl) - 1];
-            dbl &= dbl - 1u;
+          if (uni) {
+            diag += u0 * (T)__popc(dbl);
+          } else {
+            while (dbl) {
+              diag += sU[__ffs(dbl) - 1];
+              dbl &= dbl - 1u;
+            }
           }
           a[r] = diag * Vec<T>::get(xv, r);
         }
-        acc = Vec<T>::make(a);
+        acc.set(a);
       }
-      const int32_t nz = sv.ptr_dn[d + 1] - sv.ptr_dn[d];
-      for (int32_t k = 0; k < nz; ++k) {
-        const uint32_t e = __ldg(sv.ell_dn + (int64_t)k * dd + d);
-        T v = sval[ent_vidx(e)];
-        v = ent_neg(e) ? -v : v;
-        Vec<T>::fma(acc, v, sx[ent_col(e)]);
+      int32_t k = 0;
+      for (; k + kPre <= nz; k += kPre) {
+        uint32_t f[kPre];
+#pragma unroll
+        for (int i = 0; i < kPre; ++i) {
+          f[i] = e[i];
+          e[i] = __ldg(p + i * dd);  // slots k + kPre + i <= zmax + kEllPad - 1
+        }
+        p += kPre * dd;
+#pragma unroll
+        for (int i = 0; i < kPre; ++i) hop(acc, f[i]);
       }
 #pragma unroll
+      for (int i = 0; i < kPre; ++i)
+        if (k + i < nz) hop(acc, e[i]);
+#pragma unroll
       for (int r = 0; r < R; ++r) {
-        if (u0 + r >= du) continue;
-        const int64_t o = (u0 + r) * ld + d;
-        T out = Vec<T>::get(acc, r);
+        if (u0r + r >= du) continue;
+        const int64_t o = (u0r + r) * ld + d;
+        T out = acc.get(r);
         if (beta) out -= b * O[o];
         O[o] = out;
       }
@@ -331,7 +436,7 @@ __global__ void __launch_bounds__(kRowThreads) k_down_rows(SectorView sv, HopPar
 }
 
 template <typename T, bool FUSED>
-__global__ void __launch_bounds__(kThreads) k_up_cols(SectorView sv, HopParams hp, const T* __restrict__ X0,
+__global__ void __launch_bounds__(kThreads, 4) k_up_cols(SectorView sv, HopParams hp, const T* __restrict__ X0,
                                                       T* __restrict__ O0, int64_t vstride, int rows_per_cta, int n,
                                                       LanczosScalars ls) {
   using RV = typename Vec<T>::t;
@@ -347,6 +452,7 @@ __global__ void __launch_bounds__(kThreads) k_up_cols(SectorView sv, HopParams h
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const int64_t ld = sv.ld;
   const int64_t c0 = (int64_t)blockIdx.y * (32 * NV) + lane * NV;
+  const T* Xc = X + c0;
   const int64_t ub = (int64_t)blockIdx.x * rows_per_cta;
   const int64_t ue = ub + rows_per_cta < sv.d_up ? ub + rows_per_cta : sv.d_up;
   Partial3<T> part3;
@@ -354,13 +460,35 @@ __global__ void __launch_bounds__(kThreads) k_up_cols(SectorView sv, HopParams h
     RV* op = reinterpret_cast<RV*>(O + u * ld + c0);
     RV acc = *op;
     const int32_t p0 = sv.ptr_up[u], p1 = sv.ptr_up[u + 1];
-    for (int32_t k = p0; k < p1; ++k) {
-      const uint32_t e = __ldg(sv.ent_up + k);
-      T v = sval[ent_vidx(e)];
-      v = ent_neg(e) ? -v : v;
-      const RV xv = __ldg(reinterpret_cast<const RV*>(X + (int64_t)ent_col(e) * ld + c0));
-      Vec<T>::fma(acc, v, xv);
+    Acc16<T> a16;
+    a16.set_vec(acc);
+    for (int32_t base = p0; base < p1; base += 32) {
+      // the warp's next 32 entries: lane j holds entry base + j (column and signed value)
+      const int cnt = p1 - base < 32 ? p1 - base : 32;
+      const uint32_t me = lane < cnt ? __ldg(sv.ent_up + base + lane) : 0u;
+      const uint32_t mcol = ent_col(me);
+      T mv = sval[ent_vidx(me)];
+      mv = ent_neg(me) ? -mv : mv;
+      int j = 0;
+      for (; j + 4 <= cnt; j += 4) {
+        ulonglong2 xv[4];
+        T v[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const uint32_t col = __shfl_sync(0xffffffffu, mcol, j + i);
+          v[i] = __shfl_sync(0xffffffffu, mv, j + i);
+          xv[i] = __ldg(reinterpret_cast<const ulonglong2*>(Xc + (int64_t)col * ld));
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a16.fma(v[i], xv[i]);
+      }
+      for (; j < cnt; ++j) {
+        const uint32_t col = __shfl_sync(0xffffffffu, mcol, j);
+        const T v = __shfl_sync(0xffffffffu, mv, j);
+        a16.fma(v, __ldg(reinterpret_cast<const ulonglong2*>(Xc + (int64_t)col * ld)));
+      }
     }
+    acc = a16.vec();
     *op = acc;
     if (FUSED) {
       const RV xs = __ldg(reinterpret_cast<const RV*>(X + u * ld + c0));
@@ -411,7 +539,7 @@ static int g_smem_optin = -1;
 
 static size_t down_rows_smem(const SectorView& sv, int dtype) {
   const size_t es = dtype == ED_FP64 ? 8 : 4;
-  return (size_t)sv.d_dn * 16 + (kMaxVals + kMaxOrb) * es;
+  return (size_t)sv.d_dn * 16 + (256 + kMaxOrb) * es;
 }
 
 // The two-pass form applies when the vector does not fit L2 comfortably and the layout allows

@@ -122,13 +122,14 @@ __global__ void k_max_int(const int32_t* __restrict__ v, int64_t n, int* __restr
   if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
-// Slot-major copy of the CSR table: ell[k * dim + r] = k-th entry of row r (0 past its end).
+// Slot-major copy of the CSR table for the row kernel: ell[k * dim + r] = k-th entry of row r
+// in row_ell_pack form (0 past its end).
 __global__ void k_ell_fill(int64_t dim, const int32_t* __restrict__ ptr, const uint32_t* __restrict__ ent, int zmax,
                            uint32_t* __restrict__ ell) {
   int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (r >= dim) return;
   const int32_t p0 = ptr[r], n = ptr[r + 1] - p0;
-  for (int k = 0; k < zmax; ++k) ell[(int64_t)k * dim + r] = k < n ? ent[p0 + k] : 0u;
+  for (int k = 0; k < zmax; ++k) ell[(int64_t)k * dim + r] = k < n ? row_ell_pack(ent[p0 + k]) : 0u;
 }
 
 // Exclusive scan of cnt[0..n) into ptr[0..n] by one block (one-time table construction).
@@ -174,6 +175,50 @@ __global__ void k_ediag(int64_t dim, int L, const uint32_t* __restrict__ basis, 
 }
 
 static inline unsigned nblocks(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+// Slot-major copy of the CSR table (ell[k * dim + r] = an entry of row r, 0 past its end) whose
+// order within each row is chosen against shared-memory bank conflicts of the row kernel: there,
+// the threads of rows 8m .. 8m+7 gather 16-byte words sx[col] together at every slot, and a
+// 16-byte load of 8 threads takes one shared-memory wavefront when their col mod 8 differ.  Per
+// group of 8 rows and per slot, a greedy pass gives each row (fewest remaining entries first) an
+// entry whose col mod 8 is still free at that slot, else any remaining one.  Every row keeps its
+// entry set, so only the order of the additions changes.
+constexpr int64_t kEllOrderMinDim = 2048;
+
+static void ell_bank_order(const std::vector<int32_t>& ptr, const std::vector<uint32_t>& ent, int64_t dim, int zmax,
+                           std::vector<uint32_t>& ell) {
+  ell.assign((size_t)zmax * dim, 0u);
+  std::vector<uint32_t> rem[8];
+  for (int64_t r0 = 0; r0 < dim; r0 += 8) {
+    const int nr = (int)std::min<int64_t>(8, dim - r0);
+    int maxn = 0;
+    for (int i = 0; i < nr; ++i) {
+      rem[i].assign(ent.begin() + ptr[r0 + i], ent.begin() + ptr[r0 + i + 1]);
+      maxn = std::max(maxn, (int)rem[i].size());
+    }
+    int order[8];
+    for (int k = 0; k < maxn; ++k) {
+      for (int i = 0; i < nr; ++i) order[i] = i;
+      std::sort(order, order + nr, [&](int a, int b) { return rem[a].size() < rem[b].size(); });
+      uint32_t used = 0;
+      for (int oi = 0; oi < nr; ++oi) {
+        const int i = order[oi];
+        auto& v = rem[i];
+        if (v.empty()) continue;
+        size_t pick = 0;
+        for (size_t j = 0; j < v.size(); ++j)
+          if (!((used >> (ent_col(v[j]) & 7u)) & 1u)) {
+            pick = j;
+            break;
+          }
+        const uint32_t e = v[pick];
+        used |= 1u << (ent_col(e) & 7u);
+        ell[(size_t)k * dim + r0 + i] = row_ell_pack(e);
+        v.erase(v.begin() + (ptrdiff_t)pick);
+      }
+    }
+  }
+}
 
 std::unique_ptr<SpinTables> build_spin_tables(const ModelHost& m, int N, cudaStream_t s) {
   auto t = std::make_unique<SpinTables>();
@@ -236,8 +281,20 @@ std::unique_ptr<SpinTables> build_spin_tables(const ModelHost& m, int N, cudaStr
     }
     ED_CUDA(cudaMemcpyAsync(&t->zmax, dz.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     ED_CUDA(cudaStreamSynchronize(s));
-    t->ell.alloc(std::max<int64_t>((int64_t)t->zmax * dim, 1));
-    if (dim > 0 && t->zmax > 0) {
+    t->ell.alloc(std::max<int64_t>((int64_t)(t->zmax + kEllPad) * dim, 1));
+    ED_CUDA(cudaMemsetAsync(t->ell.p, 0, (size_t)(t->zmax + kEllPad) * dim * sizeof(uint32_t), s));
+    if (dim >= kEllOrderMinDim && t->zmax > 0) {
+      // large sectors: slot order chosen on the host against shared-memory bank conflicts
+      std::vector<int32_t> hptr(dim + 1);
+      std::vector<uint32_t> hent(std::max<int64_t>(nnz, 1));
+      ED_CUDA(cudaMemcpyAsync(hptr.data(), t->ptr.p, (dim + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      ED_CUDA(cudaMemcpyAsync(hent.data(), t->ent.p, std::max<int64_t>(nnz, 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+      ED_CUDA(cudaStreamSynchronize(s));
+      std::vector<uint32_t> hell;
+      ell_bank_order(hptr, hent, dim, t->zmax, hell);
+      ED_CUDA(cudaMemcpyAsync(t->ell.p, hell.data(), hell.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+      ED_CUDA(cudaStreamSynchronize(s));
+    } else if (dim > 0 && t->zmax > 0) {
       { ProfScope ps_(K_TABLES, s, 0.0); k_ell_fill<<<nblocks(dim, bs), bs, 0, s>>>(dim, t->ptr.p, t->ent.p, t->zmax, t->ell.p); }
       ED_CHECK_LAUNCH();
     }

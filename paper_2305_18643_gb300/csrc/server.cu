@@ -54,7 +54,7 @@ size_t spin_table_bytes(int L, int N, int npairs) {
   const int64_t d = (int64_t)binomial(L, N);
   const int split = L / 2;
   const int64_t nnz = (int64_t)npairs * (int64_t)binomial(L - 2, N - 1);
-  const int64_t zmax = std::min<int64_t>(npairs, (int64_t)N * (L - N));
+  const int64_t zmax = std::min<int64_t>(npairs, (int64_t)N * (L - N)) + kEllPad;
   return (size_t)d * (4 + 4 + 8 + 4) + 4 + (size_t)std::max<int64_t>(nnz, 1) * 4 + (size_t)zmax * d * 4 +
          ((size_t(1) << split) + (size_t(1) << (L - split))) * 4 + 4096;
 }
