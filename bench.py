@@ -79,6 +79,22 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(x, world, device):
+    """The largest x over all ranks (the timed region of the slowest rank); x itself at N = 1."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, ms):
+    """Units processed by all ranks per second of the slowest rank's timed region (weak scaling:
+    every rank solves its own seeded instances, no data exchange)."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 # ----------------------------------------------------------------------------- measurement helpers
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
@@ -210,12 +226,8 @@ def run_ours(args, rank, world, local_rank):
             solve(to_host)
         e1.record()
         barrier()
-        ms = e0.elapsed_time(e1)
+        ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
         launches = ed.ed_launch_count() - launches0
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
         return ms, launches
 
     for _ in range(args.warmup):
@@ -227,10 +239,10 @@ def run_ours(args, rank, world, local_rank):
     e2e = None
     if not args.no_e2e:
         ms_e2e, _ = timed(True, args.steps, False)
-        e2e = {"value": world * args.steps / (ms_e2e / 1e3), "unit": "solves/s",
+        e2e = {"value": whole_job_rate(args.steps, world, ms_e2e), "unit": "solves/s",
                "h2d_bytes_per_step": int(8 * (ns * ns + ns + len(c["eps"]) + c["theta"].size + 1)),
                "d2h_bytes_per_step": int(nfreq * ns * ns * 16 if gf != "none" else 0) + 8}
-    value = world * args.steps / (ms / 1e3)
+    value = whole_job_rate(args.steps, world, ms)
     n_step, ms_step, by_step = prof[ed.ED_K_LANCZOS_STEP]
     peak, peak_kind = measured_peak_hbm()
     achieved = (by_step / 1e9) / (ms_step / 1e3) if ms_step > 0 else None
@@ -301,11 +313,7 @@ def run_batch(args, rank, world, local_rank, torch, ed):
             solve(to_host)
         e1.record()
         barrier()
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
         return ms, ed.ed_launch_count() - l0
 
     for _ in range(args.warmup):
@@ -317,7 +325,7 @@ def run_batch(args, rank, world, local_rank, torch, ed):
     e2e = None
     if not args.no_e2e:
         ms_e2e, _ = timed(True, args.steps, False)
-        e2e = {"value": world * len(fam) * args.steps / (ms_e2e / 1e3), "unit": "cluster solves/s",
+        e2e = {"value": whole_job_rate(len(fam) * args.steps, world, ms_e2e), "unit": "cluster solves/s",
                "h2d_bytes_per_step": int(sum(8 * (c["t"].size + c["t"].shape[0] + c["eps"].size + c["theta"].size + 1)
                                              for c in fam)),
                "d2h_bytes_per_step": int(gsize * 16 + len(fam) * 8 * 4)}
@@ -331,7 +339,7 @@ def run_batch(args, rank, world, local_rank, torch, ed):
     achieved = (gs_bytes * args.steps / 1e9) / (ms_b / 1e3) if ms_b > 0 else None
     result = {
         "metric": "ED solves/s (batched form; H.psi GB/s and % roofline in `roofline`)",
-        "value": world * len(fam) * args.steps / (ms / 1e3), "unit": "cluster solves/s", "n_gpus": world,
+        "value": whole_job_rate(len(fam) * args.steps, world, ms), "unit": "cluster solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 vectors, f64 reductions" if prec == "fp32" else "f64", "data": "synthetic (seeded cluster parameters)",
@@ -459,12 +467,9 @@ def run_served(args, rank, world, local_rank, torch, ed):
     launches = ed.ed_launch_count() - l0
     prof = {k: ed.ed_profile_read(k) for k in range(ed.ED_K_COUNT)}
     ed.ed_profile_enable(0)
-    if world > 1:
-        t = torch.tensor([wall], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        wall = float(t.item())
+    wall = max_over_ranks(wall, world, "cuda")
     n_req = args.requests * args.steps
-    value = world * n_req / wall
+    value = whole_job_rate(n_req, world, 1e3 * wall)
     lat = np.array([r["latency_ms"] for r in all_res])
     # Poisson streams at multiples of the sequential FP64 rate
     sweep = []

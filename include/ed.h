@@ -137,10 +137,12 @@ ed_status ed_green_stats(const ed_cluster* c, int64_t* total_steps, int* max_ste
  *    ED_WARN_DEGENERATE or ED_WARN_NOT_CONVERGED.
  *  - G_out: complex128 (2 doubles each), clusters one after the other, cluster c holding
  *    [2 spins][n_freq][n_sites_c][n_sites_c]; host or device memory as out_is_device says.
- * Tables, ground states and continued fractions of all clusters are built by a few launches:
- * persistent kernels in which every thread block takes the next cluster (or continued fraction)
- * from a queue, largest first.  The block width and the mapping of the block-level H.psi are
- * picked by timing candidates on the first call for a batch shape (then cached). */
+ * Tables of all clusters are built by three launches; the solve proper is one CUDA graph: a
+ * persistent ground-state kernel and a persistent continued-fraction kernel, in which every
+ * thread block takes the next cluster (or continued fraction) from a queue, largest first, then
+ * the evaluation on the grid and the assembly of G.  The block width and the mapping of the
+ * block-level H.psi are picked by timing candidates on the first call for a batch shape (then
+ * cached). */
 ed_status ed_batch_solve(const ed_cluster_desc* descs, int n, int precision, const double* omega, int n_freq,
                          double eta, int axis, int cf_max_levels, double* E0, double* residual, int* status, int* iters,
                          int64_t* gf_steps, double* G_out, int out_is_device);

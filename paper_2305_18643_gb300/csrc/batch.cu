@@ -689,22 +689,44 @@ struct BatchResult {
 };
 
 // Runs the persistent ground-state and continued-fraction kernels with `threads` per block.
+// (prof: time each launch with the profiler; off while the launches are captured into a graph)
 template <typename T>
 static void run_batch_kernels(int threads, int mode, BCluster* C, const int* corder, int nclu, const BTable* tabs,
                               BRun* R, const int* rorder, int nruns, int* queues, const BWork& w, int blocks,
-                              const double2* z, int nz, double tol, bool do_gf, cudaStream_t s) {
+                              const double2* z, int nz, double tol, bool do_gf, cudaStream_t s, bool prof = true) {
   ED_CUDA(cudaMemsetAsync(queues, 0, 2 * sizeof(int), s));
   {
-    ProfScope ps_(K_BATCH, s, 0.0);
+    std::unique_ptr<ProfScope> ps_(prof ? new ProfScope(K_BATCH, s, 0.0) : nullptr);
     k_batch_gs<T><<<blocks, threads, 0, s>>>(C, corder, nclu, tabs, queues, w, mode);
     ED_CHECK_LAUNCH();
   }
   if (do_gf && nruns > 0) {
-    ProfScope ps_(K_BATCH, s, 0.0);
+    std::unique_ptr<ProfScope> ps_(prof ? new ProfScope(K_BATCH, s, 0.0) : nullptr);
     k_batch_cf<T><<<blocks, threads, 0, s>>>(R, rorder, nruns, C, tabs, queues + 1, w, z, nz, tol, mode);
     ED_CHECK_LAUNCH();
   }
 }
+
+// Ends a stream capture left open by an exception (the stream is usable again afterwards).
+struct CaptureGuard {
+  cudaStream_t s;
+  bool open = true;
+  ~CaptureGuard() {
+    if (!open) return;
+    cudaGraph_t g = nullptr;
+    cudaStreamEndCapture(s, &g);
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+  }
+};
+struct GraphHolder {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t x = nullptr;
+  ~GraphHolder() {
+    if (x) cudaGraphExecDestroy(x);
+    if (g) cudaGraphDestroy(g);
+  }
+};
 
 // Device bytes batch_solve allocates for these clusters (tables, ground states, continued-fraction
 // coefficients, evaluated fractions and the per-block workspace; the caller's G not included).
@@ -1000,29 +1022,39 @@ void batch_solve(const ed_cluster_desc* descs, int n, int precision, const doubl
     g_tune[key] = cfg;
   }
   const double gtol = precision == ED_FP64 ? 1e-10 : 1e-6;
-  if (precision == ED_FP64)
-    run_batch_kernels<double>(cfg.first, cfg.second, dC.p, dCo.p, n, dT.p, dR.p, dRo.p, nruns, dQ.p, w, blocks,
-                              dz.p, nz, gtol, do_gf, s);
-  else
-    run_batch_kernels<float>(cfg.first, cfg.second, dC.p, dCo.p, n, dT.p, dR.p, dRo.p, nruns, dQ.p, w, blocks,
-                             dz.p, nz, gtol, do_gf, s);
-  if (do_gf && nruns > 0) {
-    {
-      ProfScope ps_(K_GF_EVAL, s, 0.0);
+  // The solve proper is one CUDA graph: queue reset, the persistent ground-state and
+  // continued-fraction kernels, evaluation on the grid and assembly of G.
+  std::vector<int64_t> goff(n + 1, 0);
+  for (int c = 0; c < n; ++c) goff[c + 1] = goff[c] + (int64_t)2 * nz * C[c].ns * C[c].ns;
+  DevBuf<int64_t> dgoff(n + 1);
+  ED_CUDA(cudaMemcpyAsync(dgoff.p, goff.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  const bool gf = do_gf && nruns > 0;
+  GraphHolder graph;
+  {
+    CaptureGuard cg{s};
+    ED_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    if (precision == ED_FP64)
+      run_batch_kernels<double>(cfg.first, cfg.second, dC.p, dCo.p, n, dT.p, dR.p, dRo.p, nruns, dQ.p, w, blocks,
+                                dz.p, nz, gtol, do_gf, s, false);
+    else
+      run_batch_kernels<float>(cfg.first, cfg.second, dC.p, dCo.p, n, dT.p, dR.p, dRo.p, nruns, dQ.p, w, blocks,
+                               dz.p, nz, gtol, do_gf, s, false);
+    if (gf) {
       k_bcf_eval<<<dim3((nz + 255) / 256, std::min(nruns, 32768)), 256, 0, s>>>(dR.p, nruns, dC.p, dz.p, nz, Gk);
       ED_CHECK_LAUNCH();
-    }
-    std::vector<int64_t> goff(n + 1, 0);
-    for (int c = 0; c < n; ++c) goff[c + 1] = goff[c] + (int64_t)2 * nz * C[c].ns * C[c].ns;
-    DevBuf<int64_t> dgoff(n + 1);
-    ED_CUDA(cudaMemcpyAsync(dgoff.p, goff.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    {
-      ProfScope ps_(K_GF_EVAL, s, 0.0);
       k_bcombine<<<dim3(64, std::min(n, 32768)), 256, 0, s>>>(dC.p, n, dBase.p, dgoff.p, Gk, nz, G_dev_out);
       ED_CHECK_LAUNCH();
     }
-    ED_CUDA(cudaStreamSynchronize(s));
+    cg.open = false;
+    ED_CUDA(cudaStreamEndCapture(s, &graph.g));
   }
+  ED_CUDA(cudaGraphInstantiate(&graph.x, graph.g, 0));
+  {
+    ProfScope ps_(K_BATCH, s, 0.0);  // counts the graph as one launch of the persistent kernels
+    ED_CUDA(cudaGraphLaunch(graph.x, s));
+  }
+  for (int k = 0; k < (gf ? 3 : 0); ++k) note_launch();  // its other kernels
+  ED_CUDA(cudaStreamSynchronize(s));
   // ---- results
   ED_CUDA(cudaMemcpyAsync(C.data(), dC.p, n * sizeof(BCluster), cudaMemcpyDeviceToHost, s));
   std::vector<BRun> Rh(nruns);
