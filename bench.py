@@ -42,6 +42,8 @@ WORKLOADS = {
             "fp32", "band", 1000),
     "cdmft": (W.cdmft_2x2_bath, "2x2 plaquette + 8 bath, U=8, mu=4, N_up=N_dn=6 (d=924^2)", "fp32", "cf", 1000),
     "2x4": (lambda instance=0: W.plain_2x4(), "2x4 open Hubbard, U=4, mu=2, N_up=N_dn=4 (d=70^2)", "fp64", "cf", 1000),
+    "2x7": (lambda instance=0: W.served_request(np.random.default_rng(20230529 + 7000 + instance), sizes=(14,)),
+            "2x7 open Hubbard, t=-1, t'=+-0.3 seeded, U=8, mu=4, N_up=N_dn=7 (d=3432^2)", "fp32", "band", 1000),
     "batch": (lambda instance=0: W.batched_family(512, instance=instance),
               "512 seeded clusters of 4-12 orbitals (chains, 2-leg ladders, 2x2 plaquettes + 0-8 bath), "
               "|t| ~ U[0.5,1.5], U ~ U[2,10], mu = U/2, random fillings; both spins", "fp32", "cf", 512),
@@ -52,7 +54,7 @@ WORKLOADS = {
 }
 ETA = 0.05
 # Krylov vectors per part of the band Green function: the paper's runs stop at R = 100-500 (Sec. 4.4)
-BAND_MAX_DIM = {"4x4": 512}
+BAND_MAX_DIM = {"4x4": 512, "2x7": 512}
 
 
 def parse():

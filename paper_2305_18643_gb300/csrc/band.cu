@@ -54,105 +54,6 @@ struct GAcc<float> {
   __device__ double get() const { return (double)s - (double)k; }
 };
 
-// blockIdx.y selects a block of X (X + blockIdx.y * xbstride); partial sums per CTA.
-// Gram partial sums, register-tiled: each thread owns a 4 x 4 tile of pairs (i, j) and a slice
-// of the kTile elements staged in shared memory, so 8 shared loads feed 16 multiply-adds.  The
-// slices are added in a fixed order at the end (deterministic).  X blocks: X0 + b * xbstride,
-// or (xbstride == 0) X0 for b = 0 and X1 for b = 1.
-template <typename T>
-__global__ void __launch_bounds__(kGT2) k_gram_partial(const T* __restrict__ X0, const T* __restrict__ X1,
-                                                       int64_t xbstride, int px, const T* __restrict__ Y, int py,
-                                                       int64_t vstride, int64_t n, double* __restrict__ P) {
-  extern __shared__ __align__(16) unsigned char gsm[];
-  T(*sx)[kTile + 1] = reinterpret_cast<T(*)[kTile + 1]>(gsm);
-  T(*sy)[kTile + 1] = reinterpret_cast<T(*)[kTile + 1]>(gsm + sizeof(T) * kBP * (kTile + 1));
-  double* red = reinterpret_cast<double*>(gsm);  // reused after the element loop: [kGT2][16]
-  const T* X = xbstride ? X0 + blockIdx.y * xbstride : (blockIdx.y == 0 ? X0 : X1);
-  const int TI = (px + 3) / 4, TJ = (py + 3) / 4, ntile = TI * TJ;
-  const int nslice = kGT2 / ntile;
-  const int q = threadIdx.x % ntile, sl = threadIdx.x / ntile;
-  const bool worker = sl < nslice;
-  const int ti = q / TJ, tj = q - ti * TJ;
-  GAcc<T> acc[4][4];
-  // thread t stages element e = t % kTile of rows i = t / kTile + 4 m, m < 8 (kGT2 = 4 kTile);
-  // the next tile is fetched into registers while the current one is multiplied.
-  constexpr int kRowsPerPass = kGT2 / kTile;
-  constexpr int kPasses = kBP / kRowsPerPass;
-  const int e_ld = threadIdx.x % kTile, i_ld = threadIdx.x / kTile;
-  T rx[kPasses], ry[kPasses];
-  auto fetch = [&](int64_t o0) {
-    const int64_t o = o0 + e_ld;
-    const bool ok = o < n;
-#pragma unroll
-    for (int m = 0; m < kPasses; ++m) {
-      const int i = i_ld + kRowsPerPass * m;
-      rx[m] = (ok && i < px) ? X[i * vstride + o] : T(0);
-      ry[m] = (ok && i < py) ? Y[i * vstride + o] : T(0);
-    }
-  };
-  int64_t o0 = (int64_t)blockIdx.x * kTile;
-  if (o0 < n) fetch(o0);
-  for (; o0 < n; o0 += (int64_t)gridDim.x * kTile) {
-    __syncthreads();
-#pragma unroll
-    for (int m = 0; m < kPasses; ++m) {
-      sx[i_ld + kRowsPerPass * m][e_ld] = rx[m];
-      sy[i_ld + kRowsPerPass * m][e_ld] = ry[m];
-    }
-    __syncthreads();
-    if (o0 + (int64_t)gridDim.x * kTile < n) fetch(o0 + (int64_t)gridDim.x * kTile);
-    if (worker) {
-      T part[4][4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) part[a][b] = T(0);
-      for (int e = sl; e < kTile; e += nslice) {
-        T xv[4], yv[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          xv[a] = 4 * ti + a < px ? sx[4 * ti + a][e] : T(0);
-          yv[a] = 4 * tj + a < py ? sy[4 * tj + a][e] : T(0);
-        }
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) part[a][b] += xv[a] * yv[b];
-      }
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b].add(part[a][b]);
-    }
-  }
-  __syncthreads();
-  if (worker) {
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) red[threadIdx.x * 16 + a * 4 + b] = acc[a][b].get();
-  }
-  __syncthreads();
-  const int npair = px * py;
-  const int64_t base = ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * npair;
-  for (int t = threadIdx.x; t < npair; t += blockDim.x) {
-    const int i = t / py, j = t - i * py;
-    const int qq = (i / 4) * TJ + (j / 4), ab = (i % 4) * 4 + (j % 4);
-    double v = 0.0;
-    for (int k = 0; k < nslice; ++k) v += red[(k * ntile + qq) * 16 + ab];
-    P[base + t] = v;
-  }
-}
-
-__global__ void k_gram_finish(const double* __restrict__ P, int nchunk, int npair, double* __restrict__ G) {
-  // blockIdx.x: X block; thread: pair
-  const int b = blockIdx.x;
-  for (int t = threadIdx.x; t < npair; t += blockDim.x) {
-    double s = 0.0;
-    for (int c = 0; c < nchunk; ++c) s += P[((int64_t)b * nchunk + c) * npair + t];
-    G[(int64_t)b * npair + t] = s;
-  }
-}
 
 template <typename T>
 struct VE;
@@ -160,12 +61,193 @@ template <>
 struct VE<float> {
   using v = float4;
   static constexpr int n = 4;
+  __device__ static float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 };
 template <>
 struct VE<double> {
   using v = double2;
   static constexpr int n = 2;
+  __device__ static double2 zero() { return make_double2(0.0, 0.0); }
 };
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+// 16-byte copy reading src_bytes (0 or 16) from global memory and zero-filling the rest.
+__device__ __forceinline__ void cp_async16_zfill(void* smem, const void* gmem, int src_bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+constexpr int kGramStages = 6;       // tiles staged per CTA (5 in flight while one is used)
+constexpr int kGramTilesPerCta = 16; // 4 x 4 pair tiles per CTA (one per warp); more go to blockIdx.z
+constexpr int kGramThreads = 32 * kGramTilesPerCta;
+
+// Products of two 16-byte groups added to a pair's partial sum: FP32 as a packed pair of partial
+// sums (fma.rn.f32x2 on (x, y) and (z, w)), FP64 as one sum.
+struct GPart32 {
+  unsigned long long v = 0ull;  // two FP32 partial sums
+  __device__ void fma(const float4& a, const float4& b) {
+    unsigned long long a0, a1, b0, b1;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(a0) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(a1) : "f"(a.z), "f"(a.w));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(b0) : "f"(b.x), "f"(b.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(b1) : "f"(b.z), "f"(b.w));
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(v) : "l"(a0), "l"(b0));
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(v) : "l"(a1), "l"(b1));
+  }
+  __device__ float take() {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+    v = 0ull;
+    return lo + hi;
+  }
+};
+struct GPart64 {
+  double v = 0.0;
+  __device__ void fma(const double2& a, const double2& b) {
+    v = ::fma(a.x, b.x, v);
+    v = ::fma(a.y, b.y, v);
+  }
+  __device__ double take() {
+    const double r = v;
+    v = 0.0;
+    return r;
+  }
+};
+template <typename T>
+struct GPartOf;
+template <>
+struct GPartOf<float> {
+  using t = GPart32;
+};
+template <>
+struct GPartOf<double> {
+  using t = GPart64;
+};
+
+// Gram G_b[i][j] = sum_e X_b,i[e] Y_j[e] (i < px, j < py <= 32; blockIdx.y = b selects the X
+// block: X0 + b xbstride, or X0 / X1 when xbstride == 0; blockIdx.z a group of 16 pair tiles of
+// 4 x 4).  Every CTA takes a contiguous chunk of elements (whole tiles of 32 x GR 16-byte groups)
+// and copies each tile's rows (X_b, then Y unless sym, where Y is X_b) to shared memory with
+// cp.async, kGramStages tiles in flight.  A warp owns one pair tile of its group and multiplies
+// it over the tile, GR 16-byte groups per lane (rows padded by 16 bytes: conflict-free 16-byte
+// shared loads).  Products are summed per pair over kGramFlush tiles (FP32: packed FMAs), then
+// added with compensation; lanes, chunks and blocks are added in a fixed order, the chunks by
+// the last CTA of each X block (a ticket), so the result is deterministic.
+constexpr int kGramFlush = 4;
+template <typename T, int GR>
+__global__ void __launch_bounds__(kGramThreads, 1) k_gram(const T* __restrict__ X0, const T* __restrict__ X1,
+                                                         int64_t xbstride, int px, const T* __restrict__ Y, int py,
+                                                         int sym, int64_t vstride, int64_t n, int64_t chunk,
+                                                         double* __restrict__ P, unsigned* __restrict__ ticket,
+                                                         double* __restrict__ G) {
+  using V = typename VE<T>::v;
+  using Part = typename GPartOf<T>::t;
+  constexpr int VN = VE<T>::n;    // elements per 16-byte group
+  constexpr int E = 32 * GR * VN; // elements per tile
+  constexpr int RS = E + VN;      // padded row stride (elements)
+  extern __shared__ __align__(16) unsigned char gsm[];
+  T* buf = reinterpret_cast<T*>(gsm);
+  __shared__ bool s_last;
+  const int nrow = px + (sym ? 0 : py);
+  const int yoff = sym ? 0 : px;
+  const T* X = xbstride ? X0 + blockIdx.y * xbstride : (blockIdx.y == 0 ? X0 : X1);
+  const T* Yp = sym ? X : Y;
+  const int64_t e_begin = (int64_t)blockIdx.x * chunk;
+  const int64_t e_end = e_begin + chunk < n ? e_begin + chunk : n;
+  const int ntile = e_begin < e_end ? (int)((e_end - e_begin + E - 1) / E) : 0;  // the last may be partial
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int TI = (px + 3) / 4, TJ = (py + 3) / 4;
+  const int q0 = blockIdx.z * kGramTilesPerCta + warp;
+  const bool h0 = q0 < TI * TJ;
+  const int ti0 = h0 ? q0 / TJ : 0, tj0 = h0 ? q0 % TJ : 0;
+  auto stage = [&](int t) {
+    if (t < ntile) {
+      const int64_t e0 = e_begin + (int64_t)t * E;
+      T* dst = buf + (size_t)(t % kGramStages) * nrow * RS;
+      for (int q = threadIdx.x; q < nrow * 32 * GR; q += blockDim.x) {
+        const int r = q / (32 * GR), g = q - r * (32 * GR);
+        const int64_t e = e0 + g * VN;  // groups past n (ragged last tile) are zero-filled
+        const T* src = (r < px ? X + (int64_t)r * vstride : Yp + (int64_t)(r - px) * vstride) + (e < n ? e : 0);
+        cp_async16_zfill(dst + r * RS + g * VN, src, e < n ? 16 : 0);
+      }
+    }
+    cp_async_commit();  // an empty group past the end keeps the wait count uniform
+  };
+  GAcc<T> acc0[16];
+  Part part0[16];
+  // rows of the pair tile (rows past px / py read row 0; those pairs are not written)
+  int xr0[4], yr0[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    xr0[a] = (4 * ti0 + a < px ? 4 * ti0 + a : 0) * RS;
+    yr0[a] = (4 * tj0 + a < py ? yoff + 4 * tj0 + a : 0) * RS;
+  }
+#pragma unroll
+  for (int t = 0; t < kGramStages - 1; ++t) stage(t);
+  for (int t = 0; t < ntile; ++t) {
+    stage(t + kGramStages - 1);
+    cp_async_wait<kGramStages - 1>();
+    __syncthreads();
+    const T* b = buf + (size_t)(t % kGramStages) * nrow * RS + lane * VN;
+    if (h0) {
+#pragma unroll
+      for (int g = 0; g < GR; ++g) {
+        const T* bg = b + g * 32 * VN;
+        V xv[4], yv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          xv[a] = *reinterpret_cast<const V*>(bg + xr0[a]);
+          yv[a] = *reinterpret_cast<const V*>(bg + yr0[a]);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) part0[a * 4 + c].fma(xv[a], yv[c]);
+      }
+      if ((t % kGramFlush) == kGramFlush - 1 || t + 1 == ntile) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) acc0[k].add(part0[k].take());
+      }
+    }
+    __syncthreads();  // the buffer of tile t is refilled by stage(t + kGramStages) next round
+  }
+  cp_async_wait<0>();
+  const int npair = px * py;
+  double* Pc = P + ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * npair;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    double v0 = acc0[k].get();
+    for (int o = 16; o > 0; o >>= 1) v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+    if (lane == 0) {
+      const int a = k >> 2, c = k & 3;
+      if (h0 && 4 * ti0 + a < px && 4 * tj0 + c < py) Pc[(4 * ti0 + a) * py + 4 * tj0 + c] = v0;
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned t = atomicAdd(ticket + blockIdx.y, 1u);
+    s_last = (t == gridDim.x * gridDim.z - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const double* Pb = P + (int64_t)blockIdx.y * gridDim.x * npair;
+  for (int q = threadIdx.x; q < npair; q += blockDim.x) {
+    double v = 0.0;
+    for (unsigned c = 0; c < gridDim.x; ++c) v += __ldcg(Pb + (int64_t)c * npair + q);
+    G[(int64_t)blockIdx.y * npair + q] = v;
+  }
+  if (threadIdx.x == 0) ticket[blockIdx.y] = 0u;
+}
 
 // Y_j[o] (mode 0: =, 1: -=) sum_k X_k[o] C[k][j] for k < K = nb * px, j < py <= PY.  Each thread
 // owns one 16-byte group of elements and all PY outputs in registers; the coefficients are
@@ -443,21 +525,47 @@ static int g_grid(int64_t n, int per) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
 }
 
-template <typename T>
-static void gram(const T* X, const T* X1, int64_t xbstride, int nb, int px, const T* Y, int py, int64_t vstride,
-                 int64_t n, DevBuf<double>& P, double* G, cudaStream_t s) {
-  const int nchunk = (int)std::min<int64_t>((n + kTile - 1) / kTile, 152 * 8);
+// G[b][i][j] = <X_b,i, Y_j> for the nb blocks of X (n elements per vector, a multiple of 128).
+template <typename T, int GR>
+static void gram_launch(const T* X, const T* X1, int64_t xbstride, int nb, int px, const T* Y, int py, bool sym,
+                        int64_t vstride, int64_t n, DevBuf<double>& P, DevBuf<unsigned>& tk, double* G, cudaStream_t s) {
+  constexpr int E = 32 * GR * VE<T>::n;
+  const int ntiles_pair = ((px + 3) / 4) * ((py + 3) / 4);
+  const int gz = (ntiles_pair + kGramTilesPerCta - 1) / kGramTilesPerCta;
+  int sms = 152, dev = 0;
+  ED_CUDA(cudaGetDevice(&dev));
+  ED_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t tiles = (n + E - 1) / E;
+  const int nchunk = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, std::max(1, sms / (nb * gz))));
+  const int64_t chunk = (tiles + nchunk - 1) / nchunk * E;
   const int npair = px * py;
   if (P.n < (size_t)nb * nchunk * npair) P.alloc((size_t)nb * nchunk * npair);
-  const size_t smem = std::max(2 * sizeof(T) * kBP * (kTile + 1), sizeof(double) * kGT2 * 16);
-  {
-    ProfScope ps_(K_BAND, s, 0.0);
-    k_gram_partial<T><<<dim3(nchunk, nb), kGT2, smem, s>>>(X, X1, xbstride, px, Y, py, vstride, n, P.p);
-    ED_CHECK_LAUNCH();
+  if (tk.n < (size_t)nb) {
+    tk.alloc((size_t)nb);
+    ED_CUDA(cudaMemsetAsync(tk.p, 0, (size_t)nb * sizeof(unsigned), s));
   }
+  const int nrow = px + (sym ? 0 : py);
+  const size_t smem = (size_t)kGramStages * nrow * (E + VE<T>::n) * sizeof(T);
+  ED_CUDA(cudaFuncSetAttribute(k_gram<T, GR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ProfScope ps_(K_BAND, s, 0.0);
-  k_gram_finish<<<nb, 256, 0, s>>>(P.p, nchunk, npair, G);
+  k_gram<T, GR><<<dim3(nchunk, nb, gz), kGramThreads, smem, s>>>(X, X1, xbstride, px, Y, py, sym ? 1 : 0, vstride, n, chunk,
+                                                        P.p, tk.p, G);
   ED_CHECK_LAUNCH();
+}
+
+template <typename T>
+static void gram(const T* X, const T* X1, int64_t xbstride, int nb, int px, const T* Y, int py, int64_t vstride,
+                 int64_t n, DevBuf<double>& P, DevBuf<unsigned>& tk, double* G, cudaStream_t s) {
+  const bool sym = nb == 1 && xbstride == 0 && X == Y && px == py;
+  const int nrow = px + (sym ? 0 : py);
+  // 16-byte groups per lane per tile: tiles of at most 32 KB, so kGramStages of them fit shared
+  // memory and ~160 KB are in flight per SM
+  if (nrow <= 16)
+    gram_launch<T, 4>(X, X1, xbstride, nb, px, Y, py, sym, vstride, n, P, tk, G, s);
+  else if (nrow <= 32)
+    gram_launch<T, 2>(X, X1, xbstride, nb, px, Y, py, sym, vstride, n, P, tk, G, s);
+  else
+    gram_launch<T, 1>(X, X1, xbstride, nb, px, Y, py, sym, vstride, n, P, tk, G, s);
 }
 
 template <typename T, int PY>
@@ -531,6 +639,7 @@ static bool band_part(ed_cluster& c, int spin, bool electron, const DevBuf<doubl
   double scale2 = 1.0;
   DevBuf<double> A((size_t)kmax * pp), B((size_t)kmax * pp), R0(pp), G((size_t)(kmax + 2) * pp), Cm(pp), Bm(pp),
       C2(pp), B2(pp), tmp(pp), P;
+  DevBuf<unsigned> gtk;  // tickets of the Gram kernel (zeroed at allocation, reset by its last CTA)
   DevBuf<int> rank(1);
   ED_CUDA(cudaMemsetAsync(A.p, 0, (size_t)kmax * pp * sizeof(double), s));
   ED_CUDA(cudaMemsetAsync(B.p, 0, (size_t)kmax * pp * sizeof(double), s));
@@ -545,26 +654,25 @@ static bool band_part(ed_cluster& c, int spin, bool electron, const DevBuf<doubl
   for (double v : c.model.h) hscale = std::max(hscale, std::fabs(v));
   for (double v : c.model.U) hscale = std::max(hscale, std::fabs(v));
   const double eps_rel = dtype == ED_FP64 ? 1e-10 : 1e-4;
-  auto orthonormalize = [&](double scale2, double* Bfinal) -> int {
-    // two SVQB passes: W = X (B2 B1)
+  auto orthonormalize = [&](double scale2, double* Bfinal, T* dst) -> int {
+    // two SVQB passes: W = X (B2 B1); the second writes the orthonormal block into dst
     int r = 0;
-    gram<T>(Wb.p, nullptr, 0, 1, p, Wb.p, p, vstride, n, P, G.p, s);
+    gram<T>(Wb.p, nullptr, 0, 1, p, Wb.p, p, vstride, n, P, gtk, G.p, s);
     { ProfScope ps_(K_BAND, s, 0.0); k_svqb<<<1, 32, 0, s>>>(G.p, p, eps_rel * eps_rel * scale2, Cm.p, Bm.p, rank.p); }
     ED_CHECK_LAUNCH();
     block_axpy<T>(Wb.p, p, Wb.p, nullptr, 0, 1, p, Cm.p, vstride, n, 0, s);
-    gram<T>(Wb.p, nullptr, 0, 1, p, Wb.p, p, vstride, n, P, G.p, s);
+    gram<T>(Wb.p, nullptr, 0, 1, p, Wb.p, p, vstride, n, P, gtk, G.p, s);
     { ProfScope ps_(K_BAND, s, 0.0); k_svqb<<<1, 32, 0, s>>>(G.p, p, 0.25, C2.p, B2.p, rank.p); }
     ED_CHECK_LAUNCH();
-    block_axpy<T>(Wb.p, p, Wb.p, nullptr, 0, 1, p, C2.p, vstride, n, 0, s);
+    block_axpy<T>(dst, p, Wb.p, nullptr, 0, 1, p, C2.p, vstride, n, 0, s);
     { ProfScope ps_(K_BAND, s, 0.0); k_small_gemm<<<1, 256, 0, s>>>(B2.p, Bm.p, p, 0, Bfinal, 1.0); }
     ED_CHECK_LAUNCH();
     ED_CUDA(cudaMemcpyAsync(&r, rank.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     ED_CUDA(cudaStreamSynchronize(s));
     return r;
   };
-  orthonormalize(1.0, R0.p);
+  orthonormalize(1.0, R0.p, Xb(0));
   scale2 = hscale * hscale;
-  ED_CUDA(cudaMemcpyAsync(Xb(0), Wb.p, blk * sizeof(T), cudaMemcpyDeviceToDevice, s));
   // check grid (every zstride-th frequency)
   const int zstride = std::max(1, nz / 512);
   const int nzc = (nz + zstride - 1) / zstride;
@@ -586,15 +694,15 @@ static bool band_part(ed_cluster& c, int spin, bool electron, const DevBuf<doubl
       int nbk;
       if (full) {
         nbk = j + 1;
-        gram<T>(Xb(0), nullptr, blk, nbk, p, Wb.p, p, vstride, n, P, G.p, s);
+        gram<T>(Xb(0), nullptr, blk, nbk, p, Wb.p, p, vstride, n, P, gtk, G.p, s);
         block_axpy<T>(Wb.p, p, Xb(0), nullptr, blk, nbk, p, G.p, vstride, n, 1, s);
       } else if (j > 0) {
         nbk = 2;
-        gram<T>(Xb(j - 1), Xb(j), 0, 2, p, Wb.p, p, vstride, n, P, G.p, s);
+        gram<T>(Xb(j - 1), Xb(j), 0, 2, p, Wb.p, p, vstride, n, P, gtk, G.p, s);
         block_axpy<T>(Wb.p, p, Xb(j - 1), Xb(j), 0, 2, p, G.p, vstride, n, 1, s);
       } else {
         nbk = 1;
-        gram<T>(Xb(0), nullptr, 0, 1, p, Wb.p, p, vstride, n, P, G.p, s);
+        gram<T>(Xb(0), nullptr, 0, 1, p, Wb.p, p, vstride, n, P, gtk, G.p, s);
         block_axpy<T>(Wb.p, p, Xb(0), nullptr, 0, 1, p, G.p, vstride, n, 1, s);
       }
       { ProfScope ps_(K_BAND, s, 0.0); k_small_axpy<<<1, 256, 0, s>>>(G.p + (int64_t)(nbk - 1) * pp, p, A.p + (int64_t)j * pp, pass ? 1.0 : 0.0); }
@@ -603,13 +711,12 @@ static bool band_part(ed_cluster& c, int spin, bool electron, const DevBuf<doubl
     { ProfScope ps_(K_BAND, s, 0.0); k_small_copy<<<1, 256, 0, s>>>(A.p + (int64_t)j * pp, p, A.p + (int64_t)j * pp, 1); }
     ED_CHECK_LAUNCH();
     // W = X_{j+1} B_j
-    const int r = orthonormalize(scale2, B.p + (int64_t)j * pp);
+    const int r = orthonormalize(scale2, B.p + (int64_t)j * pp, j + 1 < kmax ? Xb(j + 1) : Wb.p);
     k = j + 1;
     if (r == 0) {
       conv = true;  // the Krylov space is exhausted: T is exact
       break;
     }
-    if (j + 1 < kmax) ED_CUDA(cudaMemcpyAsync(Xb(j + 1), Wb.p, blk * sizeof(T), cudaMemcpyDeviceToDevice, s));
     if (k == next_check || j + 1 == kmax) {
       BandCoeffs bc{A.p, B.p, R0.p, k, p, c.gs.E0, sgn};
       ED_CUDA(cudaMemsetAsync(dmax.p, 0, sizeof(double), s));
