@@ -330,9 +330,11 @@ struct Acc16<double> {
 // are staged in shared memory as 16-byte groups (one per column); each thread owns columns d and
 // gathers the groups sx[col] of its hops.  The slot-major entries (row_ell_pack) carry the byte
 // offsets of the group and of the signed hop value, so a hop costs one table load, two shared
-// loads and the FMAs.  Table loads run one chunk of kPre slots ahead of their use (the table
-// has kEllPad zero slots at its end, so the look-ahead needs no bounds check).
-template <typename T>
+// loads and the FMAs (one shared load when the cluster has at most four distinct hop values,
+// REG: the value is then selected in registers).  Table loads run one chunk of kPre slots ahead
+// of their use (the table has kEllPad zero slots at its end, so the look-ahead needs no bounds
+// check).
+template <typename T, bool REG>
 __global__ void __launch_bounds__(kRowThreads) k_down_rows(SectorView sv, HopParams hp, const T* __restrict__ X0,
                                                    T* __restrict__ O0, int64_t vstride, const double* __restrict__ beta,
                                                    int beta_stride, int n_step, const int* __restrict__ active) {
@@ -358,8 +360,19 @@ __global__ void __launch_bounds__(kRowThreads) k_down_rows(SectorView sv, HopPar
   const T* eup = Prec<T>::e_up(sv);
   const T* edn = Prec<T>::e_dn(sv);
   const unsigned char* ssvb = reinterpret_cast<const unsigned char*>(ssv);
+  const T v0 = Prec<T>::val(hp, 0), v1 = Prec<T>::val(hp, 1), v2 = Prec<T>::val(hp, 2), v3 = Prec<T>::val(hp, 3);
   auto hop = [&](Acc16<T>& acc, uint32_t e) {
-    const T v = *reinterpret_cast<const T*>(ssvb + (e & 0x3FCu) * (sizeof(T) / 4));
+    T v;
+    if constexpr (REG) {  // at most four distinct values: select in registers, sign bit from the entry
+      const uint32_t i = (e >> 3) & 3u;
+      v = (i & 2u) ? ((i & 1u) ? v3 : v2) : ((i & 1u) ? v1 : v0);
+      if constexpr (sizeof(T) == 4)
+        v = __int_as_float(__float_as_int(v) ^ (int)((e & 4u) << 29));
+      else
+        v = __longlong_as_double(__double_as_longlong(v) ^ ((long long)(e & 4u) << 61));
+    } else {
+      v = *reinterpret_cast<const T*>(ssvb + (e & 0x3FCu) * (sizeof(T) / 4));
+    }
     acc.fma(v, *reinterpret_cast<const ulonglong2*>(sxb + (e >> 10)));
   };
   for (int64_t u0r = (int64_t)blockIdx.x * R; u0r < du; u0r += (int64_t)gridDim.x * R) {
@@ -565,14 +578,19 @@ static void launch_two_pass(const SectorView& sv, const HopParams& hp, const T* 
   const double es = sizeof(T);
   const double dim = (double)sv.d_up * sv.d_dn;
   const size_t smem = down_rows_smem(sv, sizeof(T) == 8 ? ED_FP64 : ED_FP32);
-  ED_CUDA(cudaFuncSetAttribute(k_down_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const bool reg = hp.nvals <= 4;
+  ED_CUDA(cudaFuncSetAttribute(k_down_rows<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ED_CUDA(cudaFuncSetAttribute(k_down_rows<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int64_t groups = (sv.d_up + Vec<T>::n - 1) / Vec<T>::n;
   dim3 g1((unsigned)std::min<int64_t>(groups, 152), runs);
   dim3 g2((unsigned)((sv.d_up + kRowsPerCta - 1) / kRowsPerCta), (unsigned)((sv.d_dn + 32 * Vec<T>::n - 1) / (32 * Vec<T>::n)),
           runs);
   // one timed unit per step: both passes (the second launch is counted separately)
   ProfScope ps_(ls ? K_LANCZOS_STEP : K_HPSI, s, (beta ? 3.0 : 2.0) * es * dim * runs);
-  k_down_rows<T><<<g1, kRowThreads, smem, s>>>(sv, hp, X, O, vstride, beta, beta_stride, n, ls ? ls->active : nullptr);
+  if (reg)
+    k_down_rows<T, true><<<g1, kRowThreads, smem, s>>>(sv, hp, X, O, vstride, beta, beta_stride, n, ls ? ls->active : nullptr);
+  else
+    k_down_rows<T, false><<<g1, kRowThreads, smem, s>>>(sv, hp, X, O, vstride, beta, beta_stride, n, ls ? ls->active : nullptr);
   ED_CHECK_LAUNCH();
   note_launch();
   if (ls)

@@ -180,40 +180,78 @@ static inline unsigned nblocks(int64_t n, int bs) { return (unsigned)((n + bs - 
 // order within each row is chosen against shared-memory bank conflicts of the row kernel: there,
 // the threads of rows 8m .. 8m+7 gather 16-byte words sx[col] together at every slot, and a
 // 16-byte load of 8 threads takes one shared-memory wavefront when their col mod 8 differ.  Per
-// group of 8 rows and per slot, a greedy pass gives each row (fewest remaining entries first) an
-// entry whose col mod 8 is still free at that slot, else any remaining one.  Every row keeps its
-// entry set, so only the order of the additions changes.
+// group of 8 rows and per slot, a maximum matching of the rows that still have entries to the
+// eight residues col mod 8 (augmenting paths; rows with more remaining entries first, each row
+// trying its most frequent residues first) picks one entry per matched row; unmatched rows take
+// their first remaining entry.  Every row keeps its entry set, so only the order of the
+// additions changes.
 constexpr int64_t kEllOrderMinDim = 2048;
+
+namespace {
+struct BankMatch {
+  std::vector<uint32_t>* rem;  // [8] remaining entries of each row
+  int owner[8];                // residue -> row (-1 free)
+  bool seen[8];
+  bool augment(int i) {
+    int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (uint32_t e : rem[i]) ++cnt[ent_col(e) & 7u];
+    for (int pass = 0; pass < 8; ++pass) {
+      int r = -1;
+      for (int k = 0; k < 8; ++k)
+        if (cnt[k] > 0 && !seen[k] && (r < 0 || cnt[k] > cnt[r])) r = k;
+      if (r < 0) return false;
+      seen[r] = true;
+      cnt[r] = 0;
+      if (owner[r] < 0 || augment(owner[r])) {
+        owner[r] = i;
+        return true;
+      }
+    }
+    return false;
+  }
+};
+}  // namespace
 
 static void ell_bank_order(const std::vector<int32_t>& ptr, const std::vector<uint32_t>& ent, int64_t dim, int zmax,
                            std::vector<uint32_t>& ell) {
   ell.assign((size_t)zmax * dim, 0u);
   std::vector<uint32_t> rem[8];
+  BankMatch bm;
+  bm.rem = rem;
   for (int64_t r0 = 0; r0 < dim; r0 += 8) {
     const int nr = (int)std::min<int64_t>(8, dim - r0);
-    int maxn = 0;
-    for (int i = 0; i < nr; ++i) {
-      rem[i].assign(ent.begin() + ptr[r0 + i], ent.begin() + ptr[r0 + i + 1]);
-      maxn = std::max(maxn, (int)rem[i].size());
+    for (int i = 0; i < 8; ++i) {
+      if (i < nr)
+        rem[i].assign(ent.begin() + ptr[r0 + i], ent.begin() + ptr[r0 + i + 1]);
+      else
+        rem[i].clear();
     }
-    int order[8];
-    for (int k = 0; k < maxn; ++k) {
-      for (int i = 0; i < nr; ++i) order[i] = i;
-      std::sort(order, order + nr, [&](int a, int b) { return rem[a].size() < rem[b].size(); });
-      uint32_t used = 0;
-      for (int oi = 0; oi < nr; ++oi) {
+    for (int k = 0;; ++k) {
+      int order[8], na = 0;
+      for (int i = 0; i < nr; ++i)
+        if (!rem[i].empty()) order[na++] = i;
+      if (na == 0) break;
+      std::sort(order, order + na, [&](int a, int b) { return rem[a].size() > rem[b].size(); });
+      for (int r = 0; r < 8; ++r) bm.owner[r] = -1;
+      for (int oi = 0; oi < na; ++oi) {
+        for (int r = 0; r < 8; ++r) bm.seen[r] = false;
+        bm.augment(order[oi]);
+      }
+      int res_of[8];
+      for (int i = 0; i < 8; ++i) res_of[i] = -1;
+      for (int r = 0; r < 8; ++r)
+        if (bm.owner[r] >= 0) res_of[bm.owner[r]] = r;
+      for (int oi = 0; oi < na; ++oi) {
         const int i = order[oi];
         auto& v = rem[i];
-        if (v.empty()) continue;
         size_t pick = 0;
-        for (size_t j = 0; j < v.size(); ++j)
-          if (!((used >> (ent_col(v[j]) & 7u)) & 1u)) {
-            pick = j;
-            break;
-          }
-        const uint32_t e = v[pick];
-        used |= 1u << (ent_col(e) & 7u);
-        ell[(size_t)k * dim + r0 + i] = row_ell_pack(e);
+        if (res_of[i] >= 0)
+          for (size_t j = 0; j < v.size(); ++j)
+            if ((int)(ent_col(v[j]) & 7u) == res_of[i]) {
+              pick = j;
+              break;
+            }
+        ell[(size_t)k * dim + r0 + i] = row_ell_pack(v[pick]);
         v.erase(v.begin() + (ptrdiff_t)pick);
       }
     }
