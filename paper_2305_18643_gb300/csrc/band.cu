@@ -275,10 +275,10 @@ __global__ void __launch_bounds__(kGT2) k_block_axpy(T* __restrict__ Y, int py, 
     for (int e = 0; e < NE; ++e)
 #pragma unroll
       for (int j = 0; j < PY; ++j) acc[e][j] = T(0);
-    for (int k0 = 0; k0 < K; k0 += 4) {
-      V xv[4];
+    for (int k0 = 0; k0 < K; k0 += 8) {  // 8 independent 16-byte loads in flight per thread
+      V xv[8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         const int k = k0 + u;
         if (k < K) {
           const int b = k / px, i = k - b * px;
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(kGT2) k_block_axpy(T* __restrict__ Y, int py, 
         }
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         if (k0 + u >= K) break;
         const T* xs = reinterpret_cast<const T*>(&xv[u]);
         const T* c = sc + (k0 + u) * PY;
@@ -317,12 +317,16 @@ __global__ void __launch_bounds__(kGT2) k_block_axpy(T* __restrict__ Y, int py, 
 // ---- small dense work of one block step (one thread block) ---------------------------------
 // SVQB of a block with Gram G: Cout = U l^{-1/2} (new basis = W Cout), Bout = l^{1/2} U^T
 // (W = new basis * Bout); directions with l <= thr are dropped (zero columns / rows).  Writes
-// the number of kept directions to *rank.  Cyclic Jacobi on one warp (lane k updates row and
-// column k of each rotation), stopped when the off-diagonal norm is below 1e-26 of the total.
+// the number of kept directions to *rank.  Parallel two-sided Jacobi on one warp: every round
+// applies m/2 disjoint rotations at once (round-robin pairing of the m = p rounded up to even
+// indices; an index >= p is a dummy), A <- J^T A J with J block-diagonal, so a sweep is m - 1
+// rounds.  Sweeps stop when the off-diagonal norm is below 1e-26 of the total.
 __global__ void __launch_bounds__(32) k_svqb(const double* __restrict__ G, int p, double thr,
                                              double* __restrict__ Cout, double* __restrict__ Bout,
                                              int* __restrict__ rank) {
   __shared__ double a[kBP][kBP + 1], v[kBP][kBP + 1];
+  __shared__ double cs[kBP / 2], sn[kBP / 2];
+  __shared__ int pr[kBP / 2], pq[kBP / 2];
   const int lane = threadIdx.x;
   for (int t = lane; t < p * p; t += 32) {
     const int i = t / p, j = t - i * p;
@@ -330,6 +334,7 @@ __global__ void __launch_bounds__(32) k_svqb(const double* __restrict__ G, int p
     v[i][j] = i == j ? 1.0 : 0.0;
   }
   __syncwarp();
+  const int m = p + (p & 1), half = m / 2;
   for (int sweep = 0; sweep < 40; ++sweep) {
     double off = 0.0, tot = 0.0;
     for (int t = lane; t < p * p; t += 32) {
@@ -342,30 +347,56 @@ __global__ void __launch_bounds__(32) k_svqb(const double* __restrict__ G, int p
       tot += __shfl_xor_sync(0xffffffffu, tot, o);
     }
     if (!(off > 1e-26 * tot)) break;
-    for (int r = 0; r < p; ++r)
-      for (int q = r + 1; q < p; ++q) {
-        __syncwarp();
-        const double arq = a[r][q];
-        if (fabs(arq) < 1e-300) continue;
-        const double theta = (a[q][q] - a[r][r]) / (2.0 * arq);
-        const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-        const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
-        __syncwarp();
-        if (lane < p) {  // columns r, q
-          const double akr = a[lane][r], akq = a[lane][q];
-          a[lane][r] = c * akr - sn * akq;
-          a[lane][q] = sn * akr + c * akq;
-          const double vkr = v[lane][r], vkq = v[lane][q];
-          v[lane][r] = c * vkr - sn * vkq;
-          v[lane][q] = sn * vkr + c * vkq;
+    for (int round = 0; round < m - 1; ++round) {
+      if (lane < half) {  // pair lane: positions lane and m - 1 - lane of the round-robin circle
+        const int pa = lane, pb = m - 1 - lane;
+        int r = pa == 0 ? 0 : 1 + (pa - 1 + round) % (m - 1);
+        int q = pb == 0 ? 0 : 1 + (pb - 1 + round) % (m - 1);
+        if (r > q) {
+          const int t = r;
+          r = q;
+          q = t;
         }
-        __syncwarp();
-        if (lane < p) {  // rows r, q
-          const double ark = a[r][lane], aqk = a[q][lane];
-          a[r][lane] = c * ark - sn * aqk;
-          a[q][lane] = sn * ark + c * aqk;
+        double c = 1.0, s = 0.0;
+        if (q < p) {
+          const double arq = a[r][q];
+          if (fabs(arq) >= 1e-300) {
+            const double theta = (a[q][q] - a[r][r]) / (2.0 * arq);
+            const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            c = 1.0 / sqrt(t * t + 1.0);
+            s = t * c;
+          }
         }
+        pr[lane] = r;
+        pq[lane] = q < p ? q : r;  // a dummy pair becomes (r, r) and is skipped below
+        cs[lane] = c;
+        sn[lane] = s;
       }
+      __syncwarp();
+      // columns: A <- A J, V <- V J
+      for (int t = lane; t < half * p; t += 32) {
+        const int i = t / p, k = t - i * p, r = pr[i], q = pq[i];
+        if (r == q) continue;
+        const double c = cs[i], s = sn[i];
+        const double akr = a[k][r], akq = a[k][q];
+        a[k][r] = c * akr - s * akq;
+        a[k][q] = s * akr + c * akq;
+        const double vkr = v[k][r], vkq = v[k][q];
+        v[k][r] = c * vkr - s * vkq;
+        v[k][q] = s * vkr + c * vkq;
+      }
+      __syncwarp();
+      // rows: A <- J^T A
+      for (int t = lane; t < half * p; t += 32) {
+        const int i = t / p, k = t - i * p, r = pr[i], q = pq[i];
+        if (r == q) continue;
+        const double c = cs[i], s = sn[i];
+        const double ark = a[r][k], aqk = a[q][k];
+        a[r][k] = c * ark - s * aqk;
+        a[q][k] = s * ark + c * aqk;
+      }
+      __syncwarp();
+    }
   }
   __syncwarp();
   int r = 0;
