@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="4x4")
     ap.add_argument("--requests", type=int, default=32, help="served workload: requests per stream")
+    ap.add_argument("--clusters", type=int, default=512, help="batch workload: clusters (512 is the named workload)")
+    ap.add_argument("--max-orb", type=int, default=12, help="batch workload: largest cluster (orbitals)")
     ap.add_argument("--rates", type=str, default="1,4,16",
                     help="served workload: Poisson arrival rates as multiples of 1 / (mean sequential FP64 solve time)")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default=None)
@@ -287,7 +289,10 @@ def run_batch(args, rank, world, local_rank, torch, ed):
     import math
     gen, label, prec_d, gf_d, nfreq = WORKLOADS["batch"]
     prec = args.precision or prec_d
-    fam = gen(instance=rank)
+    fam = W.batched_family(args.clusters, instance=rank, max_orb=args.max_orb)
+    if args.clusters != 512 or args.max_orb != 12:
+        label = "%d seeded clusters of 4-%d orbitals (a smaller case of the named 512-cluster workload)" % (
+            args.clusters, args.max_orb)
     omega = W.real_grid(nfreq)
     precision = ed.ED_FP32 if prec == "fp32" else ed.ED_FP64
     gsize = sum(2 * nfreq * c["t"].shape[0] ** 2 for c in fam)
@@ -331,14 +336,23 @@ def run_batch(args, rank, world, local_rank, torch, ed):
                "h2d_bytes_per_step": int(sum(8 * (c["t"].size + c["t"].shape[0] + c["eps"].size + c["theta"].size + 1)
                                              for c in fam)),
                "d2h_bytes_per_step": int(gsize * 16 + len(fam) * 8 * 4)}
-    # algorithmic bytes of the ground-state kernel: 3 vectors per Lanczos level (both passes)
+    # algorithmic bytes of a Lanczos level: read v_n, v_{n-1}, write v_{n+1} (3 d s); ground-state
+    # levels (both passes) on the ground-state sector, continued-fraction levels on the N +- 1
+    # sectors (a cluster's levels spread over its parts: the mean target dimension is used)
     es = 4 if prec == "fp32" else 8
-    dims = [math.comb(c["t"].shape[0] + c["eps"].size, c["n_up"]) * math.comb(c["t"].shape[0] + c["eps"].size, c["n_dn"])
-            for c in fam]
-    gs_bytes = sum(2 * int(it) * d * 3 * es for it, d in zip(info["iters"], dims))
+    alg_bytes = 0.0
+    for c, it, gf_l in zip(fam, info["iters"], info["gf_steps"]):
+        L = c["t"].shape[0] + c["eps"].size
+        nu, nd = c["n_up"], c["n_dn"]
+        alg_bytes += 2 * int(it) * math.comb(L, nu) * math.comb(L, nd) * 3 * es
+        tgt = [math.comb(L, nu + dn) * math.comb(L, nd) for dn in (1, -1) if 0 <= nu + dn <= L]
+        if nu != nd:
+            tgt += [math.comb(L, nu) * math.comb(L, nd + dn) for dn in (1, -1) if 0 <= nd + dn <= L]
+        if tgt:
+            alg_bytes += int(gf_l) * float(np.mean(tgt)) * 3 * es
     n_b, ms_b, _ = prof[ed.ED_K_BATCH]
     peak, peak_kind = measured_peak_hbm()
-    achieved = (gs_bytes * args.steps / 1e9) / (ms_b / 1e3) if ms_b > 0 else None
+    achieved = (alg_bytes * args.steps / 1e9) / (ms_b / 1e3) if ms_b > 0 else None
     result = {
         "metric": "ED solves/s (batched form; H.psi GB/s and % roofline in `roofline`)",
         "value": whole_job_rate(len(fam) * args.steps, world, ms), "unit": "cluster solves/s", "n_gpus": world,
@@ -352,8 +366,10 @@ def run_batch(args, rank, world, local_rank, torch, ed):
         "roofline": {"bound": "hbm", "kernel": "batched ground-state and continued-fraction persistent kernels",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
                      "traffic": None, "peak_source": peak_kind, "launches": n_b,
-                     "note": "algorithmic bytes of the ground-state Lanczos levels only (3 vectors per level) over "
-                             "the time of both persistent kernels; sector vectors mostly L2-resident"},
+                     "note": "3 vectors per Lanczos level over all ground-state and continued-fraction levels "
+                             "(the mean N +- 1 dimension of a cluster for its continued-fraction levels), over the "
+                             "time of the graph (persistent kernels, evaluation, assembly); small sectors are "
+                             "L2-resident, so this is an effective rate, not HBM traffic"},
         "solve": {"E0_first": float(info["E0"][0]), "max_residual": float(max(info["residual"])),
                   "not_converged": int(sum(1 for x in info["status"] if x == ed.ED_WARN_NOT_CONVERGED)),
                   "degenerate": int(sum(1 for x in info["status"] if x == ed.ED_WARN_DEGENERATE)),
@@ -432,6 +448,7 @@ def run_served(args, rank, world, local_rank, torch, ed):
     t_seq = float(np.mean(seq_ms))
 
     srv = ed.Server(budget, max_slots=lanes)
+    failures = []
 
     def run_stream(reqs, gaps_s, seed0):
         """Submits reqs with the given gaps (seconds before each), waits for all; returns results."""
@@ -446,6 +463,10 @@ def run_served(args, rank, world, local_rank, torch, ed):
             ids.append(srv.submit(c, omega=om, eta=0.0, axis=ed.ED_AXIS_MATSUBARA, precision=ed.ED_FP32,
                                   gf_method=gfm(m), seed=seed0 + k))
         res = [srv.wait(i, timeout_s=1800.0)[0] for i in ids]
+        for (c, m), r in zip(reqs, res):
+            if r["status"] < 0:
+                failures.append({"orbitals": int(c["t"].shape[0]), "method": m, "status": r["status"],
+                                 "error": r.get("error", "")})
         return res, time.perf_counter() - t0
 
     # warm-up: the first requests of every size (pool growth, module load)
@@ -522,6 +543,7 @@ def run_served(args, rank, world, local_rank, torch, ed):
         "poisson": sweep,
         "server": {k: stats[k] for k in ("completed", "failed", "max_running", "peak_reserved_bytes",
                                          "batched_solves")},
+        "failed_requests": failures[:8],
         "roofline": {"bound": "hbm", "kernel": "lanczos_step (fused H.psi + Lanczos epilogue), all requests",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": None, "peak_source": peak_kind,

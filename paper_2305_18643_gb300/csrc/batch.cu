@@ -243,10 +243,16 @@ __device__ void block_hx(const BTable& tu, const BTable& td, const T* sval, cons
     for (int64_t u = warp; u < du; u += nw)
       for (int64_t d = lane; d < dd; d += 32) element(u, d);
   } else {
-    const int64_t n = du * dd;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-      const int64_t u = i / dd;
-      element(u, i - u * dd);
+    // element i = u dd + d, stepped by blockDim.x without a division per element
+    const int64_t su = blockDim.x / dd, sd = blockDim.x - su * dd;
+    int64_t u = threadIdx.x / dd, d = threadIdx.x - u * dd;
+    for (; u < du; u += su, d += sd) {
+      if (d >= dd) {
+        d -= dd;
+        ++u;
+        if (u >= du) break;
+      }
+      element(u, d);
     }
   }
   bred3(a, b, c, sh);

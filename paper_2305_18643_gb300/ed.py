@@ -412,7 +412,10 @@ class Server:
         if st == ED_PENDING:
             return None
         G = self._live.pop(rid)[0]
-        return res.as_dict(), G
+        out = res.as_dict()
+        if out["status"] < 0:
+            out["error"] = ed_last_error()  # the request's own message (set by the collecting call)
+        return out, G
 
     def poll(self, rid):
         res = ed_result()
