@@ -209,6 +209,8 @@ ed_status ed_server_set_option(ed_server* srv, int option, double value);
 
 /* Device bytes a request would reserve on the single-cluster path with the given Green-function
  * budget (gf_budget_bytes <= 0: unlimited), from closed forms only: no CUDA call, no allocation.
+ * Continued fractions reserve up to the budget (their runs go in chunks); band Lanczos reserves
+ * all its blocks when they fit the budget, else its ring of blocks.
  * ED_ERR_INVALID for a bad description. */
 ed_status ed_request_bytes(const ed_cluster_desc* desc, const ed_request_opts* opts, size_t gf_budget_bytes,
                            size_t* bytes);

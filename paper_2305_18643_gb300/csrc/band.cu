@@ -577,7 +577,7 @@ static void gram_launch(const T* X, const T* X1, int64_t xbstride, int nb, int p
   }
   const int nrow = px + (sym ? 0 : py);
   const size_t smem = (size_t)kGramStages * nrow * (E + VE<T>::n) * sizeof(T);
-  ED_CUDA(cudaFuncSetAttribute(k_gram<T, GR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  allow_max_dynamic_smem(k_gram<T, GR>);
   ProfScope ps_(K_BAND, s, 0.0);
   k_gram<T, GR><<<dim3(nchunk, nb, gz), kGramThreads, smem, s>>>(X, X1, xbstride, px, Y, py, sym ? 1 : 0, vstride, n, chunk,
                                                         P.p, tk.p, G);

@@ -202,8 +202,8 @@ __device__ __forceinline__ void bred3(double& a, double& b, double& c, BlockShar
 // thread.  mode 0: element-strided (consecutive threads take consecutive elements); mode 1: one
 // warp per row (warp-uniform up-spin entries, lanes over the columns).
 template <typename T>
-__device__ void block_hx(const BTable& tu, const BTable& td, const T* sval, const T* sU, uint32_t umask, const T* X,
-                         T* W, T bcoef, int mode, double& sxw, double& sww, double& sxx, BlockShared& sh) {
+__device__ void block_hx(const BTable& tu, const BTable& td, const T* sval, const T* sU, uint32_t umask, T u0, bool uni,
+                         const T* X, T* W, T bcoef, int mode, double& sxw, double& sww, double& sxx, BlockShared& sh) {
   const int64_t du = tu.dim, dd = td.dim;
   const T* eu = BP<T>::e(tu);
   const T* ed = BP<T>::e(td);
@@ -213,9 +213,13 @@ __device__ void block_hx(const BTable& tu, const BTable& td, const T* sval, cons
     const uint32_t bu = tu.basis[u], bd = td.basis[d];
     T diag = eu[u] + ed[d];
     uint32_t dbl = bu & bd & umask;
-    while (dbl) {
-      diag += sU[__ffs(dbl) - 1];
-      dbl &= dbl - 1u;
+    if (uni) {  // the same U on every interacting orbital: one popcount
+      diag += u0 * (T)__popc(dbl);
+    } else {
+      while (dbl) {
+        diag += sU[__ffs(dbl) - 1];
+        dbl &= dbl - 1u;
+      }
     }
     const T x = X[o];
     T acc = diag * x;
@@ -300,7 +304,7 @@ __device__ __forceinline__ const T* sU_of(const S& g) {
 // One Lanczos pass set (first pass + retrace) from the normalized start Vs; the ground state
 // accumulates in omega (FP64).  Returns the levels used; eval[0..2] = lowest, second, Ritz.
 template <typename T>
-__device__ int block_lanczos(const BTable& tu, const BTable& td, uint32_t umask, GSShared& g, T* V0, T* V1,
+__device__ int block_lanczos(const BTable& tu, const BTable& td, uint32_t umask, double u0, bool uni, GSShared& g, T* V0, T* V1,
                              const T* Vs, double* omega, double tol_ritz, int mode, bool* breakdown) {
   const int64_t n = tu.dim * td.dim;
   const T* sval = sval_of<T>(g);
@@ -320,7 +324,7 @@ __device__ int block_lanczos(const BTable& tu, const BTable& td, uint32_t umask,
     const int nmax = pass == 0 ? kBMaxIter : m - 1;
     for (int k = 0; k < nmax; ++k) {
       double sxw, sww, sxx;
-      block_hx<T>(tu, td, sval, sU, umask, X, P, (T)g.beta[k], mode, sxw, sww, sxx, g.bs);
+      block_hx<T>(tu, td, sval, sU, umask, (T)u0, uni, X, P, (T)g.beta[k], mode, sxw, sww, sxx, g.bs);
       const double alpha = sxx > 0.0 ? sxw / sxx : 0.0;
       const double b2 = sxx > 0.0 ? sww - sxw * sxw / sxx : 0.0;
       const double bn = b2 > 0.0 ? sqrt(b2) : 0.0;
@@ -384,7 +388,7 @@ __device__ void block_ground_state(BCluster& c, const BTable* tabs, GSShared& g,
       const T f = (T)(1.0 / sqrt(s2));
       for (int64_t i = threadIdx.x; i < n; i += blockDim.x) Vs[i] *= f;
       __syncthreads();
-      m = block_lanczos<T>(tu, td, umask, g, V0, V1, Vs, om, 1e-7, mode, &brk);
+      m = block_lanczos<T>(tu, td, umask, c.hp.u0, c.hp.uniform_u != 0, g, V0, V1, Vs, om, 1e-7, mode, &brk);
     } else {
       for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
         const double r = (double)(b_splitmix64(c.seed ^ (uint64_t)i) >> 11) * (1.0 / 9007199254740992.0);
@@ -395,7 +399,8 @@ __device__ void block_ground_state(BCluster& c, const BTable* tabs, GSShared& g,
       const double f = 1.0 / sqrt(s2);
       for (int64_t i = threadIdx.x; i < n; i += blockDim.x) Vds[i] *= f;
       __syncthreads();
-      m = block_lanczos<double>(tu, td, umask, g, Vd0, Vd1, Vds, om, fmin(1e-2, 0.1 * c.tol), mode, &brk);
+      m = block_lanczos<double>(tu, td, umask, c.hp.u0, c.hp.uniform_u != 0, g, Vd0, Vd1, Vds, om,
+                                fmin(1e-2, 0.1 * c.tol), mode, &brk);
     }
     total += m;
     lam0 = g.eval[0];
@@ -411,7 +416,8 @@ __device__ void block_ground_state(BCluster& c, const BTable* tabs, GSShared& g,
     }
     __syncthreads();
     double sxw, sww, sxx;
-    block_hx<double>(tu, td, g.svald, g.sUd, umask, om, Y64, 0.0, mode, sxw, sww, sxx, g.bs);
+    block_hx<double>(tu, td, g.svald, g.sUd, umask, c.hp.u0, c.hp.uniform_u != 0, om, Y64, 0.0, mode, sxw, sww, sxx,
+                     g.bs);
     E = sxw;
     double r2 = 0.0, q1 = 0.0, q2 = 0.0;
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
@@ -573,7 +579,8 @@ __global__ void k_batch_cf(BRun* __restrict__ R, const int* __restrict__ order, 
       const double sgn = create ? -1.0 : 1.0;
       for (int k = 0; k < r.mmax; ++k) {
         double sxw, sww, sxx;
-        block_hx<T>(tu, td, sval_of<T>(g), sU_of<T>(g), c.hp.umask, X, P, (T)bprev, mode, sxw, sww, sxx, g.bs);
+        block_hx<T>(tu, td, sval_of<T>(g), sU_of<T>(g), c.hp.umask, (T)c.hp.u0, c.hp.uniform_u != 0, X, P, (T)bprev,
+                    mode, sxw, sww, sxx, g.bs);
         const double alpha = sxx > 0.0 ? sxw / sxx : 0.0;
         const double b2 = sxx > 0.0 ? sww - sxw * sxw / sxx : 0.0;
         const double bn = b2 > 0.0 ? sqrt(b2) : 0.0;

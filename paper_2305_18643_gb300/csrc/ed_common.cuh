@@ -92,6 +92,21 @@ struct AllocStreamScope {
 constexpr int kPinnedSlots = 32;
 double* pinned_scratch();
 
+// Allows kernel fn the largest dynamic shared memory of the current device (its opt-in limit less
+// the kernel's static shared memory).  Every caller sets the same value, so threads that launch
+// the kernel with different sizes at the same time (the server's lanes) cannot undo each other's
+// setting between setting it and launching.
+template <typename K>
+inline void allow_max_dynamic_smem(K* fn) {
+  int dev = 0, optin = 0;
+  ED_CUDA(cudaGetDevice(&dev));
+  ED_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  cudaFuncAttributes fa;
+  ED_CUDA(cudaFuncGetAttributes(&fa, (const void*)fn));
+  ED_CUDA(cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               optin - (int)fa.sharedSizeBytes));
+}
+
 // Device buffer with RAII ownership (cudaMalloc / cudaFree, or the stream-ordered pair when
 // g_alloc_stream is set at allocation; the buffer is then freed on that stream).
 template <typename T>

@@ -579,8 +579,8 @@ static void launch_two_pass(const SectorView& sv, const HopParams& hp, const T* 
   const double dim = (double)sv.d_up * sv.d_dn;
   const size_t smem = down_rows_smem(sv, sizeof(T) == 8 ? ED_FP64 : ED_FP32);
   const bool reg = hp.nvals <= 4;
-  ED_CUDA(cudaFuncSetAttribute(k_down_rows<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  ED_CUDA(cudaFuncSetAttribute(k_down_rows<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  allow_max_dynamic_smem(k_down_rows<T, true>);
+  allow_max_dynamic_smem(k_down_rows<T, false>);
   const int64_t groups = (sv.d_up + Vec<T>::n - 1) / Vec<T>::n;
   dim3 g1((unsigned)std::min<int64_t>(groups, 152), runs);
   dim3 g2((unsigned)((sv.d_up + kRowsPerCta - 1) / kRowsPerCta), (unsigned)((sv.d_dn + 32 * Vec<T>::n - 1) / (32 * Vec<T>::n)),

@@ -123,6 +123,15 @@ Footprint single_footprint(const ModelHost& m, const ed_cluster_desc& d, int nz,
   return f;
 }
 
+// Green-function vector storage to reserve within `share` bytes: continued fractions use any
+// amount between one run's vectors and all runs' (they run in chunks); band Lanczos keeps every
+// block only when all of them fit (full reorthogonalization), else a ring of blocks, so it gets
+// either the full amount or the ring's.
+size_t gf_reservation(const Footprint& f, int gf_method, size_t share) {
+  if (gf_method == ED_GF_BAND) return f.gf_want <= share ? f.gf_want : f.gf_min;
+  return std::max(f.gf_min, std::min(f.gf_want, share));
+}
+
 int64_t largest_sector(const ed_cluster_desc& d, bool gf) {
   const int L = d.n_sites + d.n_bath;
   auto dimN = [&](int N) -> int64_t { return (N < 0 || N > L) ? 0 : (int64_t)binomial(L, N); };
@@ -451,7 +460,7 @@ ed_status ed_request_bytes(const ed_cluster_desc* desc, const ed_request_opts* o
     const int nz = opts ? opts->n_freq : 0;
     const int cap = opts && opts->cf_max_levels > 0 ? opts->cf_max_levels : kDefaultCfCap;
     Footprint f = single_footprint(m, *desc, nz, cap);
-    *bytes = f.total(gf_budget_bytes > 0 ? gf_budget_bytes : SIZE_MAX / 4);
+    *bytes = f.total(gf_reservation(f, desc->gf_method, gf_budget_bytes > 0 ? gf_budget_bytes : SIZE_MAX / 4));
     return ED_OK;
   });
 }
@@ -574,7 +583,7 @@ ed_status ed_submit(ed_server* srv, const ed_cluster_desc* desc, const ed_reques
     } else {
       Footprint f = single_footprint(m, *desc, r->n_freq, r->cf_cap);
       const size_t share = (size_t)(srv->gf_fraction * (double)srv->budget);
-      r->gf_budget = std::max(f.gf_min, std::min(f.gf_want, share));
+      r->gf_budget = gf_reservation(f, desc->gf_method, share);
       r->need = f.total(r->gf_budget);
     }
     if (r->need > srv->budget)

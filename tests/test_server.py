@@ -164,3 +164,25 @@ def test_destroy_with_work_in_flight():
     for k in range(3):
         srv.submit(c, omega=W.real_grid(64), precision=ed.ED_FP64, seed=k)
     srv.close()
+
+
+def test_concurrent_band_requests_of_different_sizes():
+    """Band requests of 12 and 14 orbitals on concurrent lanes (their kernels launch with different
+    shared-memory sizes at the same time) all complete, with the energies of the same requests
+    solved alone."""
+    rng = np.random.default_rng(20230529 + 5002)
+    reqs = [W.served_request(rng, sizes=(n,)) for n in (12, 14, 12, 14, 12, 14)]
+    om = W.matsubara_grid(256)
+    with ed.Server(64 * GB, max_slots=6, batch_max_dim=0, paused=1) as srv:
+        ids = [srv.submit(c, omega=om, axis=ed.ED_AXIS_MATSUBARA, precision=ed.ED_FP32, gf_method=ed.ED_GF_BAND,
+                          seed=3 + k) for k, c in enumerate(reqs)]
+        srv.pause(False)
+        out = [srv.wait(i)[0] for i in ids]
+        assert srv.stats()["max_running"] >= 2
+    for r in out:
+        assert r["status"] >= 0, r.get("error")
+    with ed.Server(64 * GB, max_slots=1, batch_max_dim=0) as srv:
+        for k in (0, 1):
+            alone = srv.wait(srv.submit(reqs[k], omega=om, axis=ed.ED_AXIS_MATSUBARA, precision=ed.ED_FP32,
+                                        gf_method=ed.ED_GF_BAND, seed=3 + k))[0]
+            assert abs(alone["E0"] - out[k]["E0"]) <= 1e-12 * abs(alone["E0"])
