@@ -293,9 +293,11 @@ def run_batch(args, rank, world, local_rank, torch, ed):
     if args.clusters != 512 or args.max_orb != 12:
         label = "%d seeded clusters of 4-%d orbitals (a smaller case of the named 512-cluster workload)" % (
             args.clusters, args.max_orb)
-    omega = W.real_grid(nfreq)
+    if args.gf == "none":  # ground states only
+        nfreq = 0
+    omega = W.real_grid(nfreq) if nfreq else None
     precision = ed.ED_FP32 if prec == "fp32" else ed.ED_FP64
-    gsize = sum(2 * nfreq * c["t"].shape[0] ** 2 for c in fam)
+    gsize = max(1, sum(2 * nfreq * c["t"].shape[0] ** 2 for c in fam))
     G_dev = torch.empty(gsize * 2, dtype=torch.float64, device="cuda")
     info = {}
 
@@ -359,7 +361,7 @@ def run_batch(args, rank, world, local_rank, torch, ed):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 vectors, f64 reductions" if prec == "fp32" else "f64", "data": "synthetic (seeded cluster parameters)",
-        "config": {"workload": "batch: " + label, "clusters": len(fam), "precision": prec, "green_function": "cf",
+        "config": {"workload": "batch: " + label, "clusters": len(fam), "precision": prec, "green_function": "cf" if nfreq else "none",
                    "n_freq": nfreq, "eta": ETA, "l2": "L2 flushed by the step's own traffic (tens of GB per step)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "clocks": clk.summary(), "e2e": e2e, "gpu_launches": int(launches),

@@ -198,6 +198,38 @@ __device__ __forceinline__ void bred3(double& a, double& b, double& c, BlockShar
   c = sh.bcast[2];
 }
 
+// Per-thread partial sums of <x,w>, <w,w>, <x,x>: FP64 for FP64 vectors; compensated (Kahan) FP32
+// for FP32 vectors, so no per-element FP64 arithmetic runs (FP64 is a small fraction of the FP32
+// rate on this GPU); the block sums them in FP64.
+template <typename T>
+struct BPart3;
+template <>
+struct BPart3<double> {
+  double s[3] = {0.0, 0.0, 0.0};
+  __device__ void add(double x, double w) {
+    s[0] += x * w;
+    s[1] += w * w;
+    s[2] += x * x;
+  }
+  __device__ double get(int i) const { return s[i]; }
+};
+template <>
+struct BPart3<float> {
+  float s[3] = {0.f, 0.f, 0.f}, k[3] = {0.f, 0.f, 0.f};
+  __device__ void add1(int i, float v) {
+    const float y = v - k[i];
+    const float t = s[i] + y;
+    k[i] = (t - s[i]) - y;
+    s[i] = t;
+  }
+  __device__ void add(float x, float w) {
+    add1(0, x * w);
+    add1(1, w * w);
+    add1(2, x * x);
+  }
+  __device__ double get(int i) const { return (double)s[i] - (double)k[i]; }
+};
+
 // W = H X - bcoef * W (in place; W may hold x_prev), with <x,w>, <w,w>, <x,x> returned to every
 // thread.  mode 0: element-strided (consecutive threads take consecutive elements); mode 1: one
 // warp per row (warp-uniform up-spin entries, lanes over the columns).
@@ -207,7 +239,7 @@ __device__ void block_hx(const BTable& tu, const BTable& td, const T* sval, cons
   const int64_t du = tu.dim, dd = td.dim;
   const T* eu = BP<T>::e(tu);
   const T* ed = BP<T>::e(td);
-  double a = 0.0, b = 0.0, c = 0.0;
+  BPart3<T> part;
   auto element = [&](int64_t u, int64_t d) {
     const int64_t o = u * dd + d;
     const uint32_t bu = tu.basis[u], bd = td.basis[d];
@@ -238,9 +270,7 @@ __device__ void block_hx(const BTable& tu, const BTable& td, const T* sval, cons
     }
     const T w = acc - bcoef * W[o];
     W[o] = w;
-    a += (double)x * (double)w;
-    b += (double)w * (double)w;
-    c += (double)x * (double)x;
+    part.add(x, w);
   };
   if (mode == 1 && dd >= 16) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -259,6 +289,7 @@ __device__ void block_hx(const BTable& tu, const BTable& td, const T* sval, cons
       element(u, d);
     }
   }
+  double a = part.get(0), b = part.get(1), c = part.get(2);
   bred3(a, b, c, sh);
   sxw = a;
   sww = b;
