@@ -479,7 +479,12 @@ struct BWork {
   char* base;          // per-block workspace
   int64_t stride;      // bytes per block
   int64_t maxd;
+  int64_t wmax;        // elements per vector of a warp's slice (warp-level runs)
 };
+
+// Runs of at most this many states are done by one warp each (no block barriers per level and
+// four to sixteen runs per block at once); larger ones by a whole block.
+constexpr int64_t kWarpRunMax = 8192;
 
 template <typename T>
 __global__ void k_batch_gs(BCluster* __restrict__ C, const int* __restrict__ order, int n, const BTable* __restrict__ tabs,
@@ -540,10 +545,168 @@ __device__ __forceinline__ double2 b_cf_eval(const double* __restrict__ a, const
   return make_double2(q * dr, -q * di);
 }
 
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// W = H X - bcoef W over a sector by one warp (lanes over elements, fixed butterfly sums), with
+// <x,w>, <w,w>, <x,x> returned to every lane.  Hopping values and U come from the cluster's
+// parameters in global memory (cached).
 template <typename T>
-__global__ void k_batch_cf(BRun* __restrict__ R, const int* __restrict__ order, int n, const BCluster* __restrict__ C,
-                           const BTable* __restrict__ tabs, int* __restrict__ queue, BWork w,
-                           const double2* __restrict__ z, int nz, double tol, int mode) {
+__device__ void warp_hx(const BTable& tu, const BTable& td, const HopParams& hp, const T* X, T* W, T bcoef,
+                        double& sxw, double& sww, double& sxx) {
+  const int lane = threadIdx.x & 31;
+  const int64_t du = tu.dim, dd = td.dim;
+  const T* eu = BP<T>::e(tu);
+  const T* ed = BP<T>::e(td);
+  const T u0 = (T)hp.u0;
+  const bool uni = hp.uniform_u != 0;
+  const uint32_t umask = hp.umask;
+  BPart3<T> part;
+  const int64_t su = 32 / dd, sd = 32 - su * dd;
+  int64_t u = lane / dd, d = lane - u * dd;
+  for (; u < du; u += su, d += sd) {
+    if (d >= dd) {
+      d -= dd;
+      ++u;
+      if (u >= du) break;
+    }
+    const int64_t o = u * dd + d;
+    const uint32_t bu = tu.basis[u], bd = td.basis[d];
+    T diag = eu[u] + ed[d];
+    uint32_t dbl = bu & bd & umask;
+    if (uni) {
+      diag += u0 * (T)__popc(dbl);
+    } else {
+      while (dbl) {
+        diag += BP<T>::U(hp, __ffs(dbl) - 1);
+        dbl &= dbl - 1u;
+      }
+    }
+    const T x = X[o];
+    T acc = diag * x;
+    const T* xr = X + u * dd;
+    const int nd = td.cnt[d];
+    for (int k = 0; k < nd; ++k) {
+      const uint32_t e = td.ell[(int64_t)k * dd + d];
+      const T v = BP<T>::val(hp, ent_vidx(e));
+      acc += (ent_neg(e) ? -v : v) * xr[ent_col(e)];
+    }
+    const int nu = tu.cnt[u];
+    for (int k = 0; k < nu; ++k) {
+      const uint32_t e = tu.ell[(int64_t)k * du + u];
+      const T v = BP<T>::val(hp, ent_vidx(e));
+      acc += (ent_neg(e) ? -v : v) * X[(int64_t)ent_col(e) * dd + d];
+    }
+    const T w = acc - bcoef * W[o];
+    W[o] = w;
+    part.add(x, w);
+  }
+  sxw = warp_sum(part.get(0));
+  sww = warp_sum(part.get(1));
+  sxx = warp_sum(part.get(2));
+}
+
+// One continued fraction run by one warp: the same steps, check schedule and stopping rule as
+// the block-level run of k_batch_cf.
+template <typename T>
+__device__ void warp_cf_run(BRun& r, const BCluster& c, const BTable* tabs, T* V0, T* V1, const double2* z, int nz,
+                            double tol) {
+  const int lane = threadIdx.x & 31;
+  const int zstride = max(1, (nz + 63) / 64);
+  const int nzs = (nz + zstride - 1) / zstride;
+  const BTable tu = tabs[r.tu], td = tabs[r.td], src = tabs[r.src];
+  const BTable dst = r.spin == 0 ? tu : td;
+  const int64_t dd = td.dim, nel = r.d;
+  const int64_t dd_s = tabs[c.t_dn].dim;
+  const uint32_t lomask = (1u << src.split) - 1u;
+  const int create = r.part == 0;
+  const int extra = r.spin == 1 ? (c.n_up & 1) : 0;
+  double s2 = 0.0;
+  for (int64_t idx = lane; idx < nel; idx += 32) {
+    const int64_t u = idx / dd, d = idx - u * dd;
+    const uint32_t bt = r.spin == 0 ? dst.basis[u] : dst.basis[d];
+    double acc = 0.0;
+    for (int k = 0; k < 2; ++k) {
+      const int site = k == 0 ? r.i : r.j;
+      if (site < 0) continue;
+      const uint32_t bit = 1u << site;
+      if (create ? !(bt & bit) : (bt & bit)) continue;
+      const uint32_t sb = bt ^ bit;
+      const int64_t rr = src.rank_lo[sb & lomask] + src.rank_hi[sb >> src.split];
+      const int neg = (__popc(bt & (bit - 1u)) + extra) & 1;
+      const double v = r.spin == 0 ? c.omega[rr * dd_s + d] : c.omega[u * dd_s + rr];
+      acc += neg ? -v : v;
+    }
+    V0[idx] = (T)acc;
+    V1[idx] = T(0);
+    s2 += acc * acc;
+  }
+  s2 = warp_sum(s2);
+  int steps = 0;
+  if (s2 > 1e-28) {
+    const T f = (T)(1.0 / sqrt(s2));
+    for (int64_t idx = lane; idx < nel; idx += 32) V0[idx] *= f;
+    __syncwarp();
+    T* X = V0;
+    T* P = V1;
+    double bprev = 0.0;
+    int next_check = 32, hits = 0;
+    const double sgn = create ? -1.0 : 1.0;
+    double2 prev0 = make_double2(0.0, 0.0), prev1 = make_double2(0.0, 0.0);  // check frequencies lane, lane + 32
+    for (int k = 0; k < r.mmax; ++k) {
+      double sxw, sww, sxx;
+      warp_hx<T>(tu, td, c.hp, X, P, (T)bprev, sxw, sww, sxx);
+      const double alpha = sxx > 0.0 ? sxw / sxx : 0.0;
+      const double b2 = sxx > 0.0 ? sww - sxw * sxw / sxx : 0.0;
+      const double bn = b2 > 0.0 ? sqrt(b2) : 0.0;
+      if (lane == 0) {
+        r.alpha[k] = alpha;
+        r.beta[k + 1] = bn;
+      }
+      steps = k + 1;
+      if (!(bn > 1e-10)) break;
+      const T aT = (T)alpha, ibT = (T)(1.0 / bn);
+      for (int64_t idx = lane; idx < nel; idx += 32) P[idx] = (P[idx] - aT * X[idx]) * ibT;
+      bprev = bn;
+      T* t = X;
+      X = P;
+      P = t;
+      __syncwarp();
+      if (steps == next_check) {
+        double mx = 0.0;
+        if (lane < nzs) {
+          const double2 gv = b_cf_eval(r.alpha, r.beta, steps, s2, z[lane * zstride], c.E0, sgn);
+          mx = fmax(mx, hypot(gv.x - prev0.x, gv.y - prev0.y));
+          prev0 = gv;
+        }
+        if (lane + 32 < nzs) {
+          const double2 gv = b_cf_eval(r.alpha, r.beta, steps, s2, z[(lane + 32) * zstride], c.E0, sgn);
+          mx = fmax(mx, hypot(gv.x - prev1.x, gv.y - prev1.y));
+          prev1 = gv;
+        }
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        hits = mx < tol ? hits + 1 : 0;
+        if (hits >= 2) break;
+        next_check = steps + max(32, steps / 8);
+      }
+    }
+  }
+  if (lane == 0) {
+    r.b0sq = s2;
+    r.nsteps = steps;
+  }
+  __syncwarp();
+}
+
+// Runs order[0, n_block) (the larger ones, largest first) are taken by whole blocks from
+// queue[0]; once those are gone, every warp takes runs order[n_block, n) from queue[1] and does
+// each alone in its slice of the block's workspace.
+template <typename T>
+__global__ void k_batch_cf(BRun* __restrict__ R, const int* __restrict__ order, int n_block, int n,
+                           const BCluster* __restrict__ C, const BTable* __restrict__ tabs, int* __restrict__ queue,
+                           BWork w, const double2* __restrict__ z, int nz, double tol, int mode) {
   __shared__ CFShared g;
   char* ws = w.base + (int64_t)blockIdx.x * w.stride;
   T* V0 = (T*)ws;
@@ -555,7 +718,7 @@ __global__ void k_batch_cf(BRun* __restrict__ R, const int* __restrict__ order, 
     if (threadIdx.x == 0) g.flag = atomicAdd(queue, 1);
     __syncthreads();
     const int item = g.flag;
-    if (item >= n) return;
+    if (item >= n_block) break;
     BRun& r = R[order[item]];
     const BCluster& c = C[r.cluster];
     for (int i = threadIdx.x; i < kMaxVals; i += blockDim.x) {
@@ -653,6 +816,19 @@ __global__ void k_batch_cf(BRun* __restrict__ R, const int* __restrict__ order, 
     }
     __syncthreads();
   }
+  // warp phase
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T* W0 = reinterpret_cast<T*>(ws) + (int64_t)warp * 2 * w.wmax;
+  T* W1 = W0 + w.wmax;
+  while (true) {
+    int t = 0;
+    if (lane == 0) t = atomicAdd(queue + 1, 1);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    const int item = n_block + t;
+    if (item >= n) return;
+    BRun& r = R[order[item]];
+    warp_cf_run<T>(r, C[r.cluster], tabs, W0, W1, z, nz, tol);
+  }
 }
 
 // -------------------------------------------------------------------------------- evaluation on the grid
@@ -736,9 +912,9 @@ struct BatchResult {
 // (prof: time each launch with the profiler; off while the launches are captured into a graph)
 template <typename T>
 static void run_batch_kernels(int threads, int mode, BCluster* C, const int* corder, int nclu, const BTable* tabs,
-                              BRun* R, const int* rorder, int nruns, int* queues, const BWork& w, int blocks,
+                              BRun* R, const int* rorder, int nblock_runs, int nruns, int* queues, const BWork& w, int blocks,
                               const double2* z, int nz, double tol, bool do_gf, cudaStream_t s, bool prof = true) {
-  ED_CUDA(cudaMemsetAsync(queues, 0, 2 * sizeof(int), s));
+  ED_CUDA(cudaMemsetAsync(queues, 0, 3 * sizeof(int), s));
   {
     std::unique_ptr<ProfScope> ps_(prof ? new ProfScope(K_BATCH, s, 0.0) : nullptr);
     k_batch_gs<T><<<blocks, threads, 0, s>>>(C, corder, nclu, tabs, queues, w, mode);
@@ -746,7 +922,7 @@ static void run_batch_kernels(int threads, int mode, BCluster* C, const int* cor
   }
   if (do_gf && nruns > 0) {
     std::unique_ptr<ProfScope> ps_(prof ? new ProfScope(K_BATCH, s, 0.0) : nullptr);
-    k_batch_cf<T><<<blocks, threads, 0, s>>>(R, rorder, nruns, C, tabs, queues + 1, w, z, nz, tol, mode);
+    k_batch_cf<T><<<blocks, threads, 0, s>>>(R, rorder, nblock_runs, nruns, C, tabs, queues + 1, w, z, nz, tol, mode);
     ED_CHECK_LAUNCH();
   }
 }
@@ -816,7 +992,8 @@ size_t batch_device_bytes(const ed_cluster_desc* descs, int n, int precision, in
   }
   bytes += r256((size_t)std::max<int64_t>(nruns, 1) * std::max(nz, 0) * 16);
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(n + nruns, (int64_t)sms * 4));
-  const size_t stride = ((3 * maxd * es + 255) / 256) * 256 + 4 * maxd * 8 + 256;
+  const int64_t wmax = std::min<int64_t>(maxd, kWarpRunMax);
+  const size_t stride = std::max<size_t>(((3 * maxd * es + 255) / 256) * 256 + 4 * maxd * 8, (size_t)16 * 2 * wmax * es) + 256;
   return bytes + (size_t)blocks * stride + (size_t(1) << 20);
 }
 
@@ -967,10 +1144,12 @@ void batch_solve(const ed_cluster_desc* descs, int n, int precision, const doubl
   std::stable_sort(corder.begin(), corder.end(), [&](int a, int b) { return C[a].d > C[b].d; });
   std::iota(rorder.begin(), rorder.end(), 0);
   std::stable_sort(rorder.begin(), rorder.end(), [&](int a, int b) { return R[a].d > R[b].d; });
+  int nblock_runs = 0;  // runs done by whole blocks (the rest by single warps)
+  while (nblock_runs < nruns && R[rorder[nblock_runs]].d > kWarpRunMax) ++nblock_runs;
   // ---- device descriptors
   DevBuf<BTable> dT(T.size());
   DevBuf<BPair> dP(std::max<size_t>(pairs.size(), 1));
-  DevBuf<int> dPoff(n + 1), dCo(n), dRo(std::max(nruns, 1)), dQ(2), dBase((size_t)n * 4);
+  DevBuf<int> dPoff(n + 1), dCo(n), dRo(std::max(nruns, 1)), dQ(3), dBase((size_t)n * 4);
   DevBuf<double> dHd(hdiag.size());
   DevBuf<BCluster> dC(n);
   DevBuf<BRun> dR(std::max(nruns, 1));
@@ -1007,7 +1186,10 @@ void batch_solve(const ed_cluster_desc* descs, int n, int precision, const doubl
   for (int c = 0; c < n; ++c) maxd = std::max(maxd, C[c].d);
   for (int r = 0; r < nruns; ++r) maxd = std::max(maxd, R[r].d);
   const size_t es = precision == ED_FP64 ? 8 : 4;
-  const size_t stride = ((3 * maxd * es + 255) / 256) * 256 + 4 * maxd * 8 + 256;
+  // per block: 3 + 4 vectors of the largest sector, or 2 vectors per warp (at most 16) of the
+  // largest warp-level run, whichever is more
+  const int64_t wmax = std::min<int64_t>(maxd, kWarpRunMax);
+  const size_t stride = std::max<size_t>(((3 * maxd * es + 255) / 256) * 256 + 4 * maxd * 8, (size_t)16 * 2 * wmax * es) + 256;
   int dev = 0, sms = 0;
   ED_CUDA(cudaGetDevice(&dev));
   ED_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1032,7 +1214,7 @@ void batch_solve(const ed_cluster_desc* descs, int n, int precision, const doubl
   const int per_sm = 4;
   const int blocks = std::max(1, std::min(n + nruns, sms * per_sm));
   DevBuf<char> work((size_t)blocks * stride);
-  BWork w{work.p, (int64_t)stride, maxd};
+  BWork w{work.p, (int64_t)stride, maxd, wmax};
   if (!tuned) {
     // time the ground-state kernel of the largest clusters with each candidate
     const int sample = std::min(n, std::max(8, blocks));
@@ -1045,10 +1227,10 @@ void batch_solve(const ed_cluster_desc* descs, int n, int precision, const doubl
       ED_CUDA(cudaMemcpyAsync(dC.p, C.data(), n * sizeof(BCluster), cudaMemcpyHostToDevice, s));
       ED_CUDA(cudaEventRecord(e0, s));
       if (precision == ED_FP64)
-        run_batch_kernels<double>(cd.first, cd.second, dC.p, dCo.p, sample, dT.p, dR.p, dRo.p, 0, dQ.p, w, blocks,
+        run_batch_kernels<double>(cd.first, cd.second, dC.p, dCo.p, sample, dT.p, dR.p, dRo.p, 0, 0, dQ.p, w, blocks,
                                   dz.p, nz, 0.0, false, s);
       else
-        run_batch_kernels<float>(cd.first, cd.second, dC.p, dCo.p, sample, dT.p, dR.p, dRo.p, 0, dQ.p, w, blocks,
+        run_batch_kernels<float>(cd.first, cd.second, dC.p, dCo.p, sample, dT.p, dR.p, dRo.p, 0, 0, dQ.p, w, blocks,
                                  dz.p, nz, 0.0, false, s);
       ED_CUDA(cudaEventRecord(e1, s));
       ED_CUDA(cudaEventSynchronize(e1));
@@ -1078,10 +1260,10 @@ void batch_solve(const ed_cluster_desc* descs, int n, int precision, const doubl
     CaptureGuard cg{s};
     ED_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     if (precision == ED_FP64)
-      run_batch_kernels<double>(cfg.first, cfg.second, dC.p, dCo.p, n, dT.p, dR.p, dRo.p, nruns, dQ.p, w, blocks,
+      run_batch_kernels<double>(cfg.first, cfg.second, dC.p, dCo.p, n, dT.p, dR.p, dRo.p, nblock_runs, nruns, dQ.p, w, blocks,
                                 dz.p, nz, gtol, do_gf, s, false);
     else
-      run_batch_kernels<float>(cfg.first, cfg.second, dC.p, dCo.p, n, dT.p, dR.p, dRo.p, nruns, dQ.p, w, blocks,
+      run_batch_kernels<float>(cfg.first, cfg.second, dC.p, dCo.p, n, dT.p, dR.p, dRo.p, nblock_runs, nruns, dQ.p, w, blocks,
                                dz.p, nz, gtol, do_gf, s, false);
     if (gf) {
       k_bcf_eval<<<dim3((nz + 255) / 256, std::min(nruns, 32768)), 256, 0, s>>>(dR.p, nruns, dC.p, dz.p, nz, Gk);
