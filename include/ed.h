@@ -138,9 +138,10 @@ ed_status ed_green_stats(const ed_cluster* c, int64_t* total_steps, int* max_ste
  *  - G_out: complex128 (2 doubles each), clusters one after the other, cluster c holding
  *    [2 spins][n_freq][n_sites_c][n_sites_c]; host or device memory as out_is_device says.
  * Tables of all clusters are built by three launches; the solve proper is one CUDA graph: a
- * persistent ground-state kernel and a persistent continued-fraction kernel, in which every
- * thread block takes the next cluster (or continued fraction) from a queue, largest first, then
- * the evaluation on the grid and the assembly of G.  The block width and the mapping of the
+ * persistent ground-state kernel, in which every thread block takes the next cluster from a
+ * queue, largest first; a persistent continued-fraction kernel, in which blocks take the
+ * continued fractions of more than 8,192 states and, once those are gone, every warp takes the
+ * smaller ones one at a time; then the evaluation on the grid and the assembly of G.  The block width and the mapping of the
  * block-level H.psi are picked by timing candidates on the first call for a batch shape (then
  * cached). */
 ed_status ed_batch_solve(const ed_cluster_desc* descs, int n, int precision, const double* omega, int n_freq,
