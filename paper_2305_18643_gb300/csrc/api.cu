@@ -65,77 +65,77 @@ static bool is_finite(double x) { return std::isfinite(x); }
 // terms of Eq. cdmft1), the list of hopping pairs and the kernel parameters.
 void build_model(const ed_cluster_desc* desc, ModelHost& m, HopParams& hp) {
   require(desc != nullptr, "cluster description is NULL");
-    const int ns = desc->n_sites, nb = desc->n_bath, L = ns + nb;
-    require(ns >= 1 && nb >= 0 && L <= kMaxOrb, "need n_sites >= 1, n_bath >= 0, n_sites + n_bath <= 32");
-    require(desc->t && desc->U, "t and U must not be NULL");
-    require(nb == 0 || (desc->eps && desc->theta), "eps and theta must not be NULL when n_bath > 0");
-    require(desc->n_up >= 0 && desc->n_up <= L && desc->n_dn >= 0 && desc->n_dn <= L, "sector outside [0, L]");
-    require(desc->precision == ED_FP64 || desc->precision == ED_FP32, "precision must be ED_FP64 or ED_FP32");
-    require(desc->gf_method == ED_GF_CF || desc->gf_method == ED_GF_BAND, "gf_method must be ED_GF_CF or ED_GF_BAND");
-    require(is_finite(desc->mu), "mu is not finite");
-    double tmax = 0.0;
-    for (int i = 0; i < ns * ns; ++i) {
-      require(is_finite(desc->t[i]), "t has a non-finite entry");
-      tmax = std::max(tmax, std::fabs(desc->t[i]));
-    }
-    for (int i = 0; i < ns; ++i)
-      for (int j = 0; j < i; ++j)
-        require(std::fabs(desc->t[i * ns + j] - desc->t[j * ns + i]) <= 1e-12 * std::max(1.0, tmax), "t is not symmetric");
-    for (int i = 0; i < ns; ++i) require(is_finite(desc->U[i]), "U has a non-finite entry");
-    for (int a = 0; a < nb; ++a) require(is_finite(desc->eps[a]), "eps has a non-finite entry");
-    for (int i = 0; i < ns * nb; ++i) require(is_finite(desc->theta[i]), "theta has a non-finite entry");
+  const int ns = desc->n_sites, nb = desc->n_bath, L = ns + nb;
+  require(ns >= 1 && nb >= 0 && L <= kMaxOrb, "need n_sites >= 1, n_bath >= 0, n_sites + n_bath <= 32");
+  require(desc->t && desc->U, "t and U must not be NULL");
+  require(nb == 0 || (desc->eps && desc->theta), "eps and theta must not be NULL when n_bath > 0");
+  require(desc->n_up >= 0 && desc->n_up <= L && desc->n_dn >= 0 && desc->n_dn <= L, "sector outside [0, L]");
+  require(desc->precision == ED_FP64 || desc->precision == ED_FP32, "precision must be ED_FP64 or ED_FP32");
+  require(desc->gf_method == ED_GF_CF || desc->gf_method == ED_GF_BAND, "gf_method must be ED_GF_CF or ED_GF_BAND");
+  require(is_finite(desc->mu), "mu is not finite");
+  double tmax = 0.0;
+  for (int i = 0; i < ns * ns; ++i) {
+    require(is_finite(desc->t[i]), "t has a non-finite entry");
+    tmax = std::max(tmax, std::fabs(desc->t[i]));
+  }
+  for (int i = 0; i < ns; ++i)
+    for (int j = 0; j < i; ++j)
+      require(std::fabs(desc->t[i * ns + j] - desc->t[j * ns + i]) <= 1e-12 * std::max(1.0, tmax), "t is not symmetric");
+  for (int i = 0; i < ns; ++i) require(is_finite(desc->U[i]), "U has a non-finite entry");
+  for (int a = 0; a < nb; ++a) require(is_finite(desc->eps[a]), "eps has a non-finite entry");
+  for (int i = 0; i < ns * nb; ++i) require(is_finite(desc->theta[i]), "theta has a non-finite entry");
 
-    m.ns = ns;
-    m.nb = nb;
-    m.L = L;
-    m.h.assign((size_t)L * L, 0.0);
-    m.U.assign(L, 0.0);
-    for (int i = 0; i < ns; ++i) {
-      for (int j = 0; j < ns; ++j) m.h[i * L + j] = desc->t[i * ns + j];
-      m.h[i * L + i] -= desc->mu;
-      m.U[i] = desc->U[i];
-      for (int a = 0; a < nb; ++a) {
-        m.h[i * L + ns + a] = desc->theta[i * nb + a];
-        m.h[(ns + a) * L + i] = desc->theta[i * nb + a];
-      }
+  m.ns = ns;
+  m.nb = nb;
+  m.L = L;
+  m.h.assign((size_t)L * L, 0.0);
+  m.U.assign(L, 0.0);
+  for (int i = 0; i < ns; ++i) {
+    for (int j = 0; j < ns; ++j) m.h[i * L + j] = desc->t[i * ns + j];
+    m.h[i * L + i] -= desc->mu;
+    m.U[i] = desc->U[i];
+    for (int a = 0; a < nb; ++a) {
+      m.h[i * L + ns + a] = desc->theta[i * nb + a];
+      m.h[(ns + a) * L + i] = desc->theta[i * nb + a];
     }
-    for (int a = 0; a < nb; ++a) m.h[(ns + a) * L + ns + a] = desc->eps[a];
-    for (int a = 0; a < L; ++a)
-      for (int b = 0; b < L; ++b) {
-        double v = m.h[a * L + b];
-        if (a == b || v == 0.0) continue;
-        int idx = -1;
-        for (size_t k = 0; k < m.vals.size(); ++k)
-          if (m.vals[k] == v) idx = (int)k;
-        if (idx < 0) {
-          require(m.vals.size() < (size_t)kMaxVals, "more than 128 distinct off-diagonal one-body values");
-          idx = (int)m.vals.size();
-          m.vals.push_back(v);
-        }
-        m.pair_a.push_back(a);
-        m.pair_b.push_back(b);
-        m.pair_vidx.push_back(idx);
+  }
+  for (int a = 0; a < nb; ++a) m.h[(ns + a) * L + ns + a] = desc->eps[a];
+  for (int a = 0; a < L; ++a)
+    for (int b = 0; b < L; ++b) {
+      double v = m.h[a * L + b];
+      if (a == b || v == 0.0) continue;
+      int idx = -1;
+      for (size_t k = 0; k < m.vals.size(); ++k)
+        if (m.vals[k] == v) idx = (int)k;
+      if (idx < 0) {
+        require(m.vals.size() < (size_t)kMaxVals, "more than 128 distinct off-diagonal one-body values");
+        idx = (int)m.vals.size();
+        m.vals.push_back(v);
       }
-    std::memset(&hp, 0, sizeof(hp));
-    for (size_t k = 0; k < m.vals.size(); ++k) {
-      hp.val[k] = m.vals[k];
-      hp.valf[k] = (float)m.vals[k];
+      m.pair_a.push_back(a);
+      m.pair_b.push_back(b);
+      m.pair_vidx.push_back(idx);
     }
-    hp.nvals = (int)m.vals.size();
-    for (int i = 0; i < L; ++i) {
-      hp.U[i] = m.U[i];
-      hp.Uf[i] = (float)m.U[i];
-      if (m.U[i] != 0.0) hp.umask |= 1u << i;
+  std::memset(&hp, 0, sizeof(hp));
+  for (size_t k = 0; k < m.vals.size(); ++k) {
+    hp.val[k] = m.vals[k];
+    hp.valf[k] = (float)m.vals[k];
+  }
+  hp.nvals = (int)m.vals.size();
+  for (int i = 0; i < L; ++i) {
+    hp.U[i] = m.U[i];
+    hp.Uf[i] = (float)m.U[i];
+    if (m.U[i] != 0.0) hp.umask |= 1u << i;
+  }
+  hp.uniform_u = 1;
+  for (int i = 0; i < L; ++i)
+    if (((hp.umask >> i) & 1u) && m.U[i] != hp.u0) {
+      if (hp.u0 == 0.0)
+        hp.u0 = m.U[i];
+      else
+        hp.uniform_u = 0;
     }
-    hp.uniform_u = 1;
-    for (int i = 0; i < L; ++i)
-      if (((hp.umask >> i) & 1u) && m.U[i] != hp.u0) {
-        if (hp.u0 == 0.0)
-          hp.u0 = m.U[i];
-        else
-          hp.uniform_u = 0;
-      }
-    hp.u0f = (float)hp.u0;
+  hp.u0f = (float)hp.u0;
 }
 
 // A cluster whose work runs on `stream` (owned by the caller) or, when stream is nullptr, on a

@@ -63,3 +63,26 @@ def test_footprint_rejects_bad_descriptions():
     c["t"] = t
     with pytest.raises(ed.EDError):
         ed.ed_request_bytes(c)
+
+
+def test_band_reserves_ring_unless_all_blocks_fit():
+    """A band request reserves every Krylov block only when they all fit the budget; one byte
+    less and it reserves its ring of blocks, the only storage it can then use."""
+    c = W.cdmft_2x2_bath()
+    full = ed.ed_request_bytes(c, n_freq=64, gf_method=ed.ED_GF_BAND, gf_budget=0)
+    ring = ed.ed_request_bytes(c, n_freq=64, gf_method=ed.ED_GF_BAND, gf_budget=1)
+    # the Green-function part of `full` is the budget at which everything fits
+    lo, hi = 1, full
+    while hi - lo > 1:  # smallest budget that still reserves the full storage
+        mid = (lo + hi) // 2
+        if ed.ed_request_bytes(c, n_freq=64, gf_method=ed.ED_GF_BAND, gf_budget=mid) == full:
+            hi = mid
+        else:
+            lo = mid
+    assert ed.ed_request_bytes(c, n_freq=64, gf_method=ed.ED_GF_BAND, gf_budget=hi) == full
+    assert ed.ed_request_bytes(c, n_freq=64, gf_method=ed.ED_GF_BAND, gf_budget=hi - 1) == ring
+    # continued fractions use whatever fits between one run's vectors and all runs'
+    cf_lo = ed.ed_request_bytes(c, n_freq=64, gf_budget=1)
+    cf_mid = ed.ed_request_bytes(c, n_freq=64, gf_budget=64 << 20)
+    cf_hi = ed.ed_request_bytes(c, n_freq=64, gf_budget=0)
+    assert cf_lo < cf_mid <= cf_hi
