@@ -15,6 +15,7 @@
 // alpha_n = <x,w>/<x,x> and b_{n+1}^2 = <w,w> - <x,w>^2/<x,x>, so the recursion never leaves
 // the device and repeated runs are bitwise identical.
 #include <algorithm>
+#include <atomic>
 
 #include "ed_common.cuh"
 
@@ -548,7 +549,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_up_cols(SectorView sv, HopParam
 }
 
 constexpr int kRowsPerCta = 64;
-static int g_smem_optin = -1;
+static std::atomic<int> g_smem_optin{-1};  // opt-in shared memory per block (read by concurrent lanes)
 
 static size_t down_rows_smem(const SectorView& sv, int dtype) {
   const size_t es = dtype == ED_FP64 ? 8 : 4;
@@ -563,13 +564,14 @@ static bool use_two_pass(const SectorView& sv, int dtype, const void* X, const v
   const int64_t need = (sv.d_dn + 32 * NV - 1) / (32 * NV) * (32 * NV);
   if (sv.ld < need || sv.ld % NV != 0) return false;
   if (((uintptr_t)X | (uintptr_t)O) % 16 != 0 || (vstride * es) % 16 != 0) return false;
-  if (g_smem_optin < 0) {
-    int dev = 0, v = 0;
+  int lim = g_smem_optin.load(std::memory_order_relaxed);
+  if (lim < 0) {
+    int dev = 0;
     ED_CUDA(cudaGetDevice(&dev));
-    ED_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    g_smem_optin = v;
+    ED_CUDA(cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    g_smem_optin.store(lim, std::memory_order_relaxed);
   }
-  return down_rows_smem(sv, dtype) <= (size_t)g_smem_optin;
+  return down_rows_smem(sv, dtype) <= (size_t)lim;
 }
 
 template <typename T>
