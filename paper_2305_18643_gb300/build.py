@@ -7,6 +7,7 @@ The library is written to paper_2305_18643_gb300/lib/libed.so; objects to _build
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import os
 import shutil
 import subprocess
@@ -59,17 +60,28 @@ def _compile(src, extra):
 
 
 def build(force=False, verbose=False):
-    """Compile every .cu under csrc/ and link libed.so; returns the library path."""
+    """Compile every .cu under csrc/ and link libed.so; returns the library path.
+
+    Processes that build at the same time (the ranks of a multi-GPU run) take turns on a file
+    lock, and the library is linked under a temporary name and renamed into place, so no
+    process loads a partly written libed.so."""
     os.makedirs(OBJDIR, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
-    srcs = sources()
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, {"force": force}), srcs))
-    if force or _stale(LIB, objs):
-        cmd = [nvcc()] + ARCH + ["-shared", "-o", LIB] + objs
-        r = subprocess.run(cmd, capture_output=True, text=True)
-        if r.returncode != 0:
-            raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))
+    with open(os.path.join(LIBDIR, ".build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            srcs = sources()
+            with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+                objs = list(ex.map(lambda s: _compile(s, {"force": force}), srcs))
+            if force or _stale(LIB, objs):
+                tmp = "%s.tmp%d" % (LIB, os.getpid())
+                cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs
+                r = subprocess.run(cmd, capture_output=True, text=True)
+                if r.returncode != 0:
+                    raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))
+                os.replace(tmp, LIB)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
     if verbose:
         print(LIB)
     return LIB
