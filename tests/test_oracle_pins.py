@@ -131,6 +131,20 @@ def test_free_fermion_ground_energy(seed, ns, nb, nu, nd):
     assert E0 == pytest.approx(eps[:nu].sum() + eps[:nd].sum(), abs=1e-11)
 
 
+@pytest.mark.parametrize("mu,eps,theta", [(1.0, -0.5, 0.7), (-0.3, 1.2, 0.4), (2.0, 2.0, 1.0)])
+def test_site_bath_pair_closed_form(mu, eps, theta):
+    """One site (on-site energy -mu) hybridized with one bath orbital (energy eps, coupling
+    theta, Eq. cdmft1), U = 0: the one-body levels are (e_s + eps)/2 -+ sqrt(((e_s - eps)/2)^2
+    + theta^2) with e_s = -mu, so E0 = 2 l_min with one electron of each spin and l_min with
+    one up electron alone."""
+    es = -mu
+    lmin = 0.5 * (es + eps) - math.sqrt((0.5 * (es - eps)) ** 2 + theta * theta)
+    for nu, nd, ref in ((1, 1, 2 * lmin), (1, 0, lmin)):
+        c = W._cluster("site+bath", np.zeros((1, 1)), 0.0, mu, nu, nd, eps=[eps], theta=[[theta]])
+        E0, _, _ = O.ground_state(O.sector_hamiltonian(_model(c), nu, nd))
+        assert E0 == pytest.approx(ref, abs=1e-13)
+
+
 @pytest.mark.parametrize("L,nu,nd,U,mu", [(6, 3, 3, 4.0, 2.0), (6, 4, 4, 3.0, 1.0), (7, 5, 3, 5.0, 0.5), (5, 1, 2, 2.0, -1.0)])
 def test_atomic_limit(L, nu, nd, U, mu):
     """t = 0: E0 = U max(0, N_up + N_dn - L) - mu (N_up + N_dn) for U > 0 (fewest double occupations)."""
