@@ -181,3 +181,41 @@ def real_grid(n_freq=1000, lo=-8.0, hi=8.0):
 def matsubara_grid(n_freq=2048, beta=50.0):
     """Fermionic Matsubara frequencies (2n + 1) pi / beta, n = 0 .. n_freq - 1."""
     return (2 * np.arange(n_freq) + 1) * np.pi / beta
+
+
+def square_superlattice(W, H, t=-1.0, tp=0.0):
+    """A square lattice (nearest-neighbour t, diagonal tp) tiled by W x H clusters (Sec. 2):
+    returns {"t_c": (L, L) cluster hops, "pos": (L, 2) site positions (x, y) with s = x + W y,
+    "E": super-lattice basis [[W, 0], [0, H]], "bonds": [(i, j, (n1, n2), t)]}.  A bond joins
+    site i of the cluster at the origin to site j of the cluster at n1 e_1 + n2 e_2; every lattice
+    bond leaving the cluster appears once (displacements (1,0), (0,1), (1,1), (-1,1) from each
+    site).  H = 1 with tp = 0 is a chain tiled by W-site clusters."""
+    L = W * H
+    t_c = np.zeros((L, L))
+    bonds = []
+    pos = np.array([[s % W, s // W] for s in range(L)], dtype=np.float64)
+    disps = [((1, 0), t), ((0, 1), t)] + ([((1, 1), tp), ((-1, 1), tp)] if tp != 0.0 else [])
+    if H == 1:
+        disps = [d for d in disps if d[0][1] == 0]
+    for s in range(L):
+        x, y = s % W, s // W
+        for (dx, dy), v in disps:
+            X, Y = x + dx, y + dy
+            n1, n2 = X // W, Y // H
+            j = (X - n1 * W) + W * (Y - n2 * H)
+            if (n1, n2) == (0, 0):
+                t_c[s, j] += v
+                t_c[j, s] += v
+            else:
+                bonds.append((s, j, (n1, n2) if H > 1 else (n1,), v))
+    E = np.array([[W, 0.0], [0.0, H]]) if H > 1 else np.array([[float(W)]])
+    return {"t_c": t_c, "pos": pos if H > 1 else pos[:, :1], "E": E, "bonds": bonds}
+
+
+def reduced_zone(E, ncells):
+    """The prod(ncells) wave vectors k~ of the super-lattice Brillouin zone that a periodic
+    lattice of ncells[a] clusters along e_a supports: k~ . e_a = 2 pi m_a / ncells[a]."""
+    E = np.atleast_2d(np.asarray(E, dtype=np.float64))
+    B = 2 * np.pi * np.linalg.inv(E).T          # rows b_a with b_a . e_b = 2 pi delta_ab
+    ms = np.array(list(np.ndindex(*[int(n) for n in ncells])), dtype=np.float64)
+    return (ms / np.asarray(ncells, dtype=np.float64)) @ B
