@@ -115,8 +115,17 @@ ed_status ed_green(ed_cluster* c, const double* omega, int n_freq, double eta, i
  *  ED_OPT_CF_MAX_STEPS  Lanczos steps per continued fraction [20000]
  *  ED_OPT_GF_TOL        a run stops once G on the grid changes by less than this between two
  *                       successive checks, twice [1e-10 for FP64, 1e-6 for FP32 vectors]
+ *  ED_OPT_TWO_PASS_MIN_BYTES
+ *                       H.psi on the library's own vectors (ground state, continued fractions,
+ *                       band Lanczos, ed_hpsi with rows padded to a multiple of 128) takes the
+ *                       two-pass kernels (a row pass for the down-spin hops and the diagonal, a
+ *                       column pass for the up-spin hops) once a vector holds at least this many
+ *                       bytes [33554432: beyond 32 MiB a vector no longer fits L2 comfortably];
+ *                       0 selects them at every size.  Both forms compute the same product; the
+ *                       option exists so that the two-pass kernels can be checked on sectors
+ *                       small enough for a CPU reference.  Must be >= 0.
  * ED_ERR_INVALID for an unknown option or a non-finite value. */
-enum { ED_OPT_BAND_MAX_DIM = 1, ED_OPT_CF_MAX_STEPS = 2, ED_OPT_GF_TOL = 3 };
+enum { ED_OPT_BAND_MAX_DIM = 1, ED_OPT_CF_MAX_STEPS = 2, ED_OPT_GF_TOL = 3, ED_OPT_TWO_PASS_MIN_BYTES = 4 };
 ed_status ed_set_option(ed_cluster* c, int option, double value);
 
 /* Statistics of the last ed_green: total Lanczos (or band) steps over all starting vectors and
@@ -129,7 +138,8 @@ ed_status ed_green_stats(const ed_cluster* c, int64_t* total_steps, int* max_ste
  * spin down (spin down equals spin up when n_up == n_dn), on z = omega + i eta (ED_AXIS_REAL)
  * or i omega (ED_AXIS_MATSUBARA); each continued fraction stops when it converges on the grid (as
  * in ed_green) or at the preset maximum of min(cf_max_levels, 2 d + 16) levels (cf_max_levels <= 0
- * selects 400; Sec. 4.3 stops at a preset maximum).  All clusters share `precision` (ED_FP64 or ED_FP32); each
+ * selects 20000, so that runs end on convergence: at eta = 0.05 on the real axis a sector of
+ * 1e4 - 3e4 states needs 1,500 - 3,000 levels for G to 1e-8; Sec. 4.3 stops at a preset maximum).  All clusters share `precision` (ED_FP64 or ED_FP32); each
  * cluster's seed and tol are taken from its description, its precision and gf_method are
  * ignored.  At most 20 orbitals per cluster.
  *  - E0, residual, status, iters (ground-state levels), gf_steps (continued-fraction levels over
@@ -172,7 +182,8 @@ typedef struct ed_request_opts {
   int n_freq;            /* 0: ground state only */
   double eta;            /* broadening of ED_AXIS_REAL */
   int axis;              /* ED_AXIS_REAL or ED_AXIS_MATSUBARA */
-  int cf_max_levels;     /* preset maximum of every continued fraction; <= 0 selects 400 */
+  int cf_max_levels;     /* preset maximum of every continued fraction; <= 0 selects 20000
+                            (runs end on convergence on the grid, as in ed_green) */
   double* G_out;         /* host, complex128 [2 spins][n_freq][n_sites][n_sites]; written before
                             ed_poll / ed_wait report completion; the caller keeps it alive until
                             then (NULL allowed when n_freq == 0) */
@@ -286,6 +297,9 @@ ed_status ed_hpsi(ed_cluster* c, int n_up, int n_dn, int dtype, const void* x, v
  *  - x, y: device arrays of d_up rows with leading dimension ld (ld <= 0 means d_dn), dtype
  *    ED_FP64 or ED_FP32; they must not overlap.  out3: 3 doubles of device memory.
  *  - Sectors larger than 4,194,304 elements (d_up * d_dn) are rejected with ED_ERR_TOO_LARGE.
+ *  - The current device must be the one the cluster was created on (its tables live there);
+ *    otherwise ED_ERR_INVALID, before any launch.  ed_ground_state, ed_ground_vector, ed_green,
+ *    ed_hop_table and ed_hpsi make the same check.
  *  - The first call on a device looks up the scratch array's device address (once per device,
  *    with that device current); make that first call before any stream capture.
  *  - Every call shares the scratch array, and the array keeps the last call's contents; calls
@@ -294,6 +308,77 @@ ed_status ed_hpsi(ed_cluster* c, int n_up, int n_dn, int dtype, const void* x, v
  *  - Asynchronous on `stream` (NULL is the CUDA default stream). */
 ed_status ed_hpsi_dots_static(ed_cluster* c, int dtype, const void* x, void* y, int64_t ld, double* out3,
                               void* stream);
+
+/* ---- lattice steps on the cluster Green function: CPT (Sec. 3) and the CDMFT bath fit (Sec. 6) -- */
+
+/* A lattice tiled by identical clusters of L sites (Sec. 2): site i of the cluster at super-lattice
+ * vector r~ = n E (n an integer vector, E the super-lattice basis) sits at r~ + pos[i].  The
+ * one-body terms that join different clusters are listed as bonds: bond q joins site
+ * bonds[q (2 + dim)] of the cluster at the origin to site bonds[q (2 + dim) + 1] of the cluster at
+ * n = (bonds[q (2 + dim) + 2], ...), with the matrix element bond_t[q] (the Hermitian partner is
+ * implied).  Hops inside the cluster belong to the cluster's own t and are not listed.  Host
+ * arrays, read during the call only. */
+typedef struct ed_superlattice {
+  int n_sites;            /* L, 1 <= L <= 32 */
+  int dim;                /* D = 1, 2 or 3 */
+  const double* pos;      /* L x D site positions */
+  const double* E;        /* D x D super-lattice basis, rows e_1 .. e_D */
+  int n_bonds;
+  const int* bonds;       /* n_bonds x (2 + D) */
+  const double* bond_t;   /* n_bonds */
+} ed_superlattice;
+
+enum { ED_CPT_MATRIX = 0, ED_CPT_PERIODIZED = 1, ED_CPT_AVERAGE = 2 };
+
+/* Hybridization function Gamma_{mu nu}(z) = sum_a theta_{mu a} theta_{nu a} / (z - eps_a)
+ * (Eq. hybridization) on nz complex frequencies z (interleaved re, im; host).  eps: n_bath, theta:
+ * n_sites x n_bath row-major (host).  Gamma_out: complex128 [nz][n_sites][n_sites], host or device
+ * as out_is_device says.  Synchronous.  ED_ERR_INVALID for bad sizes or NULL arrays. */
+ed_status ed_hybridization(int n_sites, int n_bath, const double* eps, const double* theta, const double* z, int nz,
+                           double* Gamma_out, int out_is_device);
+
+/* Cluster perturbation theory on nk wave vectors kt (nk x D, host) from the cluster Green function
+ * Gc (complex128 [nz][L][L], e.g. the output of ed_green):
+ *   ED_CPT_MATRIX      out [nk][nz][L][L] = G(k~, z) = [Gc(z)^-1 + Gamma(z) - V(k~)]^-1
+ *                      (Eq. CPT1; with the bath compensation of Eq. CPT_CDMFT when Gamma, complex128
+ *                      [nz][L][L], is not NULL)
+ *   ED_CPT_PERIODIZED  out [nk][nz] = (1/L) sum_{R R'} e^{-i k.(R - R')} G_{R R'}(k, z) (Eq. CPT3,
+ *                      the Green-function periodization, k~ taken equal to k)
+ *   ED_CPT_AVERAGE     out [nz][L][L] = the mean of G(k~, z) over the nk given k~, i.e. the
+ *                      super-lattice-averaged Green function of the CDMFT loop (Sec. 6, step 3)
+ *                      when kt is a grid of the reduced Brillouin zone.
+ * V(k~)_{ij} = sum over bonds of t e^{i k~.r~} at (i, j) and its conjugate at (j, i) (the mixed
+ * representation of Sec. 2.2).  Gc, Gamma and out are host or device arrays as io_is_device says.
+ * Synchronous.  ED_ERR_INVALID for a bad lattice or mode, or when a matrix to invert is singular. */
+ed_status ed_cpt_green(const ed_superlattice* lat, const double* Gc, const double* Gamma, int nz, const double* kt, int nk,
+                       int mode, double* out, int io_is_device);
+
+/* The fixed part of the CDMFT distance (Sec. 6, steps 3-4): from the cluster Green function Gc of
+ * the impurity solved with the current bath, that bath's Gamma (may be NULL: no bath) and the
+ * reduced-zone grid kt, A(z) = Gamma(z) + Gc(z)^-1 - G_bar(z)^-1, which equals
+ * z - h_c - calG_0(z)^-1 with calG_0^-1 = G_bar^-1 + Sigma_c, so that Eq. dist_func reads
+ * d = sum_n W_n ||A(z_n) - Gamma'(z_n)||_F^2 for a trial bath Gamma'.  A_out: complex128
+ * [nz][L][L]; Gc, Gamma, A_out host or device as io_is_device says.  Synchronous. */
+ed_status ed_cdmft_target(const ed_superlattice* lat, const double* Gc, const double* Gamma, int nz, const double* kt,
+                          int nk, double* A_out, int io_is_device);
+
+/* The distance of Eq. dist_func, d_c = sum_n W_n ||A(z_n) - Gamma_c(z_n)||_F^2, for n_cand trial
+ * baths at once (eps: n_cand x n_bath, theta: n_cand x n_sites x n_bath), and, when grad_out is
+ * not NULL, its gradient: grad_out[c][a] = dd/deps_a, grad_out[c][n_bath + mu n_bath + a] =
+ * dd/dtheta_{mu a}.  z: nz complex frequencies, weights: nz values W_n >= 0, A: complex128
+ * [nz][n_sites][n_sites] from ed_cdmft_target; all host arrays.  Synchronous. */
+ed_status ed_cdmft_distance(int n_sites, int n_bath, int n_cand, const double* eps, const double* theta, const double* z,
+                            int nz, const double* weights, const double* A, double* d_out, double* grad_out);
+
+/* Bath fit of the CDMFT loop (Sec. 6, step 4): minimizes the distance over the bath energies and
+ * the hybridizations theta_{mu a} with theta_free[mu n_bath + a] != 0 (theta_free NULL: all),
+ * starting from eps and theta, which receive the result (host arrays).  BFGS with a backtracking
+ * line search on the host; every distance and gradient is computed by ed_cdmft_distance's kernels.
+ * Stops when the largest gradient component is below gtol (<= 0: 1e-10), when a step no longer
+ * lowers d, or after max_iter iterations (<= 0: 500).  d_out, iters_out may be NULL.  Synchronous. */
+ed_status ed_cdmft_fit(int n_sites, int n_bath, double* eps, double* theta, const unsigned char* theta_free,
+                       const double* z, int nz, const double* weights, const double* A, double gtol, int max_iter,
+                       double* d_out, int* iters_out);
 
 /* ---- measurement of the library's own kernels (no counterpart in the paper) --------------- */
 
@@ -309,7 +394,8 @@ enum {
   ED_K_GF_EVAL = 7,       /* Green-function evaluation and assembly on the grid */
   ED_K_BAND = 8,          /* band-Lanczos orthogonalization */
   ED_K_BATCH = 9,         /* persistent kernels of the batched form */
-  ED_K_COUNT = 10
+  ED_K_LATTICE = 10,      /* CPT and CDMFT kernels (batched small-matrix inversions, distance) */
+  ED_K_COUNT = 11
 };
 
 /* Turns per-family timing on (1) or off (0) and clears the totals.  While on, each launch of a

@@ -47,7 +47,8 @@ import scipy.sparse.linalg as spla
 __all__ = [
     "popcount", "one_body_matrix", "Model", "sector_basis", "basis_index",
     "hopping_matrix", "hop_entries", "interaction_diagonal", "sector_hamiltonian",
-    "apply_h", "apply_h_rows", "apply_h_sampled", "jw_hamiltonian_dense", "ground_state",
+    "apply_h", "apply_h_rows", "row_tables", "apply_h_rows_tables", "apply_h_sampled",
+    "jw_hamiltonian_dense", "ground_state",
     "apply_cdag", "apply_c", "density", "green_exact", "lanczos_coefficients",
     "cf_green", "green_cf", "band_lanczos_lehmann", "lehmann_green", "green_band",
     "frequency_grid",
@@ -221,16 +222,28 @@ def apply_h(op, psi):
     return op.matvec(np.asarray(psi).reshape(-1)).reshape(op.shape2)
 
 
-def apply_h_rows(model, n_up, n_dn, psi, rows):
-    """Rows y[rows, :] of y = H psi from Eq. factorized, without building the full operator:
-    y[u, :] = sum_u' K_up[u, u'] psi[u', :] + psi[u, :] K_dn^T + V_int[u, :] * psi[u, :]."""
+def row_tables(model, n_up, n_dn, rows):
+    """The pieces of Eq. factorized that rows y[rows, :] of y = H psi need: the rows of K_up, all
+    of K_dn and the rows of the interaction diagonal."""
     rows = np.asarray(rows)
     B_up = sector_basis(model.L, n_up)
     B_dn = sector_basis(model.L, n_dn)
     K_up = hopping_matrix(model.h, n_up)
     K_dn = hopping_matrix(model.h, n_dn)
-    V = interaction_diagonal(model, B_up[rows], B_dn)
-    return K_up[rows] @ psi + (K_dn @ psi[rows].T).T + V * psi[rows]
+    return K_up[rows], K_dn, interaction_diagonal(model, B_up[rows], B_dn)
+
+
+def apply_h_rows_tables(tables, psi, rows):
+    """y[rows, :] = sum_u' K_up[u, u'] psi[u', :] + psi[u, :] K_dn^T + V_int[u, :] * psi[u, :]
+    (Eq. factorized) from the pieces of row_tables."""
+    K_up_rows, K_dn, V = tables
+    rows = np.asarray(rows)
+    return K_up_rows @ psi + (K_dn @ psi[rows].T).T + V * psi[rows]
+
+
+def apply_h_rows(model, n_up, n_dn, psi, rows):
+    """Rows y[rows, :] of y = H psi from Eq. factorized, without building the full operator."""
+    return apply_h_rows_tables(row_tables(model, n_up, n_dn, rows), psi, rows)
 
 
 def apply_h_sampled(op, psi, us, ds):
@@ -309,17 +322,19 @@ def jw_hamiltonian_dense(model, n_up, n_dn):
 # Sec. 4.2: ground state (the plain definition: lowest eigenpair of H in the sector)
 # ---------------------------------------------------------------------------------------
 
-def ground_state(op, dense_limit=6000, k=2):
+def ground_state(op, dense_limit=6000, k=2, tol=1e-14):
     """Lowest eigenvalue E0, eigenvector Omega[u, d] (unit norm) and gap E1 - E0 of H.
 
-    Dense LAPACK (numpy.linalg.eigh) up to ``dense_limit`` states, else ARPACK (eigsh).
+    Dense LAPACK (numpy.linalg.eigh) up to ``dense_limit`` states, else ARPACK (eigsh) with
+    relative tolerance ``tol`` on the Ritz pairs (the eigenvalue error is of order tol^2 |E|
+    for a Hermitian operator, so 1e-12 is ample for a 1e-10 check on E0).
     """
     if op.dim <= dense_limit:
         w, V = np.linalg.eigh(op.sparse().toarray())
         gap = w[1] - w[0] if len(w) > 1 else np.inf
         return w[0], V[:, 0].reshape(op.shape2), gap
     v0 = np.cos(np.arange(op.dim) * 0.7) + 1.0
-    w, V = spla.eigsh(op.linear_operator(), k=k, which="SA", tol=1e-14, v0=v0, ncv=max(20, 2 * k + 1))
+    w, V = spla.eigsh(op.linear_operator(), k=k, which="SA", tol=tol, v0=v0, ncv=max(20, 2 * k + 1))
     order = np.argsort(w)
     w, V = w[order], V[:, order]
     return w[0], V[:, 0].reshape(op.shape2), (w[1] - w[0]) if k > 1 else np.inf

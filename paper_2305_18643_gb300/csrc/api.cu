@@ -61,6 +61,16 @@ static void require(bool ok, const std::string& msg) {
 
 static bool is_finite(double x) { return std::isfinite(x); }
 
+// The cluster's tables and buffers live on the device it was created on; a call that launches
+// work must find that device current (caller pointers are addresses on the current device).
+static void require_cluster_device(const ed_cluster* c) {
+  int dev = -1;
+  ED_CUDA(cudaGetDevice(&dev));
+  if (dev != c->device)
+    throw Error(ED_ERR_INVALID, "the current device (" + std::to_string(dev) + ") is not the cluster's device (" +
+                                    std::to_string(c->device) + ")");
+}
+
 // Validates a cluster description and builds the one-body matrix h (Eq. Hubbard with the bath
 // terms of Eq. cdmft1), the list of hopping pairs and the kernel parameters.
 void build_model(const ed_cluster_desc* desc, ModelHost& m, HopParams& hp) {
@@ -191,6 +201,7 @@ SectorView ed_cluster::view(int n_up, int n_dn, int64_t ld) {
   v.e_dn = d.ediag.p;
   v.e_up32 = u.ediag32.p;
   v.e_dn32 = d.ediag32.p;
+  v.two_pass_min_bytes = two_pass_min_bytes;
   return v;
 }
 
@@ -221,6 +232,7 @@ void ed_cluster_destroy(ed_cluster* c) {
 ed_status ed_ground_state(ed_cluster* c, double* E0, double* residual, int* iters) {
   return guarded([&]() -> ed_status {
     require(c != nullptr, "cluster is NULL");
+    require_cluster_device(c);
     GroundResult r = run_ground_state(*c, c->desc.precision, c->desc.tol, c->desc.max_iter, c->desc.seed);
     c->gs = r;
     c->have_gs = true;
@@ -235,6 +247,7 @@ ed_status ed_ground_state(ed_cluster* c, double* E0, double* residual, int* iter
 ed_status ed_ground_vector(ed_cluster* c, double* out, int out_is_device) {
   return guarded([&]() -> ed_status {
     require(c != nullptr && out != nullptr, "cluster and out must not be NULL");
+    require_cluster_device(c);
     if (!c->have_gs) throw Error(ED_ERR_STATE, "no ground state yet");
     int64_t n = (int64_t)binomial(c->model.L, c->desc.n_up) * (int64_t)binomial(c->model.L, c->desc.n_dn);
     ED_CUDA(cudaMemcpyAsync(out, c->omega.p, n * sizeof(double), out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
@@ -252,6 +265,7 @@ ed_status ed_green(ed_cluster* c, const double* omega, int n_freq, double eta, i
     require(axis == ED_AXIS_REAL || axis == ED_AXIS_MATSUBARA, "axis must be ED_AXIS_REAL or ED_AXIS_MATSUBARA");
     require(spin == 0 || spin == 1, "spin must be 0 or 1");
     require(is_finite(eta), "eta is not finite");
+    require_cluster_device(c);
     ed_status st = ED_OK;
     if (!c->have_gs) {
       st = ed_ground_state(c, nullptr, nullptr, nullptr);
@@ -291,6 +305,10 @@ ed_status ed_set_option(ed_cluster* c, int option, double value) {
       case ED_OPT_BAND_MAX_DIM: c->band_max_dim = (int)value; break;
       case ED_OPT_CF_MAX_STEPS: c->cf_max_steps = (int)value; break;
       case ED_OPT_GF_TOL: c->gf_tol = value; break;
+      case ED_OPT_TWO_PASS_MIN_BYTES:
+        require(value >= 0.0, "ED_OPT_TWO_PASS_MIN_BYTES must be >= 0");
+        c->two_pass_min_bytes = value >= 9.0e18 ? INT64_MAX : (int64_t)value;
+        break;
       default: throw Error(ED_ERR_INVALID, "unknown option");
     }
     return ED_OK;
@@ -332,6 +350,7 @@ ed_status ed_hop_table(ed_cluster* c, int N, int32_t* row_ptr, uint32_t* entries
                        int64_t* n_entries, int* n_values) {
   return guarded([&]() -> ed_status {
     require(c != nullptr, "cluster is NULL");
+    require_cluster_device(c);
     SpinTables& t = c->tables(N);
     if (n_entries) *n_entries = t.nnz;
     if (n_values) *n_values = (int)c->model.vals.size();
@@ -349,6 +368,7 @@ ed_status ed_hpsi(ed_cluster* c, int n_up, int n_dn, int dtype, const void* x, v
   return guarded([&]() -> ed_status {
     require(c != nullptr && x != nullptr && y != nullptr, "cluster, x and y must not be NULL");
     require(dtype == ED_FP64 || dtype == ED_FP32, "dtype must be ED_FP64 or ED_FP32");
+    require_cluster_device(c);
     SectorView sv = c->view(n_up, n_dn, ld);
     require(ld <= 0 || ld >= sv.d_dn, "ld must be >= d_dn (or <= 0 for d_dn)");
     cudaStream_t s = (cudaStream_t)stream;  // NULL is the CUDA default stream

@@ -1327,7 +1327,7 @@ extern "C" ed_status ed_batch_solve(const ed_cluster_desc* descs, int n, int pre
       Gd.alloc(std::max<int64_t>(total, 1));
       Gdev = Gd.p;
     }
-    batch_solve(descs, n, precision, z.data(), n_freq, n_freq > 0, cf_max_levels > 0 ? cf_max_levels : 400, E0,
+    batch_solve(descs, n, precision, z.data(), n_freq, n_freq > 0, cf_max_levels > 0 ? cf_max_levels : kCfDefaultMaxLevels, E0,
                 residual, status, iters, gf_steps, Gdev, s, 0, 0);
     if (n_freq > 0 && !out_is_device) {
       ED_CUDA(cudaMemcpyAsync(G_out, Gd.p, total * sizeof(double2), cudaMemcpyDeviceToHost, s));

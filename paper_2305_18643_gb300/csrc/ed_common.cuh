@@ -53,7 +53,7 @@ void set_last_error(const std::string& msg);
 // Kernel families timed by the profiler (ed_profile_* in ed.h).
 enum KernelId {
   K_TABLES = 0, K_HPSI, K_LANCZOS_STEP, K_LANCZOS_NEXT, K_TRIDIAG, K_VECTOR, K_APPLY_COP, K_GF_EVAL,
-  K_BAND, K_BATCH, K_COUNT
+  K_BAND, K_BATCH, K_LATTICE, K_COUNT
 };
 const char* kernel_name(int kid);
 void note_launch();  // counts a launch that is timed inside another kernel's scope
@@ -201,7 +201,16 @@ struct SectorView {
   const double* e_dn;
   const float* e_up32;
   const float* e_dn32;
+  int64_t two_pass_min_bytes;  // vectors of at least this many bytes take the two-pass H.psi
 };
+
+// Preset maximum of a continued fraction of the batched and served forms when the caller gives
+// none: high enough that runs stop on convergence on the grid (a 10-orbital sector of ~2.5e4
+// states needs about 3,000 levels for 1e-8 on the real axis at eta = 0.05).
+constexpr int kCfDefaultMaxLevels = 20000;
+
+// Default of ED_OPT_TWO_PASS_MIN_BYTES: a vector of 32 MiB no longer sits comfortably in L2.
+constexpr int64_t kTwoPassMinBytes = int64_t(32) << 20;
 
 struct RankView {
   const int32_t* lo;
@@ -261,9 +270,10 @@ int lanczos_blocks(const SectorView& sv);   // partial-sum slots per run of the 
 int two_pass_blocks(const SectorView& sv, int dtype);
 
 // lanczos.cu
+// omega (contiguous) += coef[n + 1] v_{n+1}; its type is omega_dtype (< 0: the vectors' dtype).
 void launch_lanczos_next(int dtype, void* W, const void* X, int64_t d_up, int64_t d_dn, int64_t ld,
                          int64_t vstride, int runs, int n, const LanczosScalars& ls,
-                         void* omega, const double* coef, cudaStream_t s);  // omega: dtype, contiguous
+                         void* omega, const double* coef, cudaStream_t s, int omega_dtype = -1);
 void launch_start_vector(int dtype, void* v, int64_t d_up, int64_t d_dn, int64_t ld, uint64_t seed,
                          cudaStream_t s);
 // Reductions into a device double: out = <a, b> over d_up x d_dn (two-stage, fixed order).
@@ -307,6 +317,7 @@ struct ed_cluster {
   bool gf_converged = true;
   size_t gf_mem_budget = 0;    // bytes for Green-function Lanczos vectors (0: default)
   int gf_max_steps = 0;
+  int64_t two_pass_min_bytes = ed::kTwoPassMinBytes;  // ED_OPT_TWO_PASS_MIN_BYTES
   ed::SpinTables& tables(int N);
   ed::SectorView view(int n_up, int n_dn, int64_t ld);
 };

@@ -10,6 +10,7 @@
 namespace ed {
 
 constexpr int kCheck = 10;
+constexpr int kRefineRounds = 4;  // FP64 refinement rounds of an FP32-storage ground state
 
 __global__ void k_scale_inv_sqrt(int dt, void* v, const double* nrm2, int64_t du, int64_t dd, int64_t ld) {
   double f = *nrm2 > 0.0 ? 1.0 / sqrt(*nrm2) : 0.0;
@@ -125,6 +126,69 @@ static int lanczos_pass(ed_cluster& c, const SectorView& sv, int dtype, LanczosR
   return m;
 }
 
+// One round of FP64 refinement of a ground state found with FP32 vectors.  The Lanczos recursion
+// of Sec. 4.2 is restarted from the FP64 vector omega itself: q_0 = omega, a_0 = E (its Rayleigh
+// quotient), b_1 q_1 = r = H omega - E omega (computed in FP64 by the caller), and the later
+// q_n are stored in FP32.  The lowest Ritz vector s of the tridiagonal matrix gives
+// omega <- s_0 omega + s_1 r / |r| + sum_{n >= 2} s_n q_n, summed in FP64 by retracing the recursion.
+// The correction sum_{n >= 1} s_n q_n has norm ~|r| / gap, so the FP32 rounding of the q_n
+// (relative 6e-8) reaches omega only at ~6e-8 |r| / gap: every round multiplies the residual by
+// ~6e-8 |H| / gap, and one or two rounds bring an FP32 ground state (residual ~1e-7 |E|) to the
+// 1e-12 of an FP64 one.  V0, V1: FP32 work vectors with leading dimension sv.ld (padding zero);
+// r is contiguous FP64 and is read only.  Returns the number of levels.
+static int refine_round(ed_cluster& c, const SectorView& sv, LanczosRun& L, float* V0, float* V1, double* omega,
+                        const double* r, double E, double rnorm, double tol_ritz, DevBuf<double>& scal, double* host,
+                        cudaStream_t s) {
+  const int64_t du = sv.d_up, dd = sv.d_dn, ld = sv.ld;
+  float* V[2] = {V0, V1};
+  int m = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    L.reset(s);
+    const double a0 = E, b1 = rnorm, inv = 1.0 / rnorm;
+    ED_CUDA(cudaMemcpyAsync(L.alpha.p, &a0, sizeof(double), cudaMemcpyHostToDevice, s));
+    ED_CUDA(cudaMemcpyAsync(L.beta.p + 1, &b1, sizeof(double), cudaMemcpyHostToDevice, s));
+    ED_CUDA(cudaMemcpyAsync(scal.p + 5, &inv, sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_copy_ld(ED_FP32, V[0], ld, ED_FP64, omega, dd, nullptr, du, dd, s);       // q_0
+    launch_copy_ld(ED_FP32, V[1], ld, ED_FP64, r, dd, scal.p + 5, du, dd, s);        // q_1 = r / |r|
+    if (pass == 1) {
+      // omega <- s_0 omega + (s_1 / |r|) r, in FP64; the loop adds s_n q_n for n >= 2
+      double sv01[2];
+      ED_CUDA(cudaMemcpyAsync(sv01, L.svec.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      ED_CUDA(cudaStreamSynchronize(s));
+      const double cc[2] = {sv01[0], m > 1 ? sv01[1] * inv : 0.0};
+      ED_CUDA(cudaMemcpyAsync(scal.p + 5, cc, 2 * sizeof(double), cudaMemcpyHostToDevice, s));
+      launch_axpby(ED_FP64, omega, ED_FP64, omega, scal.p + 5, ED_FP64, r, scal.p + 6, du, dd, dd, s);
+    }
+    int cur = 1;
+    const int nmax = pass == 0 ? L.M : m - 1;
+    for (int n = 1; n < nmax; ++n) {
+      launch_lanczos_step(sv, c.hp, ED_FP32, V[cur], V[cur ^ 1], 0, 1, n, L.ls, L.nblk, s);
+      launch_lanczos_next(ED_FP32, V[cur ^ 1], V[cur], du, dd, ld, 0, 1, n, L.ls, pass == 1 ? omega : nullptr, L.svec.p,
+                          s, ED_FP64);
+      cur ^= 1;
+      if (pass == 0 && ((n + 1) % kCheck == 0 || n + 1 == L.M)) {
+        ED_CUDA(cudaMemcpyAsync(host + 8, L.active.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        ED_CUDA(cudaStreamSynchronize(s));
+        const int act = *(int*)(host + 8);
+        int levels = n + 1;
+        if (!act) {
+          std::vector<double> b(n + 2);
+          ED_CUDA(cudaMemcpyAsync(b.data(), L.beta.p, (n + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
+          ED_CUDA(cudaStreamSynchronize(s));
+          levels = 2;
+          while (levels < n + 1 && b[levels] > L.ls.btol) ++levels;
+        }
+        launch_tridiag_lowest(L.alpha.p, L.beta.p, levels, L.evals.p, L.svec.p, s);
+        ED_CUDA(cudaMemcpyAsync(host, L.evals.p, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        ED_CUDA(cudaStreamSynchronize(s));
+        m = levels;
+        if (!act || host[2] < tol_ritz) break;
+      }
+    }
+  }
+  return m;
+}
+
 GroundResult run_ground_state(ed_cluster& c, int dtype, double tol, int max_iter, uint64_t seed) {
   cudaStream_t s = c.stream;
   const int nu = c.desc.n_up, nd = c.desc.n_dn;
@@ -172,32 +236,41 @@ GroundResult run_ground_state(ed_cluster& c, int dtype, double tol, int max_iter
     int m = lanczos_pass(c, sv, dt, L, V0.p, V1.p, Vs.p, acc, tol_ritz, host, &breakdown, s);
     if (dt == ED_FP32) launch_copy_ld(ED_FP64, c.omega.p, dd, ED_FP32, om32.p, dd, nullptr, du, dd, s);
     total_iters += m;
-    const double lam0 = host[0], lam1 = host[1], ritz = host[2];
-    // FP64 polish: normalize omega, Rayleigh quotient and explicit residual.
-    launch_dot(ED_FP64, c.omega.p, ED_FP64, c.omega.p, du, dd, dd, part.p, nblk + 8, scal.p + 1, s);
-    axpby_inv_sqrt(ED_FP64, c.omega.p, scal.p + 1, du, dd, dd, s);
-    launch_hpsi(svc, c.hp, ED_FP64, c.omega.p, y64.p, s);
-    launch_dot(ED_FP64, c.omega.p, ED_FP64, y64.p, du, dd, dd, part.p, nblk + 8, scal.p + 2, s);
-    axpy_neg(y64.p, scal.p + 2, c.omega.p, dim, s);  // y <- y - E omega
-    launch_dot(ED_FP64, y64.p, ED_FP64, y64.p, du, dd, dd, part.p, nblk + 8, scal.p + 3, s);
-    ED_CUDA(cudaMemcpyAsync(host + 4, scal.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
-    ED_CUDA(cudaStreamSynchronize(s));
-    const double E = host[6];
-    const double res_abs = std::sqrt(std::max(0.0, host[7]));
-    const double scale = std::max(1.0, std::fabs(E));
+    const double lam0 = host[0], lam1 = host[1];
+    // FP64 polish: normalize omega, Rayleigh quotient E and explicit residual r = H omega - E omega
+    // (left in y64), all with the FP64 operator.
+    double E = 0.0, res_abs = 0.0;
+    auto polish = [&]() {
+      launch_dot(ED_FP64, c.omega.p, ED_FP64, c.omega.p, du, dd, dd, part.p, nblk + 8, scal.p + 1, s);
+      axpby_inv_sqrt(ED_FP64, c.omega.p, scal.p + 1, du, dd, dd, s);
+      launch_hpsi(svc, c.hp, ED_FP64, c.omega.p, y64.p, s);
+      launch_dot(ED_FP64, c.omega.p, ED_FP64, y64.p, du, dd, dd, part.p, nblk + 8, scal.p + 2, s);
+      axpy_neg(y64.p, scal.p + 2, c.omega.p, dim, s);  // y <- y - E omega
+      launch_dot(ED_FP64, y64.p, ED_FP64, y64.p, du, dd, dd, part.p, nblk + 8, scal.p + 3, s);
+      ED_CUDA(cudaMemcpyAsync(host + 4, scal.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      ED_CUDA(cudaStreamSynchronize(s));
+      E = host[6];
+      res_abs = std::sqrt(std::max(0.0, host[7]));
+    };
+    polish();
+    double scale = std::max(1.0, std::fabs(E));
+    // a breakdown of the recursion (invariant subspace) is exact only with FP64 vectors
+    bool ok = res_abs <= tol * scale || (breakdown && dt == ED_FP64);
+    if (!ok && dt == ED_FP32) {
+      // FP32 storage: FP64 refinement rounds (refine_round) until the FP64 residual meets tol
+      for (int round = 0; round < kRefineRounds && !ok; ++round) {
+        const double ritz_stop = std::max(0.1 * tol * scale, 1e-6 * res_abs);
+        total_iters += refine_round(c, sv, L, (float*)V0.p, (float*)V1.p, c.omega.p, y64.p, E, res_abs, ritz_stop, scal,
+                                    host, s);
+        polish();
+        scale = std::max(1.0, std::fabs(E));
+        ok = res_abs <= tol * scale;
+      }
+    }
     R.E0 = E;
     R.residual = res_abs / scale;
     R.iters = total_iters;
     R.gap = lam1 - lam0;
-    (void)ritz;
-    bool ok;
-    if (dtype == ED_FP64 || dt == ED_FP64) {
-      ok = R.residual <= tol || breakdown;
-    } else {
-      // FP32 storage: accept when the Kato-Temple bound on the Rayleigh quotient meets 1e-10.
-      double gap = lam1 - E;
-      ok = gap > 0.0 && res_abs * res_abs / gap <= 1e-10 * scale * 0.1;
-    }
     R.degenerate = (lam1 - lam0) < 1e-8 * std::max(1.0, std::fabs(lam0));
     if (ok) {
       R.converged = true;

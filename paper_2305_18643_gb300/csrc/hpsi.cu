@@ -18,93 +18,11 @@
 #include <atomic>
 
 #include "ed_common.cuh"
+#include "hpsi_element.cuh"
 
 namespace ed {
 
 constexpr int kThreads = 256;
-
-template <typename T>
-struct Prec;
-template <>
-struct Prec<double> {
-  __device__ static const double* e_up(const SectorView& s) { return s.e_up; }
-  __device__ static const double* e_dn(const SectorView& s) { return s.e_dn; }
-  __device__ static double val(const HopParams& h, int i) { return h.val[i]; }
-  __device__ static double U(const HopParams& h, int i) { return h.U[i]; }
-};
-template <>
-struct Prec<float> {
-  __device__ static const float* e_up(const SectorView& s) { return s.e_up32; }
-  __device__ static const float* e_dn(const SectorView& s) { return s.e_dn32; }
-  __device__ static float val(const HopParams& h, int i) { return h.valf[i]; }
-  __device__ static float U(const HopParams& h, int i) { return h.Uf[i]; }
-};
-
-// Deterministic block reduction of three FP64 sums (fixed shuffle tree, fixed warp order).
-__device__ __forceinline__ void block_sum3(double& a, double& b, double& c) {
-  __shared__ double sm[3][kThreads / 32];
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_down_sync(0xffffffffu, a, o);
-    b += __shfl_down_sync(0xffffffffu, b, o);
-    c += __shfl_down_sync(0xffffffffu, c, o);
-  }
-  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) {
-    sm[0][w] = a;
-    sm[1][w] = b;
-    sm[2][w] = c;
-  }
-  __syncthreads();
-  if (w == 0) {
-    a = l < kThreads / 32 ? sm[0][l] : 0.0;
-    b = l < kThreads / 32 ? sm[1][l] : 0.0;
-    c = l < kThreads / 32 ? sm[2][l] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_down_sync(0xffffffffu, a, o);
-      b += __shfl_down_sync(0xffffffffu, b, o);
-      c += __shfl_down_sync(0xffffffffu, c, o);
-    }
-  }
-  __syncthreads();
-}
-
-template <typename T>
-__device__ __forceinline__ T hpsi_element(const SectorView& sv, const T* __restrict__ sval, const T* __restrict__ sU,
-                                          uint32_t umask, const T* __restrict__ X, int64_t u, int64_t d) {
-  const T* xr = X + u * sv.ld;
-  uint32_t bu = sv.B_up[u], bd = sv.B_dn[d];
-  T diag = Prec<T>::e_up(sv)[u] + Prec<T>::e_dn(sv)[d];
-  uint32_t dbl = bu & bd & umask;
-  while (dbl) {
-    int i = __ffs(dbl) - 1;
-    diag += sU[i];
-    dbl &= dbl - 1u;
-  }
-  T acc = diag * xr[d];
-  int32_t p0 = sv.ptr_dn[d], p1 = sv.ptr_dn[d + 1];
-  for (int32_t k = p0; k < p1; ++k) {
-    uint32_t e = __ldg(sv.ent_dn + k);
-    T v = sval[ent_vidx(e)];
-    T x = __ldg(xr + ent_col(e));
-    acc += ent_neg(e) ? -v * x : v * x;
-  }
-  p0 = sv.ptr_up[u];
-  p1 = sv.ptr_up[u + 1];
-  for (int32_t k = p0; k < p1; ++k) {
-    uint32_t e = __ldg(sv.ent_up + k);
-    T v = sval[ent_vidx(e)];
-    T x = __ldg(X + (int64_t)ent_col(e) * sv.ld + d);
-    acc += ent_neg(e) ? -v * x : v * x;
-  }
-  return acc;
-}
-
-template <typename T>
-__device__ __forceinline__ void load_params(const HopParams& hp, T* sval, T* sU) {
-  for (int i = threadIdx.x; i < kMaxVals; i += blockDim.x) sval[i] = Prec<T>::val(hp, i);
-  for (int i = threadIdx.x; i < kMaxOrb; i += blockDim.x) sU[i] = Prec<T>::U(hp, i);
-  __syncthreads();
-}
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_hpsi_flat(SectorView sv, HopParams hp, const T* __restrict__ X,
@@ -145,7 +63,7 @@ __global__ void __launch_bounds__(kThreads) k_lanczos_step(SectorView sv, HopPar
     sww += wd * wd;
     sxx += x * x;
     });
-  block_sum3(sxw, sww, sxx);
+  block_sum3<kThreads>(sxw, sww, sxx);
   double* part = ls.partial + ((int64_t)run * gridDim.x) * 3;
   if (threadIdx.x == 0) {
     part[blockIdx.x * 3 + 0] = sxw;
@@ -164,7 +82,7 @@ __global__ void __launch_bounds__(kThreads) k_lanczos_step(SectorView sv, HopPar
     b += __ldcg(part + i * 3 + 1);
     c += __ldcg(part + i * 3 + 2);
   }
-  block_sum3(a, b, c);
+  block_sum3<kThreads>(a, b, c);
   if (threadIdx.x == 0) {
     double alpha = c > 0.0 ? a / c : 0.0;
     double b2 = c > 0.0 ? b - a * a / c : 0.0;
@@ -514,7 +432,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_up_cols(SectorView sv, HopParam
   if (!FUSED) return;
   double sxw, sww, sxx;
   part3.get(sxw, sww, sxx);
-  block_sum3(sxw, sww, sxx);
+  block_sum3<kThreads>(sxw, sww, sxx);
   const unsigned nblk = gridDim.x * gridDim.y;
   const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
   double* part = ls.partial + ((int64_t)run * nblk) * 3;
@@ -535,7 +453,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_up_cols(SectorView sv, HopParam
     b += __ldcg(part + i * 3 + 1);
     c += __ldcg(part + i * 3 + 2);
   }
-  block_sum3(a, b, c);
+  block_sum3<kThreads>(a, b, c);
   if (threadIdx.x == 0) {
     double alpha = c > 0.0 ? a / c : 0.0;
     double b2 = c > 0.0 ? b - a * a / c : 0.0;
@@ -556,11 +474,12 @@ static size_t down_rows_smem(const SectorView& sv, int dtype) {
   return (size_t)sv.d_dn * 16 + (256 + kMaxOrb) * es;
 }
 
-// The two-pass form applies when the vector does not fit L2 comfortably and the layout allows
-// 16-byte vector access.
+// The two-pass form applies when the vector has at least sv.two_pass_min_bytes (32 MiB unless the
+// cluster's ED_OPT_TWO_PASS_MIN_BYTES says otherwise: beyond that it no longer fits L2
+// comfortably) and the layout allows 16-byte vector access.
 static bool use_two_pass(const SectorView& sv, int dtype, const void* X, const void* O, int64_t vstride) {
   const int64_t es = dtype == ED_FP64 ? 8 : 4, NV = dtype == ED_FP64 ? 2 : 4;
-  if (sv.d_up * sv.d_dn * es < (int64_t(32) << 20)) return false;
+  if (sv.d_up * sv.d_dn * es < sv.two_pass_min_bytes) return false;
   const int64_t need = (sv.d_dn + 32 * NV - 1) / (32 * NV) * (32 * NV);
   if (sv.ld < need || sv.ld % NV != 0) return false;
   if (((uintptr_t)X | (uintptr_t)O) % 16 != 0 || (vstride * es) % 16 != 0) return false;

@@ -36,10 +36,12 @@ static int vgrid(int64_t n) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 8));
 }
 
-template <typename T>
+// TO: type of the ground-state accumulator omega (the vectors' type, or FP64 for FP32 vectors
+// whose sum must keep FP64 precision).
+template <typename T, typename TO>
 __global__ void __launch_bounds__(kVT) k_lanczos_next(T* __restrict__ W0, const T* __restrict__ X0, int64_t d_up, int64_t d_dn,
                                                       int64_t ld, int64_t vstride, int n, LanczosScalars ls,
-                                                      T* __restrict__ omega, const double* __restrict__ coef) {
+                                                      TO* __restrict__ omega, const double* __restrict__ coef) {
   const int run = blockIdx.y;
   if (!ls.active[run]) return;
   T* W = W0 + run * vstride;
@@ -47,28 +49,34 @@ __global__ void __launch_bounds__(kVT) k_lanczos_next(T* __restrict__ W0, const 
   const double a = ls.alpha[(int64_t)run * ls.mstride + n];
   const double b = ls.beta[(int64_t)run * (ls.mstride + 1) + n + 1];
   const double ib = 1.0 / b;
-  const T cf = omega ? (T)coef[n + 1] : T(0);
+  const TO cf = omega ? (TO)coef[n + 1] : TO(0);
   const T aT = (T)a, ibT = (T)ib;
   const int64_t dim = d_up * d_dn;
   for_each_element(d_up, d_dn, [&](int64_t u, int64_t d, int64_t idx) {
     int64_t o = u * ld + d;
     const T vt = (W[o] - aT * X[o]) * ibT;
     W[o] = vt;
-    if (omega) omega[idx] += cf * vt;
+    if (omega) omega[idx] += cf * (TO)vt;
     });
 }
 
 void launch_lanczos_next(int dtype, void* W, const void* X, int64_t d_up, int64_t d_dn, int64_t ld, int64_t vstride,
-                         int runs, int n, const LanczosScalars& ls, void* omega, const double* coef, cudaStream_t s) {
+                         int runs, int n, const LanczosScalars& ls, void* omega, const double* coef, cudaStream_t s,
+                         int omega_dtype) {
   dim3 g(vgrid(d_up * d_dn), runs);
   const double es = dtype == ED_FP64 ? 8.0 : 4.0;
-  ProfScope ps_(K_LANCZOS_NEXT, s, (3.0 * es + (omega ? 16.0 : 0.0)) * (double)(d_up * d_dn) * runs);
+  if (omega_dtype < 0) omega_dtype = dtype;
+  const double eo = omega_dtype == ED_FP64 ? 8.0 : 4.0;
+  ProfScope ps_(K_LANCZOS_NEXT, s, (3.0 * es + (omega ? 2.0 * eo : 0.0)) * (double)(d_up * d_dn) * runs);
   if (dtype == ED_FP64)
-    k_lanczos_next<double><<<g, kVT, 0, s>>>((double*)W, (const double*)X, d_up, d_dn, ld, vstride, n, ls,
-                                              (double*)omega, coef);
+    k_lanczos_next<double, double><<<g, kVT, 0, s>>>((double*)W, (const double*)X, d_up, d_dn, ld, vstride, n, ls,
+                                                      (double*)omega, coef);
+  else if (omega_dtype == ED_FP64)
+    k_lanczos_next<float, double><<<g, kVT, 0, s>>>((float*)W, (const float*)X, d_up, d_dn, ld, vstride, n, ls,
+                                                     (double*)omega, coef);
   else
-    k_lanczos_next<float><<<g, kVT, 0, s>>>((float*)W, (const float*)X, d_up, d_dn, ld, vstride, n, ls,
-                                             (float*)omega, coef);
+    k_lanczos_next<float, float><<<g, kVT, 0, s>>>((float*)W, (const float*)X, d_up, d_dn, ld, vstride, n, ls,
+                                                    (float*)omega, coef);
   ED_CHECK_LAUNCH();
 }
 

@@ -8,6 +8,7 @@
 #include <mutex>
 
 #include "ed_common.cuh"
+#include "hpsi_element.cuh"
 
 namespace ed {
 
@@ -20,50 +21,6 @@ constexpr int64_t kStaticMaxDim = (int64_t)kStaticMaxBlocks * kStaticThreads * k
 static __device__ __align__(256) double g_static_partial[kStaticMaxBlocks * 3];
 static __device__ __align__(256) unsigned int g_static_ticket[64];
 
-template <typename T>
-struct SPrec;
-template <>
-struct SPrec<double> {
-  __device__ static const double* e_up(const SectorView& s) { return s.e_up; }
-  __device__ static const double* e_dn(const SectorView& s) { return s.e_dn; }
-  __device__ static double val(const HopParams& h, int i) { return h.val[i]; }
-  __device__ static double U(const HopParams& h, int i) { return h.U[i]; }
-};
-template <>
-struct SPrec<float> {
-  __device__ static const float* e_up(const SectorView& s) { return s.e_up32; }
-  __device__ static const float* e_dn(const SectorView& s) { return s.e_dn32; }
-  __device__ static float val(const HopParams& h, int i) { return h.valf[i]; }
-  __device__ static float U(const HopParams& h, int i) { return h.Uf[i]; }
-};
-
-__device__ __forceinline__ void static_block_sum3(double& a, double& b, double& c) {
-  __shared__ double sm[3][kStaticThreads / 32];
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_down_sync(0xffffffffu, a, o);
-    b += __shfl_down_sync(0xffffffffu, b, o);
-    c += __shfl_down_sync(0xffffffffu, c, o);
-  }
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) {
-    sm[0][w] = a;
-    sm[1][w] = b;
-    sm[2][w] = c;
-  }
-  __syncthreads();
-  if (w == 0) {
-    a = l < kStaticThreads / 32 ? sm[0][l] : 0.0;
-    b = l < kStaticThreads / 32 ? sm[1][l] : 0.0;
-    c = l < kStaticThreads / 32 ? sm[2][l] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_down_sync(0xffffffffu, a, o);
-      b += __shfl_down_sync(0xffffffffu, b, o);
-      c += __shfl_down_sync(0xffffffffu, c, o);
-    }
-  }
-  __syncthreads();
-}
-
 // One thread per element (kStaticPerThread elements per thread, one grid pass); block partial
 // sums go to `partial`, the last block (ticket) adds them in block order into out3.
 template <typename T>
@@ -74,41 +31,24 @@ __global__ void __launch_bounds__(kStaticThreads) k_hpsi_dots_static(SectorView 
   __shared__ T sval[kMaxVals];
   __shared__ T sU[kMaxOrb];
   __shared__ bool s_last;
-  for (int i = threadIdx.x; i < kMaxVals; i += blockDim.x) sval[i] = SPrec<T>::val(hp, i);
-  for (int i = threadIdx.x; i < kMaxOrb; i += blockDim.x) sU[i] = SPrec<T>::U(hp, i);
-  __syncthreads();
+  // The host rejects sectors that need more blocks than the fixed scratch has partial slots for;
+  // a grid beyond it would write past the array, so such a launch writes nothing at all.
+  if (gridDim.x > kStaticMaxBlocks) return;
+  load_params<T>(hp, sval, sU);
   const int64_t dim = sv.d_up * sv.d_dn;
   double sxy = 0.0, syy = 0.0, sxx = 0.0;
   for (int k = 0; k < kStaticPerThread; ++k) {
     const int64_t idx = ((int64_t)blockIdx.x * kStaticPerThread + k) * kStaticThreads + threadIdx.x;
     if (idx >= dim) break;
     const int64_t u = idx / sv.d_dn, d = idx - u * sv.d_dn;
-    const T* xr = X + u * sv.ld;
-    const uint32_t bu = sv.B_up[u], bd = sv.B_dn[d];
-    T diag = SPrec<T>::e_up(sv)[u] + SPrec<T>::e_dn(sv)[d];
-    uint32_t dbl = bu & bd & hp.umask;
-    while (dbl) {
-      diag += sU[__ffs(dbl) - 1];
-      dbl &= dbl - 1u;
-    }
-    T acc = diag * xr[d];
-    for (int32_t q = sv.ptr_dn[d]; q < sv.ptr_dn[d + 1]; ++q) {
-      const uint32_t e = __ldg(sv.ent_dn + q);
-      const T v = sval[ent_vidx(e)], x = __ldg(xr + ent_col(e));
-      acc += ent_neg(e) ? -v * x : v * x;
-    }
-    for (int32_t q = sv.ptr_up[u]; q < sv.ptr_up[u + 1]; ++q) {
-      const uint32_t e = __ldg(sv.ent_up + q);
-      const T v = sval[ent_vidx(e)], x = __ldg(X + (int64_t)ent_col(e) * sv.ld + d);
-      acc += ent_neg(e) ? -v * x : v * x;
-    }
+    const T acc = hpsi_element<T>(sv, sval, sU, hp.umask, X, u, d);
     Y[u * sv.ld + d] = acc;
-    const double xv = (double)xr[d], yv = (double)acc;
+    const double xv = (double)X[u * sv.ld + d], yv = (double)acc;
     sxy += xv * yv;
     syy += yv * yv;
     sxx += xv * xv;
   }
-  static_block_sum3(sxy, syy, sxx);
+  block_sum3<kStaticThreads>(sxy, syy, sxx);
   if (threadIdx.x == 0) {
     partial[blockIdx.x * 3 + 0] = sxy;
     partial[blockIdx.x * 3 + 1] = syy;
@@ -126,7 +66,7 @@ __global__ void __launch_bounds__(kStaticThreads) k_hpsi_dots_static(SectorView 
     b += __ldcg(partial + i * 3 + 1);
     c += __ldcg(partial + i * 3 + 2);
   }
-  static_block_sum3(a, b, c);
+  block_sum3<kStaticThreads>(a, b, c);
   if (threadIdx.x == 0) {
     out3[0] = a;
     out3[1] = b;
@@ -179,6 +119,13 @@ extern "C" ed_status ed_hpsi_dots_static(ed_cluster* c, int dtype, const void* x
       throw Error(ED_ERR_TOO_LARGE, "sector dimension " + std::to_string(du * dd) +
                                         " exceeds the 4,194,304 elements covered by the fixed scratch of ed_hpsi_dots_static");
     if (ld > 0 && ld < dd) throw Error(ED_ERR_INVALID, "ld must be >= d_dn (or <= 0 for d_dn)");
+    // the tables live on the device the cluster was created on; x, y and the scratch are on the
+    // current one, so the two must be the same device
+    int dev = -1;
+    ED_CUDA(cudaGetDevice(&dev));
+    if (dev != c->device)
+      throw Error(ED_ERR_INVALID, "the current device (" + std::to_string(dev) + ") is not the cluster's device (" +
+                                      std::to_string(c->device) + ")");
     SectorView sv = c->view(c->desc.n_up, c->desc.n_dn, ld);
     StaticScratch s = static_scratch();
     cudaStream_t st = (cudaStream_t)stream;

@@ -23,7 +23,7 @@ struct Totals {
 };
 Totals g_tot[K_COUNT];
 const char* kNames[K_COUNT] = {"tables", "hpsi", "lanczos_step", "lanczos_next", "tridiag", "vector",
-                               "apply_cop", "gf_eval", "band", "batch"};
+                               "apply_cop", "gf_eval", "band", "batch", "lattice"};
 
 void drain_locked() {
   for (auto& p : g_pending) {

@@ -46,7 +46,7 @@ using Clock = std::chrono::steady_clock;
 
 constexpr int kMaxBypass = 8;
 constexpr int kBatchThreads = 256, kBatchMode = 1;  // fixed block configuration of the batched path
-constexpr int kDefaultCfCap = 400;
+constexpr int kDefaultCfCap = kCfDefaultMaxLevels;
 constexpr size_t kMargin = size_t(32) << 20;
 
 // ---------------------------------------------------------------- footprints (closed forms)

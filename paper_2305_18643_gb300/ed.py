@@ -75,6 +75,7 @@ def lib():
                                      C.POINTER(i32), C.POINTER(i32), C.POINTER(i64), vp, i32]),
         }
         sig.update(_server_sigs)
+        sig.update(_lattice_sigs)
         for name, (res, args) in sig.items():
             f = getattr(L, name)
             f.restype = res
@@ -160,7 +161,7 @@ def ed_green(h, omega, eta, n_sites, axis=ED_AXIS_REAL, spin=0, out_ptr=None):
     return st, G
 
 
-ED_OPT_BAND_MAX_DIM, ED_OPT_CF_MAX_STEPS, ED_OPT_GF_TOL = 1, 2, 3
+ED_OPT_BAND_MAX_DIM, ED_OPT_CF_MAX_STEPS, ED_OPT_GF_TOL, ED_OPT_TWO_PASS_MIN_BYTES = 1, 2, 3, 4
 
 
 def ed_set_option(h, option, value):
@@ -202,7 +203,7 @@ def ed_hpsi(h, n_up, n_dn, dtype, x_ptr, y_ptr, ld=0, stream=0):
 
 
 ED_K_TABLES, ED_K_HPSI, ED_K_LANCZOS_STEP, ED_K_LANCZOS_NEXT, ED_K_TRIDIAG = 0, 1, 2, 3, 4
-ED_K_VECTOR, ED_K_APPLY_COP, ED_K_GF_EVAL, ED_K_BAND, ED_K_BATCH, ED_K_COUNT = 5, 6, 7, 8, 9, 10
+ED_K_VECTOR, ED_K_APPLY_COP, ED_K_GF_EVAL, ED_K_BAND, ED_K_BATCH, ED_K_LATTICE, ED_K_COUNT = 5, 6, 7, 8, 9, 10, 11
 
 
 def ed_profile_enable(on):
@@ -250,7 +251,8 @@ def ed_batch_solve(clusters, precision=ED_FP64, omega=None, eta=0.05, axis=ED_AX
                    out_ptr=None, cf_max_levels=0):
     """Solve many clusters together.  Returns (E0, residual, status, iters, G) where G is a list of
     complex128 arrays [2, n_freq, n_sites, n_sites] (None when omega is None or out_ptr is given).
-    cf_max_levels caps every continued fraction (<= 0: the library's preset, 400 levels); the
+    cf_max_levels caps every continued fraction (<= 0: the library's preset of 20000 levels, so
+    that runs end on convergence on the grid); the
     continued-fraction levels of each cluster are left in ed_batch_solve.gf_steps."""
     n = len(clusters)
     descs, keep = _desc_array(clusters, seed, tol)
@@ -459,3 +461,133 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# ----------------------------------------------------------------------------- lattice steps (CPT, CDMFT)
+class ed_superlattice(C.Structure):
+    _fields_ = [("n_sites", C.c_int), ("dim", C.c_int), ("pos", _dp), ("E", _dp), ("n_bonds", C.c_int),
+                ("bonds", C.POINTER(C.c_int)), ("bond_t", _dp)]
+
+
+ED_CPT_MATRIX, ED_CPT_PERIODIZED, ED_CPT_AVERAGE = 0, 1, 2
+
+_lattice_sigs = {
+    "ed_hybridization": (C.c_int, [C.c_int, C.c_int, _dp, _dp, _dp, C.c_int, C.c_void_p, C.c_int]),
+    "ed_cpt_green": (C.c_int, [C.POINTER(ed_superlattice), C.c_void_p, C.c_void_p, C.c_int, _dp, C.c_int, C.c_int,
+                               C.c_void_p, C.c_int]),
+    "ed_cdmft_target": (C.c_int, [C.POINTER(ed_superlattice), C.c_void_p, C.c_void_p, C.c_int, _dp, C.c_int,
+                                  C.c_void_p, C.c_int]),
+    "ed_cdmft_distance": (C.c_int, [C.c_int, C.c_int, C.c_int, _dp, _dp, _dp, C.c_int, _dp, _dp, _dp, _dp]),
+    "ed_cdmft_fit": (C.c_int, [C.c_int, C.c_int, _dp, _dp, C.POINTER(C.c_ubyte), _dp, C.c_int, _dp, _dp,
+                               C.c_double, C.c_int, _dp, C.POINTER(C.c_int)]),
+}
+
+
+def _c128(a, shape=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.complex128))
+    if shape is not None and a.shape != tuple(shape):
+        a = a.reshape(shape)
+    return a
+
+
+def _superlattice(lat):
+    """ed_superlattice from a dict {"t_c", "pos", "E", "bonds": [(i, j, n, t)]}; returns
+    (struct, arrays kept alive)."""
+    pos = np.ascontiguousarray(np.asarray(lat["pos"], dtype=np.float64))
+    L, D = pos.shape
+    E = np.ascontiguousarray(np.asarray(lat["E"], dtype=np.float64).reshape(D, D))
+    nb = len(lat["bonds"])
+    bonds = np.zeros((max(nb, 1), 2 + D), dtype=np.int32)
+    bt = np.zeros(max(nb, 1))
+    for q, (i, j, n, t) in enumerate(lat["bonds"]):
+        bonds[q, 0], bonds[q, 1] = i, j
+        bonds[q, 2:] = np.atleast_1d(n)
+        bt[q] = t
+    s = ed_superlattice(L, D, pos.ctypes.data_as(_dp), E.ctypes.data_as(_dp), nb,
+                        bonds.ctypes.data_as(C.POINTER(C.c_int)), bt.ctypes.data_as(_dp))
+    return s, (pos, E, bonds, bt)
+
+
+def ed_hybridization(theta, eps, z):
+    """Gamma[nz, L, L] (Eq. hybridization) for theta (L, nb), eps (nb,), complex z (nz,)."""
+    theta = np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+    L, nb = theta.shape
+    eps = np.ascontiguousarray(np.asarray(eps, dtype=np.float64).ravel())
+    z = _c128(z).ravel()
+    out = np.empty((z.size, L, L), dtype=np.complex128)
+    _check(lib().ed_hybridization(L, nb, eps.ctypes.data_as(_dp), theta.ctypes.data_as(_dp),
+                                  z.view(np.float64).ctypes.data_as(_dp), z.size, out.ctypes.data_as(C.c_void_p), 0))
+    return out
+
+
+def ed_cpt_green(lat, Gc, kt, mode=ED_CPT_MATRIX, Gamma=None):
+    """CPT from the cluster Green function Gc[nz, L, L] on wave vectors kt[nk, D] (host arrays).
+    Returns G[nk, nz, L, L] (ED_CPT_MATRIX), G_per[nk, nz] (ED_CPT_PERIODIZED) or G_bar[nz, L, L]
+    (ED_CPT_AVERAGE)."""
+    s, keep = _superlattice(lat)
+    Gc = _c128(Gc)
+    nz, L = Gc.shape[0], Gc.shape[1]
+    kt = np.ascontiguousarray(np.asarray(kt, dtype=np.float64).reshape(-1, s.dim))
+    nk = kt.shape[0]
+    Gm = _c128(Gamma) if Gamma is not None else None
+    shape = {ED_CPT_MATRIX: (nk, nz, L, L), ED_CPT_PERIODIZED: (nk, nz), ED_CPT_AVERAGE: (nz, L, L)}[mode]
+    out = np.empty(shape, dtype=np.complex128)
+    _check(lib().ed_cpt_green(C.byref(s), Gc.ctypes.data_as(C.c_void_p),
+                              Gm.ctypes.data_as(C.c_void_p) if Gm is not None else None, nz,
+                              kt.ctypes.data_as(_dp), nk, int(mode), out.ctypes.data_as(C.c_void_p), 0))
+    return out
+
+
+def ed_cdmft_target(lat, Gc, kt, Gamma=None):
+    """A[nz, L, L] = Gamma + Gc^-1 - G_bar^-1 (CDMFT steps 3-4) on the reduced-zone grid kt."""
+    s, keep = _superlattice(lat)
+    Gc = _c128(Gc)
+    nz, L = Gc.shape[0], Gc.shape[1]
+    kt = np.ascontiguousarray(np.asarray(kt, dtype=np.float64).reshape(-1, s.dim))
+    Gm = _c128(Gamma) if Gamma is not None else None
+    out = np.empty((nz, L, L), dtype=np.complex128)
+    _check(lib().ed_cdmft_target(C.byref(s), Gc.ctypes.data_as(C.c_void_p),
+                                 Gm.ctypes.data_as(C.c_void_p) if Gm is not None else None, nz,
+                                 kt.ctypes.data_as(_dp), kt.shape[0], out.ctypes.data_as(C.c_void_p), 0))
+    return out
+
+
+def ed_cdmft_distance(theta, eps, z, weights, A, grad=False):
+    """Distances (and gradients) of n_cand trial baths: theta (n_cand, L, nb), eps (n_cand, nb).
+    Returns d[n_cand] (and grad[n_cand, nb + L nb])."""
+    theta = np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+    if theta.ndim == 2:
+        theta = theta[None]
+    nc, L, nb = theta.shape
+    eps = np.ascontiguousarray(np.asarray(eps, dtype=np.float64).reshape(nc, nb))
+    z = _c128(z).ravel()
+    W = np.ascontiguousarray(np.asarray(weights, dtype=np.float64).ravel())
+    A = _c128(A)
+    d = np.empty(nc)
+    g = np.empty((nc, nb + L * nb)) if grad else None
+    _check(lib().ed_cdmft_distance(L, nb, nc, eps.ctypes.data_as(_dp), theta.ctypes.data_as(_dp),
+                                   z.view(np.float64).ctypes.data_as(_dp), z.size, W.ctypes.data_as(_dp),
+                                   A.view(np.float64).ctypes.data_as(_dp), d.ctypes.data_as(_dp),
+                                   g.ctypes.data_as(_dp) if grad else None))
+    return (d, g) if grad else d
+
+
+def ed_cdmft_fit(theta, eps, z, weights, A, theta_free=None, gtol=0.0, max_iter=0):
+    """Bath fit (CDMFT step 4) from the starting bath (theta (L, nb), eps (nb,)); returns
+    (theta, eps, d, iterations)."""
+    theta = np.array(theta, dtype=np.float64, order="C")
+    L, nb = theta.shape
+    eps = np.array(eps, dtype=np.float64).ravel().copy()
+    z = _c128(z).ravel()
+    W = np.ascontiguousarray(np.asarray(weights, dtype=np.float64).ravel())
+    A = _c128(A)
+    free = None
+    if theta_free is not None:
+        free = np.ascontiguousarray(np.asarray(theta_free, dtype=np.uint8).reshape(L, nb))
+    d, it = C.c_double(), C.c_int()
+    _check(lib().ed_cdmft_fit(L, nb, eps.ctypes.data_as(_dp), theta.ctypes.data_as(_dp),
+                              free.ctypes.data_as(C.POINTER(C.c_ubyte)) if free is not None else None,
+                              z.view(np.float64).ctypes.data_as(_dp), z.size, W.ctypes.data_as(_dp),
+                              A.view(np.float64).ctypes.data_as(_dp), float(gtol), int(max_iter), C.byref(d),
+                              C.byref(it)))
+    return theta, eps, d.value, it.value

@@ -240,3 +240,19 @@ def test_cf_without_reorthogonalization_converges():
     Ge = O.green_exact(m, 3, 3, z)[0]
     Gc = O.green_cf(m, 3, 3, z, reorth=False, max_steps=600, btol=0.0)[0]
     assert np.max(np.abs(Gc - Ge)) < 1e-11
+
+
+def test_ladder14_golden_properties():
+    """The stored 2x7 reference (tests/golden/make_ladder14.py, oracle only): G_ij = G_ji for a
+    real H (Sec. 4.3), Im G_ii(i omega) < 0 for omega > 0 (positive spectral weight, Eq. spectral1),
+    G_ii(i omega) purely damped toward -i/omega (its magnitude below 1/omega, Eq. norm), and an E0
+    below the ladder's atomic-limit energy with every hop removed (a variational bound)."""
+    import os
+    g = np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "ladder14_band.npz"))
+    G, om = g["G"], g["omega"]
+    assert np.max(np.abs(G - G.transpose(0, 2, 1))) <= 1e-12
+    d = np.einsum("kii->ki", G)
+    assert np.all(d.imag < 0)
+    assert np.all(np.abs(d) <= 1.0 / om[:, None] + 1e-12)
+    c = W.served_request(np.random.default_rng(int(g["seed"])), sizes=(14,))
+    assert float(g["E0"]) < -c["mu"] * 14  # below the atomic state with one electron per site (U n n = 0)
