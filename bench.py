@@ -46,6 +46,9 @@ WORKLOADS = {
     "2x7": (lambda instance=0: W.served_request(np.random.default_rng(20230529 + 7000 + instance), sizes=(14,)),
             "2x7 open Hubbard, t=-1, t'=+-0.3 seeded, U=8, mu=4, N_up=N_dn=7 (d=3432^2); band-Lanczos G on 1000 "
             "Matsubara frequencies (beta=50)", "fp32", "band", 1000),
+    "hpsi": (W.periodic_4x4, "standalone H.psi of the band Lanczos: 4x4 periodic cluster, sector N_up=9, N_dn=8 "
+             "(11440 x 12870 = 147,232,800 states, rows padded to 12928), FP32 vectors (two-pass kernels)",
+             "fp32", "none", 0),
     "batch": (lambda instance=0: W.batched_family(512, instance=instance),
               "512 seeded clusters of 4-12 orbitals (chains, 2-leg ladders, 2x2 plaquettes + 0-8 bath), "
               "|t| ~ U[0.5,1.5], U ~ U[2,10], mu = U/2, random fillings; both spins", "fp32", "cf", 512),
@@ -87,7 +90,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--sequential", type=int, default=0,
                     help="batch workload: also time this many clusters one by one through the single-cluster "
-                         "FP64 path (the plain FP64 GPU path, same 400-level preset maximum) and report its solves/s")
+                         "FP64 path (the plain FP64 GPU path, continued fractions run to convergence as in the "
+                         "batch) and report its solves/s")
     return ap.parse_args()
 
 
@@ -201,6 +205,8 @@ def run_ours(args, rank, world, local_rank):
         return run_batch(args, rank, world, local_rank, torch, ed)
     if args.workload == "served":
         return run_served(args, rank, world, local_rank, torch, ed)
+    if args.workload == "hpsi":
+        return run_hpsi(args, rank, world, local_rank, torch, ed)
     c = gen(instance=rank)
     ns = c["t"].shape[0]
     axis_name = AXIS.get(args.workload, "real")
@@ -320,6 +326,73 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.destroy_process_group()
     return result
+
+
+def run_hpsi(args, rank, world, local_rank, torch, ed):
+    """Kernel-level workload: y = H x on the electron sector (N_up + 1, N_dn) of the 4x4 cluster,
+    the product the band Lanczos applies to each vector of a block, FP32 (or --precision fp64)
+    vectors with rows padded to 128 elements (the two-pass kernels).  A step is 16 products (one
+    block); value = products/s, roofline = 2 d s bytes per product over its CUDA-event time."""
+    gen, label, prec_d, gf_d, nfreq = WORKLOADS["hpsi"]
+    prec = args.precision or prec_d
+    c = gen(instance=rank)
+    precision = ed.ED_FP32 if prec == "fp32" else ed.ED_FP64
+    tdt = torch.float32 if prec == "fp32" else torch.float64
+    nu, nd = c["n_up"] + 1, c["n_dn"]
+    cl = ed.Cluster(c, precision=precision)
+    du, dd = ed.ed_sector_dims(cl.h, nu, nd)
+    ld = (dd + 127) // 128 * 128
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5 + rank)
+    x = torch.zeros((du, ld), dtype=tdt, device="cuda")
+    x[:, :dd] = torch.rand((du, dd), generator=g, device="cuda", dtype=tdt) * 2 - 1
+    y = torch.zeros_like(x)
+    stream = torch.cuda.current_stream().cuda_stream
+    per_step = 16
+
+    def step():
+        for _ in range(per_step):
+            ed.ed_hpsi(cl.h, nu, nd, precision, x.data_ptr(), y.data_ptr(), ld, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ed.ed_profile_enable(1)
+    l0 = ed.ed_launch_count()
+    with ClockSampler(local_rank) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+    launches = ed.ed_launch_count() - l0
+    ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
+    n_l, ms_l, by_l = ed.ed_profile_read(ed.ED_K_HPSI)
+    ed.ed_profile_enable(0)
+    peak, peak_kind = measured_peak_hbm()
+    ach = (by_l / 1e9) / (ms_l / 1e3) if ms_l > 0 else None
+    cl.close()
+    es = 4 if prec == "fp32" else 8
+    return {
+        "metric": "H.psi HBM GB/s (% roofline), band-Lanczos sector of the 4x4 cluster",
+        "value": whole_job_rate(args.steps * per_step, world, ms), "unit": "H.psi/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
+        "data": "synthetic (uniform random vector, seeded)",
+        "config": {"workload": "hpsi: " + label, "products_per_step": per_step,
+                   "l2": "inputs larger than L2 (%.2f GB per vector)" % (du * ld * es / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "clocks": clk.summary(), "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "kernel": "hpsi (two-pass: k_down_rows + k_up_cols)", "achieved": ach,
+                     "peak": peak, "unit": "GB/s", "frac": (ach / peak) if ach else None,
+                     "traffic": ncu_traffic("hpsi.cu", "band_hpsi_4x4.md"),
+                     "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
+                     "launches": n_l, "avg_launch_ms": ms_l / max(n_l, 1), "alg_bytes_per_launch": by_l / max(n_l, 1)},
+        "e2e": None,
+    }
 
 
 def fp64_arm(args, c, gf_method, band_dim, omega, axis, ns, G32_dev, info32, world, torch, ed):
@@ -462,7 +535,7 @@ def run_batch(args, rank, world, local_rank, torch, ed):
         for k, cl in enumerate(seq):
             h = ed.ed_cluster_create(cl, precision=ed.ED_FP64, gf_method=ed.ED_GF_CF, seed=1234 + k)
             try:
-                ed.ed_set_option(h, ed.ED_OPT_CF_MAX_STEPS, 400)  # the same preset maximum as the batch
+                # the same stopping rule as the batch: convergence on the grid (1e-10 with FP64 vectors)
                 ed.ed_ground_state(h)
                 ed.ed_green(h, omega, ETA, cl["t"].shape[0], spin=0, out_ptr=G_dev.data_ptr())
                 if cl["n_up"] != cl["n_dn"]:

@@ -124,9 +124,29 @@ ed_status ed_green(ed_cluster* c, const double* omega, int n_freq, double eta, i
  *                       0 selects them at every size.  Both forms compute the same product; the
  *                       option exists so that the two-pass kernels can be checked on sectors
  *                       small enough for a CPU reference.  Must be >= 0.
+ *  ED_OPT_DAVIDSON_STATES
+ *                       k in [1, 16] [1]: with k > 1 ed_ground_state finds the k lowest states of
+ *                       the sector by the Davidson method (FP64 vectors whatever the precision;
+ *                       Sec. 4.2 recommends it for degenerate ground states, and the library's
+ *                       Davidson_states option of Sec. 9 targets several low states), and ed_green
+ *                       returns the mixed-state Green function sum_s p_s G_s(z), G_s that of state s
+ *                       (its energy in the place of E0, Eq. green).  Setting it discards the ground
+ *                       state found so far.
+ *  ED_OPT_TEMPERATURE   T >= 0 [0] of the mixed state: p_s = exp(-(E_s - E_0) / T) / Z over the k
+ *                       states; T = 0 gives equal weights to the states within 1e-9 max(1,|E_0|)
+ *                       of E_0 (a degenerate ground manifold), so G does not depend on the basis
+ *                       chosen inside it.  The paper's temperature option: low, since only a few
+ *                       states are kept.
  * ED_ERR_INVALID for an unknown option or a non-finite value. */
-enum { ED_OPT_BAND_MAX_DIM = 1, ED_OPT_CF_MAX_STEPS = 2, ED_OPT_GF_TOL = 3, ED_OPT_TWO_PASS_MIN_BYTES = 4 };
+enum { ED_OPT_BAND_MAX_DIM = 1, ED_OPT_CF_MAX_STEPS = 2, ED_OPT_GF_TOL = 3, ED_OPT_TWO_PASS_MIN_BYTES = 4,
+       ED_OPT_DAVIDSON_STATES = 5, ED_OPT_TEMPERATURE = 6 };
 ed_status ed_set_option(ed_cluster* c, int option, double value);
+
+/* The states behind the cluster's Green function after ed_ground_state: their energies (ascending)
+ * and mixed-state weights p_s (ED_OPT_TEMPERATURE); one state of weight 1 with the Lanczos method.
+ * Writes min(capacity, count) values to each non-NULL array and the number of states to *count.
+ * ED_ERR_STATE before ed_ground_state. */
+ed_status ed_low_states(const ed_cluster* c, int capacity, double* E, double* weights, int* count);
 
 /* Statistics of the last ed_green: total Lanczos (or band) steps over all starting vectors and
  * the longest run.  Any pointer may be NULL. */

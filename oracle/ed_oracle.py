@@ -51,7 +51,7 @@ __all__ = [
     "jw_hamiltonian_dense", "ground_state",
     "apply_cdag", "apply_c", "density", "green_exact", "lanczos_coefficients",
     "cf_green", "green_cf", "band_lanczos_lehmann", "lehmann_green", "green_band",
-    "frequency_grid",
+    "frequency_grid", "low_states", "mixed_weights", "green_mixed",
 ]
 
 _POP8 = np.array([bin(i).count("1") for i in range(256)], dtype=np.int64)
@@ -422,15 +422,20 @@ def lehmann_green(Q, w, z):
     return np.einsum("ir,zr,jr->zij", Q, R, Q)
 
 
-def green_exact(model, n_up, n_dn, z, spin=0, orbitals=None, dense_limit=6000):
+def green_exact(model, n_up, n_dn, z, spin=0, orbitals=None, dense_limit=6000, state=None):
     """Exact G_ij(z) by full diagonalization of the N +- 1 sectors (Eqs. green, spectral1).
 
     Returns (G[nz, p, p], Q[p, R], w[R], E0, gap) with the electron and hole poles
     concatenated: electron poles w_r = E_r - E0, hole poles w_r = E0 - E_r (Eq. spectral1).
+    ``state = (E, psi)`` takes that eigenpair of the sector in place of the ground state (the
+    Green function of one of the low-lying states of a mixed state; gap is then returned as nan).
     """
     orbitals = list(range(model.ns)) if orbitals is None else list(orbitals)
     op = sector_hamiltonian(model, n_up, n_dn)
-    E0, Om, gap = ground_state(op, dense_limit=dense_limit)
+    if state is None:
+        E0, Om, gap = ground_state(op, dense_limit=dense_limit)
+    else:
+        E0, Om, gap = float(state[0]), np.asarray(state[1]).reshape(op.shape2), float("nan")
     Qs, ws = [], []
     for kind in ("e", "h"):
         nu = n_up + (1 if kind == "e" else -1) * (spin == 0)
@@ -609,3 +614,48 @@ def green_band(model, n_up, n_dn, z, spin=0, orbitals=None, max_dim=600, dtol=1e
     Q = np.concatenate(Qs, axis=1)
     w = np.concatenate(ws)
     return lehmann_green(Q, w, z), Q, w
+
+
+# ---------------------------------------------------------------------------------------
+# Several low-lying states and mixed-state Green functions (Sec. 4.2, the library's
+# Davidson_states and temperature options of Sec. 9)
+# ---------------------------------------------------------------------------------------
+
+def low_states(op, k, dense_limit=6000, tol=1e-13):
+    """The k lowest eigenpairs of H in the sector: energies E[k] (ascending) and states
+    V[k, d_up, d_dn] (unit norm).  Dense LAPACK up to dense_limit states, else ARPACK."""
+    if op.dim <= dense_limit:
+        w, V = np.linalg.eigh(op.sparse().toarray())
+        w, V = w[:k], V[:, :k]
+    else:
+        v0 = np.cos(np.arange(op.dim) * 0.7) + 1.0
+        w, V = spla.eigsh(op.linear_operator(), k=k, which="SA", tol=tol, v0=v0, ncv=max(24, 3 * k + 1))
+        order = np.argsort(w)
+        w, V = w[order], V[:, order]
+    return w, np.stack([V[:, s].reshape(op.shape2) for s in range(len(w))])
+
+
+def mixed_weights(E, T, degenerate_tol=1e-9):
+    """Weights p_s of the low-lying states in the mixed state of temperature T: Boltzmann factors
+    exp(-(E_s - E_0) / T) normalized over the states given; at T = 0 equal weights on the states
+    within degenerate_tol max(1, |E_0|) of E_0 (the T -> 0 limit over a degenerate manifold)."""
+    E = np.asarray(E, dtype=np.float64)
+    if T > 0:
+        w = np.exp(-(E - E[0]) / T)
+    else:
+        w = (E - E[0] <= degenerate_tol * max(1.0, abs(E[0]))).astype(np.float64)
+    return w / w.sum()
+
+
+def green_mixed(model, n_up, n_dn, z, k, T=0.0, spin=0, orbitals=None):
+    """G(z) = sum_s p_s G_s(z) over the k lowest states s of the sector (mixed_weights), each G_s
+    the exact Lehmann sum (Eq. spectral1) with E_s in place of E_0.  Returns (G, E, p)."""
+    op = sector_hamiltonian(model, n_up, n_dn)
+    E, V = low_states(op, k)
+    p = mixed_weights(E, T)
+    G = 0.0
+    for s in range(len(E)):
+        if p[s] == 0.0:
+            continue
+        G = G + p[s] * green_exact(model, n_up, n_dn, z, spin=spin, orbitals=orbitals, state=(E[s], V[s]))[0]
+    return G, E, p

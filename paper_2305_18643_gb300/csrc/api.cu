@@ -36,6 +36,9 @@ void throw_cuda(cudaError_t e, const char* what, const char* file, int line) {
 }
 
 GroundResult run_ground_state(ed_cluster& c, int dtype, double tol, int max_iter, uint64_t seed);
+LowStatesResult run_davidson(ed_cluster& c, int k, double tol, int max_iter, uint64_t seed);
+bool run_green_mixed(ed_cluster& c, int spin, const double2* z_host, int nz, double2* G_dev);
+std::vector<double> mixed_weights(const std::vector<double>& E, double T);
 void run_green_cf(ed_cluster& c, int spin, const double2* z_host, int nz, double2* G_dev);
 bool run_green_band(ed_cluster& c, int spin, const double2* z_host, int nz, double2* G_dev);
 
@@ -233,7 +236,21 @@ ed_status ed_ground_state(ed_cluster* c, double* E0, double* residual, int* iter
   return guarded([&]() -> ed_status {
     require(c != nullptr, "cluster is NULL");
     require_cluster_device(c);
-    GroundResult r = run_ground_state(*c, c->desc.precision, c->desc.tol, c->desc.max_iter, c->desc.seed);
+    GroundResult r;
+    if (c->davidson_states > 1) {
+      LowStatesResult d = run_davidson(*c, c->davidson_states, c->desc.tol, c->desc.max_iter, c->desc.seed);
+      c->low_E = d.E;
+      r.E0 = d.E[0];
+      r.residual = *std::max_element(d.residual.begin(), d.residual.end());
+      r.iters = d.iters;
+      r.converged = d.converged;
+      r.gap = d.E.size() > 1 ? d.E[1] - d.E[0] : 0.0;
+      // the mixture covers the degenerate ground manifold only if a state above it was found
+      r.degenerate = d.E.size() > 1 && d.E.back() - d.E[0] <= 1e-9 * std::max(1.0, std::fabs(d.E[0]));
+    } else {
+      r = run_ground_state(*c, c->desc.precision, c->desc.tol, c->desc.max_iter, c->desc.seed);
+      c->low_E.clear();
+    }
     c->gs = r;
     c->have_gs = true;
     if (E0) *E0 = r.E0;
@@ -283,7 +300,10 @@ ed_status ed_green(ed_cluster* c, const double* omega, int n_freq, double eta, i
       Gd.alloc((size_t)n_freq * p * p);
       Gdev = Gd.p;
     }
-    if (c->desc.gf_method == ED_GF_CF) {
+    if (c->davidson_states > 1) {
+      c->gf_converged = run_green_mixed(*c, spin, z.data(), n_freq, Gdev);
+      if (!c->gf_converged && st == ED_OK) st = ED_WARN_NOT_CONVERGED;
+    } else if (c->desc.gf_method == ED_GF_CF) {
       run_green_cf(*c, spin, z.data(), n_freq, Gdev);
     } else {
       c->gf_converged = run_green_band(*c, spin, z.data(), n_freq, Gdev);
@@ -305,11 +325,36 @@ ed_status ed_set_option(ed_cluster* c, int option, double value) {
       case ED_OPT_BAND_MAX_DIM: c->band_max_dim = (int)value; break;
       case ED_OPT_CF_MAX_STEPS: c->cf_max_steps = (int)value; break;
       case ED_OPT_GF_TOL: c->gf_tol = value; break;
+      case ED_OPT_DAVIDSON_STATES:
+        require(value >= 1.0 && value <= 16.0, "ED_OPT_DAVIDSON_STATES must be in [1, 16]");
+        c->davidson_states = (int)value;
+        c->have_gs = false;
+        break;
+      case ED_OPT_TEMPERATURE:
+        require(value >= 0.0, "ED_OPT_TEMPERATURE must be >= 0");
+        c->temperature = value;
+        break;
       case ED_OPT_TWO_PASS_MIN_BYTES:
         require(value >= 0.0, "ED_OPT_TWO_PASS_MIN_BYTES must be >= 0");
         c->two_pass_min_bytes = value >= 9.0e18 ? INT64_MAX : (int64_t)value;
         break;
       default: throw Error(ED_ERR_INVALID, "unknown option");
+    }
+    return ED_OK;
+  });
+}
+
+ed_status ed_low_states(const ed_cluster* c, int capacity, double* E, double* weights, int* count) {
+  return guarded([&]() -> ed_status {
+    require(c != nullptr, "cluster is NULL");
+    if (!c->have_gs) throw Error(ED_ERR_STATE, "no ground state yet");
+    std::vector<double> e = c->low_E.empty() ? std::vector<double>{c->gs.E0} : c->low_E;
+    std::vector<double> w = mixed_weights(e, c->low_E.empty() ? 0.0 : c->temperature);
+    if (count) *count = (int)e.size();
+    const int n = std::min<int>(capacity, (int)e.size());
+    for (int i = 0; i < n; ++i) {
+      if (E) E[i] = e[i];
+      if (weights) weights[i] = w[i];
     }
     return ED_OK;
   });

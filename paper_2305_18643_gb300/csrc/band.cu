@@ -631,6 +631,17 @@ static void block_axpy(T* Y, int py, const T* X, const T* X1, int64_t xbstride, 
   }
 }
 
+// FP64 forms of the two block kernels for other drivers (Davidson): G[b][i][j] = sum X_{b,i} Y_j
+// over nb blocks of px vectors (X + b xbstride), and Y (mode 0: =, 1: -=) X C.
+void gram_f64(const double* X, int64_t xbstride, int nb, int px, const double* Y, int py, int64_t vstride, int64_t n,
+              DevBuf<double>& P, DevBuf<unsigned>& tk, double* G, cudaStream_t s) {
+  gram<double>(X, nullptr, xbstride, nb, px, Y, py, vstride, n, P, tk, G, s);
+}
+void block_axpy_f64(double* Y, int py, const double* X, int64_t xbstride, int nb, int px, const double* C,
+                    int64_t vstride, int64_t n, int mode, cudaStream_t s) {
+  block_axpy<double>(Y, py, X, nullptr, xbstride, nb, px, C, vstride, n, mode, s);
+}
+
 struct BandOptions {
   double tol;         // |Delta G| on the grid between checks
   int max_dim;        // Krylov vectors per part

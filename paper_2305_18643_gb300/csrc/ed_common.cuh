@@ -295,6 +295,13 @@ struct GroundResult {
   bool converged = false, degenerate = false;
 };
 
+// Several low states of a sector (davidson.cu): energies ascending, relative residuals.
+struct LowStatesResult {
+  std::vector<double> E, residual;
+  int iters = 0;
+  bool converged = false;
+};
+
 }  // namespace ed
 
 // The opaque cluster handle.
@@ -318,6 +325,10 @@ struct ed_cluster {
   size_t gf_mem_budget = 0;    // bytes for Green-function Lanczos vectors (0: default)
   int gf_max_steps = 0;
   int64_t two_pass_min_bytes = ed::kTwoPassMinBytes;  // ED_OPT_TWO_PASS_MIN_BYTES
+  int davidson_states = 1;     // ED_OPT_DAVIDSON_STATES: > 1 selects the Davidson method
+  double temperature = 0.0;    // ED_OPT_TEMPERATURE of the mixed state
+  ed::DevBuf<double> low;      // the low states (FP64, contiguous d_up x d_dn each) of a Davidson run
+  std::vector<double> low_E;   // their energies
   ed::SpinTables& tables(int N);
   ed::SectorView view(int n_up, int n_dn, int64_t ld);
 };

@@ -82,24 +82,136 @@ struct LanczosRun {
 
 static size_t esize(int dtype) { return dtype == ED_FP64 ? sizeof(double) : sizeof(float); }
 
+// Lanczos vectors kept in device memory, so that a Ritz vector is summed in one pass over them
+// instead of by retracing the recursion.  The paper retraces because its runs keep three vectors in
+// memory (Sec. 4.2); the 280 GB of a GB300 hold a hundred or more vectors of the 4x4 sector, and
+// the second pass (as many fused steps as the first) becomes one read of the stored vectors.
+// Vectors go into chunks allocated as the run grows, while the device keeps a quarter of its memory
+// (at least 8 GiB) free; when a chunk does not fit, or on a server lane (whose memory admission
+// counts three vectors per run), storing stops and the run is retraced.
+struct VectorStore {
+  static constexpr int kChunk = 8;
+  size_t vbytes = 0;
+  int count = 0;
+  bool ok = false;
+  std::vector<DevBuf<char>> chunks;
+  void start(size_t vb) {
+    vbytes = vb;
+    count = 0;
+    chunks.clear();
+    ok = g_alloc_stream == nullptr;
+  }
+  char* at(int n) { return chunks[n / kChunk].p + (size_t)(n % kChunk) * vbytes; }
+  void drop() {
+    ok = false;
+    chunks.clear();  // cudaFree waits for the copies in flight
+    count = 0;
+  }
+  void push(const void* src, cudaStream_t s) {
+    if (!ok) return;
+    if (count == (int)chunks.size() * kChunk) {
+      size_t fr = 0, tot = 0;
+      if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        cudaGetLastError();
+        drop();
+        return;
+      }
+      const size_t need = (size_t)kChunk * vbytes;
+      if (fr < need + std::max<size_t>(tot / 4, size_t(8) << 30)) {
+        drop();
+        return;
+      }
+      DevBuf<char> b;
+      try {
+        b.alloc(need);
+      } catch (const Error&) {
+        drop();
+        return;
+      }
+      chunks.push_back(std::move(b));
+    }
+    ED_CUDA(cudaMemcpyAsync(at(count), src, vbytes, cudaMemcpyDeviceToDevice, s));
+    ++count;
+  }
+};
+
+// out[u][d] (FP64, contiguous) = (acc ? out[u][d] : 0) + sum_{n < m} coef[n] v_n[u][d] over m stored
+// vectors (leading dimension ld); pointers and coefficients staged in shared memory.
+template <typename T>
+__global__ void k_ritz_sum(const T* const* __restrict__ vecs, int m, const double* __restrict__ coef, double* __restrict__ out,
+                           int64_t du, int64_t dd, int64_t ld, int acc) {
+  extern __shared__ __align__(16) unsigned char rs_smem[];
+  const T** sp = reinterpret_cast<const T**>(rs_smem);
+  double* sc = reinterpret_cast<double*>(rs_smem + (size_t)m * sizeof(T*));
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    sp[i] = vecs[i];
+    sc[i] = coef[i];
+  }
+  __syncthreads();
+  for_each_element(du, dd, [&](int64_t u, int64_t d, int64_t idx) {
+    const int64_t o = u * ld + d;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int n = 0;
+    for (; n + 4 <= m; n += 4) {
+      s0 += sc[n] * (double)sp[n][o];
+      s1 += sc[n + 1] * (double)sp[n + 1][o];
+      s2 += sc[n + 2] * (double)sp[n + 2][o];
+      s3 += sc[n + 3] * (double)sp[n + 3][o];
+    }
+    for (; n < m; ++n) s0 += sc[n] * (double)sp[n][o];
+    const double v = (s0 + s1) + (s2 + s3);
+    out[idx] = acc ? out[idx] + v : v;
+  });
+}
+
+// omega (+)= sum_{n < m} coef[n] store[first + n]
+static void ritz_sum(int dtype, VectorStore& st, int first, int m, const double* coef, double* omega, int64_t du,
+                     int64_t dd, int64_t ld, int acc, cudaStream_t s) {
+  if (m <= 0) return;
+  std::vector<const void*> ptr(m);
+  for (int n = 0; n < m; ++n) ptr[n] = st.at(first + n);
+  DevBuf<const void*> dptr(m);
+  ED_CUDA(cudaMemcpyAsync(dptr.p, ptr.data(), m * sizeof(void*), cudaMemcpyHostToDevice, s));
+  const size_t smem = (size_t)m * (sizeof(void*) + sizeof(double));
+  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((du * dd + 255) / 256, 152 * 8));
+  ProfScope ps_(K_VECTOR, s, (double)m * du * ld * esize(dtype) + 8.0 * du * dd * (acc ? 2 : 1));
+  if (dtype == ED_FP64)
+    k_ritz_sum<double><<<g, 256, smem, s>>>((const double* const*)dptr.p, m, coef, omega, du, dd, ld, acc);
+  else
+    k_ritz_sum<float><<<g, 256, smem, s>>>((const float* const*)dptr.p, m, coef, omega, du, dd, ld, acc);
+  ED_CHECK_LAUNCH();
+  ED_CUDA(cudaStreamSynchronize(s));  // the pointer table goes out of scope
+}
+
 // Runs pass 1 (until the Ritz estimate < tol_ritz) and the retrace; returns levels used.
+// Pass 0 runs until the Ritz estimate < tol_ritz; the ground state sum_n s_n v_n then comes from
+// the stored vectors into omega64 (FP64; *summed64 = true) or, when they could not all be stored,
+// from pass 1, a retrace accumulating into omega (the vectors' dtype).  Returns the levels used.
 static int lanczos_pass(ed_cluster& c, const SectorView& sv, int dtype, LanczosRun& L, char* V0, char* V1, char* Vstart,
-                        void* omega, double tol_ritz, double* host, bool* breakdown, cudaStream_t s) {
+                        void* omega, double* omega64, bool* summed64, double tol_ritz, double* host, bool* breakdown,
+                        cudaStream_t s) {
   const int64_t du = sv.d_up, dd = sv.d_dn, ld = sv.ld, dim = du * dd;
   const size_t bytes = (size_t)du * ld * esize(dtype);
   char* V[2] = {V0, V1};
   int m = 0;
   *breakdown = false;
+  *summed64 = false;
+  VectorStore store;
   for (int pass = 0; pass < 2; ++pass) {
     L.reset(s);
     ED_CUDA(cudaMemcpyAsync(V[0], Vstart, bytes, cudaMemcpyDeviceToDevice, s));
     ED_CUDA(cudaMemsetAsync(V[1], 0, bytes, s));
+    if (pass == 0) {
+      store.start(bytes);
+      store.push(V[0], s);
+    }
     if (pass == 1) launch_copy_ld(dtype, omega, dd, dtype, V[0], ld, L.svec.p, du, dd, s);
     int cur = 0;
     const int nmax = pass == 0 ? L.M : m - 1;
     for (int n = 0; n < nmax; ++n) {
       launch_lanczos_step(sv, c.hp, dtype, V[cur], V[cur ^ 1], 0, 1, n, L.ls, L.nblk, s);
       launch_lanczos_next(dtype, V[cur ^ 1], V[cur], du, dd, ld, 0, 1, n, L.ls, pass == 1 ? omega : nullptr, L.svec.p, s);
+      if (pass == 0) store.push(V[cur ^ 1], s);
       cur ^= 1;
       if (pass == 0 && ((n + 1) % kCheck == 0 || n + 1 == L.M)) {
         ED_CUDA(cudaMemcpyAsync(host + 8, L.active.p, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -122,6 +234,11 @@ static int lanczos_pass(ed_cluster& c, const SectorView& sv, int dtype, LanczosR
         if (!act || host[2] < tol_ritz * std::max(1.0, std::fabs(host[0]))) break;
       }
     }
+    if (pass == 0 && store.ok && store.count >= m) {
+      ritz_sum(dtype, store, 0, m, L.svec.p, omega64, du, dd, ld, 0, s);
+      *summed64 = true;
+      break;
+    }
   }
   return m;
 }
@@ -142,6 +259,7 @@ static int refine_round(ed_cluster& c, const SectorView& sv, LanczosRun& L, floa
   const int64_t du = sv.d_up, dd = sv.d_dn, ld = sv.ld;
   float* V[2] = {V0, V1};
   int m = 0;
+  VectorStore store;  // q_1, q_2, ...: with all of them stored the retrace is skipped
   for (int pass = 0; pass < 2; ++pass) {
     L.reset(s);
     const double a0 = E, b1 = rnorm, inv = 1.0 / rnorm;
@@ -150,6 +268,10 @@ static int refine_round(ed_cluster& c, const SectorView& sv, LanczosRun& L, floa
     ED_CUDA(cudaMemcpyAsync(scal.p + 5, &inv, sizeof(double), cudaMemcpyHostToDevice, s));
     launch_copy_ld(ED_FP32, V[0], ld, ED_FP64, omega, dd, nullptr, du, dd, s);       // q_0
     launch_copy_ld(ED_FP32, V[1], ld, ED_FP64, r, dd, scal.p + 5, du, dd, s);        // q_1 = r / |r|
+    if (pass == 0) {
+      store.start((size_t)du * ld * sizeof(float));
+      store.push(V[1], s);
+    }
     if (pass == 1) {
       // omega <- s_0 omega + (s_1 / |r|) r, in FP64; the loop adds s_n q_n for n >= 2
       double sv01[2];
@@ -165,6 +287,7 @@ static int refine_round(ed_cluster& c, const SectorView& sv, LanczosRun& L, floa
       launch_lanczos_step(sv, c.hp, ED_FP32, V[cur], V[cur ^ 1], 0, 1, n, L.ls, L.nblk, s);
       launch_lanczos_next(ED_FP32, V[cur ^ 1], V[cur], du, dd, ld, 0, 1, n, L.ls, pass == 1 ? omega : nullptr, L.svec.p,
                           s, ED_FP64);
+      if (pass == 0) store.push(V[cur ^ 1], s);
       cur ^= 1;
       if (pass == 0 && ((n + 1) % kCheck == 0 || n + 1 == L.M)) {
         ED_CUDA(cudaMemcpyAsync(host + 8, L.active.p, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -184,6 +307,17 @@ static int refine_round(ed_cluster& c, const SectorView& sv, LanczosRun& L, floa
         m = levels;
         if (!act || host[2] < tol_ritz) break;
       }
+    }
+    if (pass == 0 && store.ok && store.count >= m - 1) {
+      // omega <- s_0 omega + (s_1 / |r|) r + sum_{n >= 2} s_n q_n, the q_n (n >= 2) from the store
+      double sv01[2];
+      ED_CUDA(cudaMemcpyAsync(sv01, L.svec.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      ED_CUDA(cudaStreamSynchronize(s));
+      const double cc[2] = {sv01[0], m > 1 ? sv01[1] / rnorm : 0.0};
+      ED_CUDA(cudaMemcpyAsync(scal.p + 5, cc, 2 * sizeof(double), cudaMemcpyHostToDevice, s));
+      launch_axpby(ED_FP64, omega, ED_FP64, omega, scal.p + 5, ED_FP64, r, scal.p + 6, du, dd, dd, s);
+      ritz_sum(ED_FP32, store, 1, m - 2, L.svec.p + 2, omega, du, dd, ld, 1, s);
+      break;
     }
   }
   return m;
@@ -233,8 +367,9 @@ GroundResult run_ground_state(ed_cluster& c, int dtype, double tol, int max_iter
     // the s_n v_n, converted to FP64 once)
     DevBuf<float> om32(dt == ED_FP32 ? dim : 0);
     void* acc = dt == ED_FP32 ? (void*)om32.p : (void*)c.omega.p;
-    int m = lanczos_pass(c, sv, dt, L, V0.p, V1.p, Vs.p, acc, tol_ritz, host, &breakdown, s);
-    if (dt == ED_FP32) launch_copy_ld(ED_FP64, c.omega.p, dd, ED_FP32, om32.p, dd, nullptr, du, dd, s);
+    bool summed64 = false;
+    int m = lanczos_pass(c, sv, dt, L, V0.p, V1.p, Vs.p, acc, c.omega.p, &summed64, tol_ritz, host, &breakdown, s);
+    if (dt == ED_FP32 && !summed64) launch_copy_ld(ED_FP64, c.omega.p, dd, ED_FP32, om32.p, dd, nullptr, du, dd, s);
     total_iters += m;
     const double lam0 = host[0], lam1 = host[1];
     // FP64 polish: normalize omega, Rayleigh quotient E and explicit residual r = H omega - E omega

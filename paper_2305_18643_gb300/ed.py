@@ -60,6 +60,7 @@ def lib():
             "ed_ground_vector": (i32, [vp, vp, i32]),
             "ed_green": (i32, [vp, _dp, i32, C.c_double, i32, i32, vp, i32]),
             "ed_green_stats": (i32, [vp, C.POINTER(i64), C.POINTER(i32)]),
+            "ed_low_states": (i32, [vp, i32, _dp, _dp, C.POINTER(i32)]),
             "ed_sector_dims": (i32, [vp, i32, i32, C.POINTER(i64), C.POINTER(i64)]),
             "ed_basis": (i32, [i32, i32, vp, i64, C.POINTER(i64)]),
             "ed_hop_table": (i32, [vp, i32, vp, vp, vp, i64, C.POINTER(i64), C.POINTER(i32)]),
@@ -162,6 +163,15 @@ def ed_green(h, omega, eta, n_sites, axis=ED_AXIS_REAL, spin=0, out_ptr=None):
 
 
 ED_OPT_BAND_MAX_DIM, ED_OPT_CF_MAX_STEPS, ED_OPT_GF_TOL, ED_OPT_TWO_PASS_MIN_BYTES = 1, 2, 3, 4
+ED_OPT_DAVIDSON_STATES, ED_OPT_TEMPERATURE = 5, 6
+
+
+def ed_low_states(h, capacity=16):
+    """(energies, mixed-state weights) of the states behind the cluster's Green function."""
+    E, wt, n = np.zeros(capacity), np.zeros(capacity), C.c_int()
+    _check(lib().ed_low_states(h, int(capacity), E.ctypes.data_as(_dp), wt.ctypes.data_as(_dp), C.byref(n)))
+    k = min(n.value, capacity)
+    return E[:k], wt[:k]
 
 
 def ed_set_option(h, option, value):

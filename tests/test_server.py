@@ -186,3 +186,22 @@ def test_concurrent_band_requests_of_different_sizes():
             alone = srv.wait(srv.submit(reqs[k], omega=om, axis=ed.ED_AXIS_MATSUBARA, precision=ed.ED_FP32,
                                         gf_method=ed.ED_GF_BAND, seed=3 + k))[0]
             assert abs(alone["E0"] - out[k]["E0"]) <= 1e-12 * abs(alone["E0"])
+
+
+def test_served_14_orbital_band_request_matches_the_oracle():
+    """A served band request of 14 orbitals (FP64, the two-pass kernels on a lane): its ground
+    energy equals the oracle's (tests/golden/ladder14_band.npz) to 1e-10, and its G equals what
+    the single-cluster path gives for the same cluster (the path whose band G is compared with
+    the oracle's band Lanczos in tests/test_benchmarked_paths.py)."""
+    import os
+    g = np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "ladder14_band.npz"))
+    c = W.served_request(np.random.default_rng(int(g["seed"])), sizes=(14,))
+    om = W.matsubara_grid(64)
+    with ed.Server(64 * GB, max_slots=2, batch_max_dim=0) as srv:
+        r, G = srv.wait(srv.submit(c, omega=om, axis=ed.ED_AXIS_MATSUBARA, precision=ed.ED_FP64,
+                                   gf_method=ed.ED_GF_BAND, seed=11))
+    assert r["status"] >= 0, r.get("error")
+    assert abs(r["E0"] - float(g["E0"])) <= 1e-10 * abs(float(g["E0"]))
+    with ed.Cluster(c, precision=ed.ED_FP64, gf_method=ed.ED_GF_BAND, seed=11) as cl:
+        st, Gs = ed.ed_green(cl.h, om, 0.0, 14, axis=ed.ED_AXIS_MATSUBARA)
+    assert np.max(np.abs(G[0] - Gs)) <= 1e-10
