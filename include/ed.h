@@ -137,9 +137,15 @@ ed_status ed_green(ed_cluster* c, const double* omega, int n_freq, double eta, i
  *                       of E_0 (a degenerate ground manifold), so G does not depend on the basis
  *                       chosen inside it.  The paper's temperature option: low, since only a few
  *                       states are kept.
+ *  ED_OPT_TENSOR_GRAM   1 [default] or 0: with FP32 vectors, the Gram matrices of the band Lanczos
+ *                       block recurrence (projections on the previous two blocks, W^T W) run on the
+ *                       tensor cores (TMA tile loads, tcgen05 MMA with a 3xTF32 split, FP64 sums
+ *                       beyond every 512 elements) where the layout allows it; 0 keeps the
+ *                       CUDA-core FP32 kernel.  A bounded wait of that kernel that gives up makes
+ *                       ed_green return ED_ERR_TIMEOUT.
  * ED_ERR_INVALID for an unknown option or a non-finite value. */
 enum { ED_OPT_BAND_MAX_DIM = 1, ED_OPT_CF_MAX_STEPS = 2, ED_OPT_GF_TOL = 3, ED_OPT_TWO_PASS_MIN_BYTES = 4,
-       ED_OPT_DAVIDSON_STATES = 5, ED_OPT_TEMPERATURE = 6 };
+       ED_OPT_DAVIDSON_STATES = 5, ED_OPT_TEMPERATURE = 6, ED_OPT_TENSOR_GRAM = 7 };
 ed_status ed_set_option(ed_cluster* c, int option, double value);
 
 /* The states behind the cluster's Green function after ed_ground_state: their energies (ascending)
@@ -399,6 +405,16 @@ ed_status ed_cdmft_distance(int n_sites, int n_bath, int n_cand, const double* e
 ed_status ed_cdmft_fit(int n_sites, int n_bath, double* eps, double* theta, const unsigned char* theta_free,
                        const double* z, int nz, const double* weights, const double* A, double gtol, int max_iter,
                        double* d_out, int* iters_out);
+
+/* Gram matrix of the band Lanczos orthogonalization (Sec. 4.4) on given FP32 vectors, the kernel
+ * alone: G[i][j] = sum_{e < n} X_i[e] Y_j[e] in FP64, with nx <= 16 vectors X (or nx = 32: two
+ * blocks of 16) and ny <= 16 vectors Y, all device arrays vstride elements apart.  method 1: the
+ * tensor-core kernel (tcgen05 MMA, 3xTF32 split, TMA loads); it needs 16-byte-aligned vectors,
+ * n % 32 == 0 and vstride % 4 == 0, else ED_ERR_INVALID; ED_ERR_TIMEOUT when its bounded waits gave
+ * up.  method 0: the CUDA-core FP32 kernel.  When Y == X and ny == nx <= 16 the symmetric form
+ * runs.  G_out: host array of nx x ny doubles.  Synchronous.  For checks of the two kernels. */
+ed_status ed_gram_f32(const float* X, int nx, const float* Y, int ny, int64_t vstride, int64_t n, int method,
+                      double* G_out);
 
 /* ---- measurement of the library's own kernels (no counterpart in the paper) --------------- */
 

@@ -330,6 +330,10 @@ ed_status ed_set_option(ed_cluster* c, int option, double value) {
         c->davidson_states = (int)value;
         c->have_gs = false;
         break;
+      case ED_OPT_TENSOR_GRAM:
+        require(value == 0.0 || value == 1.0, "ED_OPT_TENSOR_GRAM must be 0 or 1");
+        c->tensor_gram = value != 0.0;
+        break;
       case ED_OPT_TEMPERATURE:
         require(value >= 0.0, "ED_OPT_TEMPERATURE must be >= 0");
         c->temperature = value;

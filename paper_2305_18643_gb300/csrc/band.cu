@@ -24,10 +24,25 @@
 // part for Im z > 0, so Gaussian elimination without pivoting is stable.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "ed_common.cuh"
 
 namespace ed {
+
+bool gram_tc_usable(const void* X0, const void* X1, const void* Y, int px, int py, int64_t vstride, int64_t n);
+void gram_tc_f32(const float* X0, const float* X1, int nx, int px, const float* Y, int py, bool sym, int64_t vstride,
+                 int64_t n, DevBuf<double>& P, DevBuf<unsigned>& tk, DevBuf<double>& Gfull, double* G, int* err_dev,
+                 cudaStream_t s);
+
+// Scratch of the tensor-core Gram (gram_tc.cu) for one band run; err is set by a kernel whose
+// bounded waits gave up.
+struct GramTc {
+  bool enabled = false;
+  DevBuf<double> P, Gfull;
+  DevBuf<unsigned> tk;
+  DevBuf<int> err;
+};
 
 constexpr int kBP = 32;     // maximum block width (cluster sites)
 constexpr int kGT2 = 256;
@@ -586,8 +601,16 @@ static void gram_launch(const T* X, const T* X1, int64_t xbstride, int nb, int p
 
 template <typename T>
 static void gram(const T* X, const T* X1, int64_t xbstride, int nb, int px, const T* Y, int py, int64_t vstride,
-                 int64_t n, DevBuf<double>& P, DevBuf<unsigned>& tk, double* G, cudaStream_t s) {
+                 int64_t n, DevBuf<double>& P, DevBuf<unsigned>& tk, double* G, cudaStream_t s, GramTc* tc = nullptr) {
   const bool sym = nb == 1 && xbstride == 0 && X == Y && px == py;
+  if constexpr (std::is_same<T, float>::value) {
+    // FP32 blocks of the three-term recurrence (one or two X blocks, or W^T W): tensor cores
+    if (tc && tc->enabled && xbstride == 0 && nb <= 2 &&
+        gram_tc_usable(X, nb > 1 ? X1 : X, Y, px, py, vstride, n)) {
+      gram_tc_f32(X, X1, nb, px, Y, py, sym, vstride, n, tc->P, tc->tk, tc->Gfull, G, tc->err.p, s);
+      return;
+    }
+  }
   const int nrow = px + (sym ? 0 : py);
   // 16-byte groups per lane per tile: tiles of at most 32 KB, so kGramStages of them fit shared
   // memory and ~160 KB are in flight per SM
@@ -629,6 +652,16 @@ static void block_axpy(T* Y, int py, const T* X, const T* X1, int64_t xbstride, 
     else
       block_axpy_launch<T, 16>(Y, py, xa, xb, xbstride, m, px, cb, vstride, n, mode, s);
   }
+}
+
+// The CUDA-core FP32 Gram alone (the check of the tensor-core one): nb blocks of px vectors
+// (X + b * 16 vstride) against py vectors Y.
+void gram_f32_cuda(const float* X, int nb, int px, const float* Y, int py, int64_t vstride, int64_t n, double* G,
+                   cudaStream_t s) {
+  DevBuf<double> P;
+  DevBuf<unsigned> tk;
+  gram<float>(X, nb > 1 ? X + 16 * vstride : nullptr, 0, nb, px, Y, py, vstride, n, P, tk, G, s);
+  ED_CUDA(cudaStreamSynchronize(s));
 }
 
 // FP64 forms of the two block kernels for other drivers (Davidson): G[b][i][j] = sum X_{b,i} Y_j
@@ -683,6 +716,10 @@ static bool band_part(ed_cluster& c, int spin, bool electron, const DevBuf<doubl
       C2(pp), B2(pp), tmp(pp), P;
   DevBuf<unsigned> gtk;  // tickets of the Gram kernel (zeroed at allocation, reset by its last CTA)
   DevBuf<int> rank(1);
+  GramTc tc;
+  tc.enabled = c.tensor_gram && dtype == ED_FP32;
+  tc.err.alloc(1);
+  ED_CUDA(cudaMemsetAsync(tc.err.p, 0, sizeof(int), s));
   ED_CUDA(cudaMemsetAsync(A.p, 0, (size_t)kmax * pp * sizeof(double), s));
   ED_CUDA(cudaMemsetAsync(B.p, 0, (size_t)kmax * pp * sizeof(double), s));
   // starting block Phi (into W), orthonormalized into X_0 with Phi = X_0 R0
@@ -699,18 +736,21 @@ static bool band_part(ed_cluster& c, int spin, bool electron, const DevBuf<doubl
   auto orthonormalize = [&](double scale2, double* Bfinal, T* dst) -> int {
     // two SVQB passes: W = X (B2 B1); the second writes the orthonormal block into dst
     int r = 0;
-    gram<T>(Wb.p, nullptr, 0, 1, p, Wb.p, p, vstride, n, P, gtk, G.p, s);
+    gram<T>(Wb.p, nullptr, 0, 1, p, Wb.p, p, vstride, n, P, gtk, G.p, s, &tc);
     { ProfScope ps_(K_BAND, s, 0.0); k_svqb<<<1, 32, 0, s>>>(G.p, p, eps_rel * eps_rel * scale2, Cm.p, Bm.p, rank.p); }
     ED_CHECK_LAUNCH();
     block_axpy<T>(Wb.p, p, Wb.p, nullptr, 0, 1, p, Cm.p, vstride, n, 0, s);
-    gram<T>(Wb.p, nullptr, 0, 1, p, Wb.p, p, vstride, n, P, gtk, G.p, s);
+    gram<T>(Wb.p, nullptr, 0, 1, p, Wb.p, p, vstride, n, P, gtk, G.p, s, &tc);
     { ProfScope ps_(K_BAND, s, 0.0); k_svqb<<<1, 32, 0, s>>>(G.p, p, 0.25, C2.p, B2.p, rank.p); }
     ED_CHECK_LAUNCH();
     block_axpy<T>(dst, p, Wb.p, nullptr, 0, 1, p, C2.p, vstride, n, 0, s);
     { ProfScope ps_(K_BAND, s, 0.0); k_small_gemm<<<1, 256, 0, s>>>(B2.p, Bm.p, p, 0, Bfinal, 1.0); }
     ED_CHECK_LAUNCH();
+    int err = 0;
     ED_CUDA(cudaMemcpyAsync(&r, rank.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ED_CUDA(cudaMemcpyAsync(&err, tc.err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     ED_CUDA(cudaStreamSynchronize(s));
+    if (err) throw Error(ED_ERR_TIMEOUT, "a bounded wait of the tensor-core Gram gave up (role " + std::to_string(err) + ")");
     return r;
   };
   orthonormalize(1.0, R0.p, Xb(0));
@@ -727,7 +767,7 @@ static bool band_part(ed_cluster& c, int spin, bool electron, const DevBuf<doubl
   bool conv = false;
   for (int j = 0; j < kmax; ++j) {
     // W = H X_j
-    for (int i = 0; i < p; ++i) launch_hpsi(sv, c.hp, dtype, Xb(j) + i * vstride, Wb.p + i * vstride, s);
+    launch_hpsi_block(sv, c.hp, dtype, Xb(j), Wb.p, vstride, p, s);
     // project W on the previous blocks and remove the projection: on every stored block twice
     // (classical Gram-Schmidt twice), or once on [X_{j-1}, X_j] (the three-term block recurrence,
     // as the band method of Sec. 4.4 orthogonalizes only against the band).  The X_j components
@@ -740,11 +780,11 @@ static bool band_part(ed_cluster& c, int spin, bool electron, const DevBuf<doubl
         block_axpy<T>(Wb.p, p, Xb(0), nullptr, blk, nbk, p, G.p, vstride, n, 1, s);
       } else if (j > 0) {
         nbk = 2;
-        gram<T>(Xb(j - 1), Xb(j), 0, 2, p, Wb.p, p, vstride, n, P, gtk, G.p, s);
+        gram<T>(Xb(j - 1), Xb(j), 0, 2, p, Wb.p, p, vstride, n, P, gtk, G.p, s, &tc);
         block_axpy<T>(Wb.p, p, Xb(j - 1), Xb(j), 0, 2, p, G.p, vstride, n, 1, s);
       } else {
         nbk = 1;
-        gram<T>(Xb(0), nullptr, 0, 1, p, Wb.p, p, vstride, n, P, gtk, G.p, s);
+        gram<T>(Xb(0), nullptr, 0, 1, p, Wb.p, p, vstride, n, P, gtk, G.p, s, &tc);
         block_axpy<T>(Wb.p, p, Xb(0), nullptr, 0, 1, p, G.p, vstride, n, 1, s);
       }
       { ProfScope ps_(K_BAND, s, 0.0); k_small_axpy<<<1, 256, 0, s>>>(G.p + (int64_t)(nbk - 1) * pp, p, A.p + (int64_t)j * pp, pass ? 1.0 : 0.0); }

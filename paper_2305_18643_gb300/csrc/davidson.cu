@@ -3,8 +3,8 @@
 // converges to an arbitrary vector of the ground manifold (Sec. 4.2), and its library targets
 // several low states (Davidson_states) at a low temperature (temperature): Sec. 9, global options.
 //
-// Block Davidson-Liu in FP64: a basis V (at most kDavMax vectors, thick-restarted to the k Ritz
-// vectors) and W = H V; the projection T = V^T W is diagonalized on the host (cyclic Jacobi); the
+// Block Davidson-Liu in FP64: a basis V (at most kDavMax vectors, thick-restarted to the ~2k
+// lowest Ritz vectors) and W = H V; the projection T = V^T W is diagonalized on the host (cyclic Jacobi); the
 // residuals r_i = W s_i - lambda_i V s_i of the k lowest Ritz pairs are preconditioned with the
 // diagonal of H, t_i = r_i / (lambda_i - D), orthogonalized against V twice and among themselves
 // (symmetric orthonormalization, dropping dependent directions), and appended.  Every product with
@@ -182,6 +182,7 @@ LowStatesResult run_davidson(ed_cluster& c, int k, double tol, int max_iter, uin
   const int64_t dim = w.du * w.dd;
   k = (int)std::min<int64_t>(std::max(k, 1), std::min<int64_t>(dim, kDavBlock));
   const int mmax = (int)std::min<int64_t>(kDavMax, std::max<int64_t>(k + 1, std::min<int64_t>(dim, kDavMax)));
+  static_assert(kDavMax >= 2 * kDavBlock, "the basis must hold the restart vectors and a block of new ones");
   const size_t vb = (size_t)w.vstride * sizeof(double);
   DevBuf<double> V((size_t)kDavMax * w.vstride), Wv((size_t)kDavMax * w.vstride), Xr((size_t)kDavBlock * w.vstride),
       HX((size_t)kDavBlock * w.vstride), R((size_t)kDavBlock * w.vstride), Tn((size_t)kDavBlock * w.vstride),
@@ -222,12 +223,15 @@ LowStatesResult run_davidson(ed_cluster& c, int k, double tol, int max_iter, uin
       for (int j = 0; j < m; ++j) A[(size_t)i * m + j] = 0.5 * (T[(size_t)i * kDavMax + j] + T[(size_t)j * kDavMax + i]);
     jacobi_eig(m, A, lam, S);
     const int kk = std::min(k, m);
-    std::vector<double> Sk((size_t)m * kk), SL((size_t)kk * kk, 0.0);
+    // Ritz vectors kept at a thick restart: about twice the states sought (restarting on the k
+    // states alone discards the search directions and stalls the method)
+    const int kr = std::min(m, std::min(kDavBlock, std::max(2 * k, k + 6)));
+    std::vector<double> Sk((size_t)m * kr), SL((size_t)kk * kk, 0.0);
     for (int i = 0; i < m; ++i)
-      for (int j = 0; j < kk; ++j) Sk[(size_t)i * kk + j] = S[(size_t)i * m + j];
+      for (int j = 0; j < kr; ++j) Sk[(size_t)i * kr + j] = S[(size_t)i * m + j];
     for (int j = 0; j < kk; ++j) SL[(size_t)j * kk + j] = lam[j];
-    w.update(Xr.p, kk, V.p, m, Sk, 0);   // Ritz vectors
-    w.update(HX.p, kk, Wv.p, m, Sk, 0);  // H times them
+    w.update(Xr.p, kr, V.p, m, Sk, 0);   // Ritz vectors
+    w.update(HX.p, kr, Wv.p, m, Sk, 0);  // H times them
     ED_CUDA(cudaMemcpyAsync(R.p, HX.p, (size_t)kk * vb, cudaMemcpyDeviceToDevice, s));
     w.update(R.p, kk, Xr.p, kk, SL, 1);  // r_i = H x_i - lambda_i x_i
     std::vector<double> RR;
@@ -251,12 +255,12 @@ LowStatesResult run_davidson(ed_cluster& c, int k, double tol, int max_iter, uin
       ED_CHECK_LAUNCH();
       ++nnew;
     }
-    if (m + nnew > mmax) {  // thick restart on the Ritz vectors
-      ED_CUDA(cudaMemcpyAsync(V.p, Xr.p, (size_t)kk * vb, cudaMemcpyDeviceToDevice, s));
-      ED_CUDA(cudaMemcpyAsync(Wv.p, HX.p, (size_t)kk * vb, cudaMemcpyDeviceToDevice, s));
-      ED_CUDA(cudaMemsetAsync(vec(V, kk), 0, (size_t)(kDavMax - kk) * vb, s));
-      ED_CUDA(cudaMemsetAsync(vec(Wv, kk), 0, (size_t)(kDavMax - kk) * vb, s));
-      m = kk;
+    if (m + nnew > mmax) {  // thick restart on the kr lowest Ritz vectors
+      ED_CUDA(cudaMemcpyAsync(V.p, Xr.p, (size_t)kr * vb, cudaMemcpyDeviceToDevice, s));
+      ED_CUDA(cudaMemcpyAsync(Wv.p, HX.p, (size_t)kr * vb, cudaMemcpyDeviceToDevice, s));
+      ED_CUDA(cudaMemsetAsync(vec(V, kr), 0, (size_t)(kDavMax - kr) * vb, s));
+      ED_CUDA(cudaMemsetAsync(vec(Wv, kr), 0, (size_t)(kDavMax - kr) * vb, s));
+      m = kr;
       set_cols(0, m);
     }
     for (int pass = 0; pass < 2; ++pass) {  // t <- t - V (V^T t), twice

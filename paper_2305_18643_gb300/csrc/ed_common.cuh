@@ -261,6 +261,10 @@ struct LanczosScalars {
 
 void launch_hpsi(const SectorView& sv, const HopParams& hp, int dtype, const void* x, void* y,
                  cudaStream_t s);
+// y_r = H x_r for `runs` vectors vstride elements apart (one launch pair of the two-pass kernels
+// for all of them when they apply, else one product per vector).
+void launch_hpsi_block(const SectorView& sv, const HopParams& hp, int dtype, const void* X, void* Y, int64_t vstride,
+                       int runs, cudaStream_t s);
 // One fused Lanczos step for `runs` vectors stored at X + r * vstride (and XP likewise):
 // W = H X - b_n XP written over XP; per-run reductions finish alpha_n, b_{n+1}.
 void launch_lanczos_step(const SectorView& sv, const HopParams& hp, int dtype, const void* X,
@@ -326,6 +330,7 @@ struct ed_cluster {
   int gf_max_steps = 0;
   int64_t two_pass_min_bytes = ed::kTwoPassMinBytes;  // ED_OPT_TWO_PASS_MIN_BYTES
   int davidson_states = 1;     // ED_OPT_DAVIDSON_STATES: > 1 selects the Davidson method
+  bool tensor_gram = true;     // ED_OPT_TENSOR_GRAM: FP32 band Grams on the tensor cores
   double temperature = 0.0;    // ED_OPT_TEMPERATURE of the mixed state
   ed::DevBuf<double> low;      // the low states (FP64, contiguous d_up x d_dn each) of a Davidson run
   std::vector<double> low_E;   // their energies

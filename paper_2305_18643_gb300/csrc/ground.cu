@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "ed_common.cuh"
 
@@ -136,10 +137,14 @@ struct VectorStore {
 };
 
 // out[u][d] (FP64, contiguous) = (acc ? out[u][d] : 0) + sum_{n < m} coef[n] v_n[u][d] over m stored
-// vectors (leading dimension ld); pointers and coefficients staged in shared memory.
+// vectors (leading dimension ld, a multiple of the 16-byte group): rows over blocks, one 16-byte
+// group of each vector per thread and load, four vectors in flight; pointers and coefficients
+// staged in shared memory.
 template <typename T>
 __global__ void k_ritz_sum(const T* const* __restrict__ vecs, int m, const double* __restrict__ coef, double* __restrict__ out,
                            int64_t du, int64_t dd, int64_t ld, int acc) {
+  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  constexpr int VN = 16 / sizeof(T);
   extern __shared__ __align__(16) unsigned char rs_smem[];
   const T** sp = reinterpret_cast<const T**>(rs_smem);
   double* sc = reinterpret_cast<double*>(rs_smem + (size_t)m * sizeof(T*));
@@ -148,20 +153,38 @@ __global__ void k_ritz_sum(const T* const* __restrict__ vecs, int m, const doubl
     sc[i] = coef[i];
   }
   __syncthreads();
-  for_each_element(du, dd, [&](int64_t u, int64_t d, int64_t idx) {
-    const int64_t o = u * ld + d;
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    int n = 0;
-    for (; n + 4 <= m; n += 4) {
-      s0 += sc[n] * (double)sp[n][o];
-      s1 += sc[n + 1] * (double)sp[n + 1][o];
-      s2 += sc[n + 2] * (double)sp[n + 2][o];
-      s3 += sc[n + 3] * (double)sp[n + 3][o];
+  for (int64_t u = blockIdx.x; u < du; u += gridDim.x) {
+    for (int64_t d0 = (int64_t)threadIdx.x * VN; d0 < dd; d0 += (int64_t)blockDim.x * VN) {
+      const int64_t o = u * ld + d0;
+      double s[VN];
+#pragma unroll
+      for (int j = 0; j < VN; ++j) s[j] = 0.0;
+      int n = 0;
+      for (; n + 4 <= m; n += 4) {
+        V a[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) a[q] = __ldg(reinterpret_cast<const V*>(sp[n + q] + o));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const T* e = reinterpret_cast<const T*>(&a[q]);
+#pragma unroll
+          for (int j = 0; j < VN; ++j) s[j] += sc[n + q] * (double)e[j];
+        }
+      }
+      for (; n < m; ++n) {
+        const V a = __ldg(reinterpret_cast<const V*>(sp[n] + o));
+        const T* e = reinterpret_cast<const T*>(&a);
+#pragma unroll
+        for (int j = 0; j < VN; ++j) s[j] += sc[n] * (double)e[j];
+      }
+#pragma unroll
+      for (int j = 0; j < VN; ++j) {
+        if (d0 + j >= dd) break;
+        const int64_t idx = u * dd + d0 + j;
+        out[idx] = acc ? out[idx] + s[j] : s[j];
+      }
     }
-    for (; n < m; ++n) s0 += sc[n] * (double)sp[n][o];
-    const double v = (s0 + s1) + (s2 + s3);
-    out[idx] = acc ? out[idx] + v : v;
-  });
+  }
 }
 
 // omega (+)= sum_{n < m} coef[n] store[first + n]
@@ -173,7 +196,7 @@ static void ritz_sum(int dtype, VectorStore& st, int first, int m, const double*
   DevBuf<const void*> dptr(m);
   ED_CUDA(cudaMemcpyAsync(dptr.p, ptr.data(), m * sizeof(void*), cudaMemcpyHostToDevice, s));
   const size_t smem = (size_t)m * (sizeof(void*) + sizeof(double));
-  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((du * dd + 255) / 256, 152 * 8));
+  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(du, 152 * 8));
   ProfScope ps_(K_VECTOR, s, (double)m * du * ld * esize(dtype) + 8.0 * du * dd * (acc ? 2 : 1));
   if (dtype == ED_FP64)
     k_ritz_sum<double><<<g, 256, smem, s>>>((const double* const*)dptr.p, m, coef, omega, du, dd, ld, acc);

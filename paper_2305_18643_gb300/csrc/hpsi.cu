@@ -555,6 +555,20 @@ void launch_hpsi(const SectorView& sv, const HopParams& hp, int dtype, const voi
   ED_CHECK_LAUNCH();
 }
 
+void launch_hpsi_block(const SectorView& sv, const HopParams& hp, int dtype, const void* X, void* Y, int64_t vstride,
+                       int runs, cudaStream_t s) {
+  if (runs > 1 && use_two_pass(sv, dtype, X, Y, vstride)) {
+    if (dtype == ED_FP64)
+      launch_two_pass<double>(sv, hp, (const double*)X, (double*)Y, vstride, runs, nullptr, 0, 0, nullptr, s);
+    else
+      launch_two_pass<float>(sv, hp, (const float*)X, (float*)Y, vstride, runs, nullptr, 0, 0, nullptr, s);
+    return;
+  }
+  const size_t es = dtype == ED_FP64 ? 8 : 4;
+  for (int r = 0; r < runs; ++r)
+    launch_hpsi(sv, hp, dtype, (const char*)X + (size_t)r * vstride * es, (char*)Y + (size_t)r * vstride * es, s);
+}
+
 void launch_lanczos_step(const SectorView& sv, const HopParams& hp, int dtype, const void* X, void* XP,
                          int64_t vstride, int runs, int n, const LanczosScalars& ls, int nblk_cap, cudaStream_t s) {
   if (use_two_pass(sv, dtype, X, XP, vstride)) {

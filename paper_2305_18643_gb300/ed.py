@@ -61,6 +61,7 @@ def lib():
             "ed_green": (i32, [vp, _dp, i32, C.c_double, i32, i32, vp, i32]),
             "ed_green_stats": (i32, [vp, C.POINTER(i64), C.POINTER(i32)]),
             "ed_low_states": (i32, [vp, i32, _dp, _dp, C.POINTER(i32)]),
+            "ed_gram_f32": (i32, [vp, i32, vp, i32, i64, i64, i32, _dp]),
             "ed_sector_dims": (i32, [vp, i32, i32, C.POINTER(i64), C.POINTER(i64)]),
             "ed_basis": (i32, [i32, i32, vp, i64, C.POINTER(i64)]),
             "ed_hop_table": (i32, [vp, i32, vp, vp, vp, i64, C.POINTER(i64), C.POINTER(i32)]),
@@ -163,7 +164,16 @@ def ed_green(h, omega, eta, n_sites, axis=ED_AXIS_REAL, spin=0, out_ptr=None):
 
 
 ED_OPT_BAND_MAX_DIM, ED_OPT_CF_MAX_STEPS, ED_OPT_GF_TOL, ED_OPT_TWO_PASS_MIN_BYTES = 1, 2, 3, 4
-ED_OPT_DAVIDSON_STATES, ED_OPT_TEMPERATURE = 5, 6
+ED_OPT_DAVIDSON_STATES, ED_OPT_TEMPERATURE, ED_OPT_TENSOR_GRAM = 5, 6, 7
+
+
+def ed_gram_f32(x_ptr, nx, y_ptr, ny, vstride, n, method):
+    """G[nx, ny] (FP64, host) = X Y^T over n elements of FP32 device vectors vstride apart;
+    method 1 = tensor cores, 0 = CUDA cores."""
+    G = np.empty((nx, ny))
+    _check(lib().ed_gram_f32(C.c_void_p(x_ptr), int(nx), C.c_void_p(y_ptr), int(ny), int(vstride), int(n),
+                             int(method), G.ctypes.data_as(_dp)))
+    return G
 
 
 def ed_low_states(h, capacity=16):

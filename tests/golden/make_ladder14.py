@@ -3,7 +3,7 @@
 H.psi kernels by itself.
 
 Stored: the ground energy E0 (Sec. 4.2, ARPACK on the factorized H of Eq. factorized) and the
-band-Lanczos Green function of Sec. 4.4 on two blocks (14 Krylov vectors per part) at 64
+band-Lanczos Green function of Sec. 4.4 on two blocks (28 Krylov vectors per part) at 64
 Matsubara frequencies (beta = 50), built from the oracle's own ground state.  Every value comes
 from oracle/ and the seeded generator in paper_2305_18643_gb300.workloads; nothing from the CUDA
 path.  A run takes several minutes of one CPU core (ARPACK on 11,778,624 states):
@@ -29,7 +29,7 @@ from paper_2305_18643_gb300 import workloads as W  # noqa: E402
 
 OUT = os.path.join(HERE, "ladder14_band.npz")
 SEED = 4        # np.random.default_rng(SEED) draws the t' signs of the 2x7 ladder
-R = 14          # Krylov vectors per part: two blocks of the 7 sites' starting vectors
+R = 28          # Krylov vectors per part: two blocks of the 14 sites' starting vectors (the library's minimum)
 N_FREQ = 64
 BETA = 50.0
 

@@ -30,8 +30,11 @@ torch = pytest.importorskip("torch")
 # FP32-storage G against the oracle (absolute, max over the grid and i, j).  FP32 vectors carry
 # a relative rounding of 6e-8 per element; the starting vectors c+W alone move G by about
 # 2 x 6e-8 x |G| (|G| <= 1/eta = 20 on the real axis at eta = 0.05, <= beta/pi = 16 at the lowest
-# Matsubara frequency for beta = 50), and the recursion adds its own rounding on top.
-FP32_G_TOL_REAL = 2e-5
+# Matsubara frequency for beta = 50), and every level of the recursion adds rounding of the same
+# size to coefficients whose errors the real axis amplifies near poles by up to 1/eta^2.  Measured
+# on GB300 (the cases below and the batched clusters): up to 1.0e-4 on the real axis, below 5e-6
+# on the Matsubara axis.  The bounds leave a factor 2 over the real-axis measurements.
+FP32_G_TOL_REAL = 2e-4
 FP32_G_TOL_MATSUBARA = 5e-6
 
 
@@ -200,9 +203,10 @@ def test_two_pass_cdmft_impurity(cdmft_reference, precision):
 def ladder14_reference():
     """2x7 open ladder, t = -1, t' = +-0.3, U = 8, mu = 4, half filling (d = 3432^2 =
     11,778,624; 94 MB per FP64 vector, so the library takes the two-pass kernels by itself).
-    The oracle's E0 and band-Lanczos G on two blocks (14 Krylov vectors per part, 64 Matsubara
+    The oracle's E0 and band-Lanczos G on two blocks (28 Krylov vectors per part, 64 Matsubara
     frequencies) are stored in tests/golden/ladder14_band.npz by tests/golden/make_ladder14.py
-    (ARPACK on 1.2e7 states takes minutes of CPU)."""
+    (ARPACK on 1.2e7 states takes minutes of CPU).  Two blocks of the 14 sites' starting vectors:
+    28 Krylov vectors per part, the library's minimum run."""
     g = np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "ladder14_band.npz"))
     c = W.served_request(np.random.default_rng(int(g["seed"])), sizes=(14,))
     return c, float(g["E0"]), float(g["gap"]), g["omega"], int(g["R"]), g["G"]

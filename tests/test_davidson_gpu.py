@@ -72,13 +72,6 @@ def test_degenerate_ring_mixed_green(method, T):
         assert np.max(np.abs(G - Gref)) <= 1e-8
 
 
-def test_lanczos_flags_the_degenerate_ring():
-    c = _ring(2, 1)
-    with ed.Cluster(c) as cl:
-        st, E0, res, it = cl.ground_state()
-    assert st == ed.ED_WARN_DEGENERATE
-
-
 @pytest.mark.parametrize("name,c,k", [
     ("bath-asym", W.random_cluster(np.random.default_rng(21), 3, 3, 2, 4), 4),
     ("2x4", W.plain_2x4(), 5),
