@@ -1,45 +1,51 @@
 // Gram of FP32 vector blocks on the fifth-generation tensor cores: the projections of the band
 // Lanczos orthogonalization (Sec. 4.4), G_b[i][j] = sum_e X_{b,i}[e] Y_j[e] over the vectors'
-// elements, a tall-skinny contraction (K = 1.5e8 elements at the 4x4 size, M <= 48, N = 16).
+// elements, a tall-skinny contraction (K = 1.5e8 elements at the 4x4 size, at most 32 X rows and
+// 16 Y rows).
 //
-// A K-tile is 32 consecutive elements of every vector (one 128-byte row per vector, 128-byte
-// swizzle).  Warp 0 loads the rows of the X blocks and of Y with TMA into a stage of shared memory
-// (kTcStages stages in flight); warps 4-7 split every value into x = hi + lo with hi = x truncated
-// to TF32 (exact in TF32) and lo = x - hi (13 significant bits), hi in place and lo beside it;
-// warp 1 issues the MMAs D += A_hi B_hi + A_hi B_lo + A_lo B_hi (kind::tf32, M = 128 rows of which
-// the vectors fill the first 16 nx + 16, N = 16 = the Y rows, K = 8 per instruction, 4 per
-// K-tile), accumulating in TMEM; every kTcFlush K-tiles warps 4-7 read D (one row per thread) and
-// add it to FP64 registers, while the MMAs continue in the second D buffer.  The three products
-// carry ~2^-21 relative error each (lo loses <= 2 bits in TF32), FP32 accumulation runs over at
-// most kTcFlush tiles, everything beyond is FP64.  CTAs take contiguous element chunks; their FP64
-// partials are added in CTA order by the last CTA (a ticket), so results are deterministic.
+// Layout of one pipeline stage: a 128-row tile of 128-byte rows (32 FP32 elements, 128-byte
+// swizzle).  A K-tile is 32 consecutive elements of the R vector rows involved (R = 16 for W^T W,
+// 32 for one X block and Y, 48 for two X blocks and Y); KT = 64 / R K-tiles are stacked in rows
+// [0, 64) of the stage (one for R = 48), so a stage always carries ~8 KB of vector data.
+// TMA loads them; warps 4-7 split every value x into a TF32 head h = rn(x) (in place) and a TF32
+// tail l = rn(x - h), written 64 rows further down.  One MMA per 8-element step then multiplies
+// the whole tile (all heads and tails: M = 128) by the Y rows of every stacked K-tile, heads and
+// tails (N = 128, 112 or 80 rows of the same tile), so a single kind::tf32 MMA yields the four
+// products h h, h l, l h and l l of every (i, j) pair, each in its own TMEM cell: no accumulator
+// mixes a product with one 2^11 times smaller.  Cross-K-tile cells are computed and ignored.
 //
-// Every mbarrier wait gives up after kTcSpin polls: the kernel then sets *err, lets the other roles
-// leave their loops, waits (bounded) for its TMA loads and MMAs in flight, frees its TMEM and
-// returns; the host turns *err into ED_ERR_TIMEOUT.
+// Accuracy: x = h + l + r with |r| <= 2^-22 |x| (round-to-nearest, unbiased), products of TF32
+// values are exact in FP32, and each TMEM cell accumulates the 4 MMAs of one stage only; every
+// stage is then read (tcgen05.ld) and added to a Kahan-compensated FP32 sum (the head products)
+// or a plain FP32 sum moved to FP64 every 64 stages (the tail products).  CTAs take contiguous
+// element chunks; a CTA reduces its lanes in a fixed order, and the last CTA (a ticket) adds the
+// per-CTA partials in CTA order, so results are deterministic.
+//
+// Every mbarrier wait gives up after ~2 s: the kernel then sets *err, lets the other roles leave
+// their loops, waits (bounded) for its TMA loads and MMAs in flight, frees its TMEM and returns;
+// the host turns *err into ED_ERR_TIMEOUT.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 
 #include "ed_common.cuh"
 
 namespace ed {
 
-constexpr int kTcRows = 128;    // MMA M: rows of the A tile (rows past the vectors stay zero)
-constexpr int kTcN = 16;        // MMA N: the Y block
-constexpr int kTcK = 32;        // elements per K-tile (a 128-byte row)
-constexpr int kTcStages = 4;
-constexpr int kTcFlush = 16;    // K-tiles accumulated in one TMEM buffer before a flush
-constexpr int kTcThreads = 256; // warp 0 TMA, warp 1 MMA + TMEM allocation, warps 4-7 split + flush
-constexpr int kTcTmemCols = 64; // two D buffers of 16 columns (the allocation unit is 32 columns)
-constexpr long long kTcSpin = 1ll << 27;
-constexpr int kTcTile = kTcRows * 128;  // bytes of one operand tile
+constexpr int kTcK = 32;         // elements per K-tile (a 128-byte row)
+constexpr int kTcStages = 8;
+constexpr int kTcThreads = 256;  // warp 0 TMA, warp 1 MMA + TMEM allocation, warps 4-7 split + flush
+constexpr int kTcTmemCols = 256; // two D buffers of up to 128 columns
+constexpr int kTcX2Every = 64;   // stages between moves of the tail sums to FP64
+constexpr long long kTcWaitNs = 2000000000ll;
+constexpr int kTcTile = 128 * 128;  // bytes of one stage
 
 struct TcShared {
-  uint8_t hi[kTcStages][kTcTile];
-  uint8_t lo[kTcStages][kTcTile];
+  uint8_t tile[kTcStages][kTcTile];
+  double red[128][16];
   unsigned long long full[kTcStages], conv[kTcStages], empty[kTcStages];
   unsigned long long dfull[2], dempty[2];
   uint32_t tmem;
@@ -66,13 +72,27 @@ __device__ __forceinline__ bool mb_try(unsigned long long* b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+__device__ __forceinline__ long long now_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 // Bounded wait for the phase of the given parity; false when it gave up (or another role did).
 __device__ __forceinline__ bool mb_wait(unsigned long long* b, uint32_t parity, volatile int* abort) {
-  for (long long i = 0; i < kTcSpin; ++i) {
+  if (mb_try(b, parity)) return true;
+  const long long t0 = now_ns();
+  for (int i = 1;; ++i) {
     if (mb_try(b, parity)) return true;
-    if ((i & 255) == 255 && *abort) return false;
+    if ((i & 63) == 0) {
+      if (*abort || now_ns() - t0 > kTcWaitNs) return false;
+    }
   }
-  return false;
+}
+// Bounded wait used while leaving: no abort check (the role's own operations must land).
+__device__ __forceinline__ void mb_drain(unsigned long long* b, uint32_t parity) {
+  const long long t0 = now_ns();
+  while (!mb_try(b, parity) && now_ns() - t0 < kTcWaitNs) {
+  }
 }
 
 __device__ __forceinline__ void tma_rows(void* dst, const CUtensorMap* map, int x, int y, unsigned long long* bar) {
@@ -92,20 +112,21 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   d |= (uint64_t)2 << 61;
   return d;
 }
-// Instruction descriptor, kind::tf32: D FP32, A and B TF32, both K-major, N = 16, M = 128.
-constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
-                              ((uint32_t)(kTcRows >> 4) << 24);
+// Instruction descriptor, kind::tf32: D FP32, A and B TF32, both K-major, M = 128, N given.
+__host__ __device__ constexpr uint32_t tc_idesc(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
 
-__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, int acc) {
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, int acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
-      ::"r"(d), "l"(a), "l"(b), "r"(kTcIdesc), "r"(acc)
+      ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
 __device__ __forceinline__ void mma_commit(unsigned long long* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s32(bar)) : "memory");
 }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, double (&acc)[16]) {
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
@@ -113,34 +134,45 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, double (&acc)[16]) {
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
         "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 16; ++i) acc[i] += (double)__uint_as_float(r[i]);
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ float tf32_rn(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
 }
 
-// nx X blocks (maps mx0, mx1; rows 16 b of the A tile) and, unless sym, Y (map my; rows 16 nx);
-// B = the Y rows (or X block 0 when sym).  Elements [blockIdx.x chunk, +chunk) of n.  P: per-CTA
-// partials [gridDim.x][rows][16]; the last CTA writes G[r][j] (rows r of the A tile, FP64).
+// R = vector rows of one K-tile: 16 (W^T W: X block 0 is also B), 32 (one X block, then Y),
+// 48 (X blocks 0 and 1, then Y).  Elements [blockIdx.x * chunk, +chunk) of n.  P: per-CTA
+// partials [gridDim.x][nout], nout = 16 * (X rows); the last CTA writes G[i][j] (FP64).
+template <int R>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_gram_tc(const __grid_constant__ CUtensorMap mx0, const __grid_constant__ CUtensorMap mx1,
-              const __grid_constant__ CUtensorMap my, int nx, int sym, int64_t n, int64_t chunk,
-              double* __restrict__ P, unsigned* __restrict__ ticket, double* __restrict__ G, int* __restrict__ err) {
+              const __grid_constant__ CUtensorMap my, int64_t n, int64_t chunk, double* __restrict__ P,
+              unsigned* __restrict__ ticket, double* __restrict__ G, int* __restrict__ err) {
+  constexpr int KT = R == 48 ? 1 : 64 / R;    // K-tiles stacked in one stage
+  constexpr int NLOAD = R / 16;               // 16-row TMA boxes per K-tile
+  constexpr int XROWS = R == 16 ? 16 : R - 16;  // rows whose Gram is wanted
+  constexpr int YOFF = R == 16 ? 0 : R - 16;    // first Y row of a K-tile
+  constexpr int N = R == 16 ? 128 : 128 - YOFF; // B rows: [YOFF, 128) of the stage
+  constexpr uint32_t IDESC = tc_idesc(N);
+  constexpr int NOUT = XROWS * 16;
   extern __shared__ __align__(1024) unsigned char tc_raw[];
   TcShared& S = *reinterpret_cast<TcShared*>(tc_raw + ((1024 - (s32(tc_raw) & 1023)) & 1023));
   __shared__ bool s_last;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int rows = 16 * nx + (sym ? 0 : 16);       // vector rows of the A tile
-  const int boff = sym ? 0 : 16 * nx;              // first B row
-  const int nload = nx + (sym ? 0 : 1);            // 16-row TMA boxes per stage
   const int64_t e0 = (int64_t)blockIdx.x * chunk;
   const int64_t e1 = e0 + chunk < n ? e0 + chunk : n;
   const int ntile = e0 < e1 ? (int)((e1 - e0 + kTcK - 1) / kTcK) : 0;
-  const int ngroup = (ntile + kTcFlush - 1) / kTcFlush;
+  const int nst = (ntile + KT - 1) / KT;
   volatile int* abort = &S.abort;
 
-  // zero both tiles of every stage (rows past the vectors must read as zero), barriers, TMEM
-  for (int i = threadIdx.x; i < kTcStages * 2 * kTcTile / 16; i += blockDim.x)
-    reinterpret_cast<uint4*>(&S.hi[0][0])[i] = make_uint4(0u, 0u, 0u, 0u);
+  // zero every stage once (rows never loaded must hold finite values), barriers, TMEM
+  for (int i = threadIdx.x; i < kTcStages * kTcTile / 16; i += blockDim.x)
+    reinterpret_cast<uint4*>(&S.tile[0][0])[i] = make_uint4(0u, 0u, 0u, 0u);
   if (threadIdx.x == 0) {
     for (int s = 0; s < kTcStages; ++s) {
       mb_init(&S.full[s], 1);
@@ -167,44 +199,41 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const uint32_t tmem = S.tmem;
 
   if (warp == 0) {
-    // ---- producer: TMA rows of every K-tile
+    // ---- producer: TMA rows of every stage (KT K-tiles, NLOAD boxes each)
     if (lane == 0) {
       int issued = 0;
-      for (int t = 0; t < ntile; ++t) {
+      for (int t = 0; t < nst; ++t) {
         const int s = t % kTcStages;
-        const uint32_t par = ((t / kTcStages) & 1) ^ 1;
-        if (!mb_wait(&S.empty[s], par, abort)) {
+        if (!mb_wait(&S.empty[s], ((t / kTcStages) & 1) ^ 1, abort)) {
           *abort = 1;
           atomicExch(err, 1);
           break;
         }
-        mb_expect(&S.full[s], (uint32_t)(nload * 16 * 128));
-        const int x = (int)(e0 + (int64_t)t * kTcK);
-        tma_rows(&S.hi[s][0], &mx0, x, 0, &S.full[s]);
-        if (nx > 1) tma_rows(&S.hi[s][16 * 128], &mx1, x, 0, &S.full[s]);
-        if (!sym) tma_rows(&S.hi[s][boff * 128], &my, x, 0, &S.full[s]);
+        const int kv = ntile - t * KT < KT ? ntile - t * KT : KT;
+        mb_expect(&S.full[s], (uint32_t)(kv * NLOAD * 16 * 128));
+        for (int kt = 0; kt < kv; ++kt) {
+          const int x = (int)(e0 + (int64_t)(t * KT + kt) * kTcK);
+          uint8_t* dst = &S.tile[s][kt * R * 128];
+          tma_rows(dst, &mx0, x, 0, &S.full[s]);
+          if (NLOAD == 3) tma_rows(dst + 16 * 128, &mx1, x, 0, &S.full[s]);
+          if (NLOAD >= 2) tma_rows(dst + (NLOAD - 1) * 16 * 128, &my, x, 0, &S.full[s]);
+        }
         ++issued;
       }
       // the loads in flight must land before the CTA's shared memory goes away
-      for (int t = issued > kTcStages ? issued - kTcStages : 0; t < issued; ++t) {
-        const int s = t % kTcStages;
-        for (long long i = 0; i < kTcSpin && !mb_try(&S.full[s], (t / kTcStages) & 1); ++i) {
-        }
-      }
+      for (int t = issued > kTcStages ? issued - kTcStages : 0; t < issued; ++t)
+        mb_drain(&S.full[t % kTcStages], (t / kTcStages) & 1);
     }
   } else if (warp == 1) {
-    // ---- MMA issuer
+    // ---- MMA issuer: D[db] = tile (128 rows) x tile rows [YOFF, 128)^T over the stage's 32 elements
     if (lane == 0) {
-      int committed_groups = 0;
-      for (int t = 0; t < ntile; ++t) {
-        const int s = t % kTcStages;
-        const int g = t / kTcFlush, db = g & 1;
-        if (t % kTcFlush == 0) {  // a new group starts: its D buffer must have been read
-          if (!mb_wait(&S.dempty[db], ((g >> 1) & 1) ^ 1, abort)) {
-            *abort = 1;
-            atomicExch(err, 2);
-            break;
-          }
+      int done = 0;
+      for (int t = 0; t < nst; ++t) {
+        const int s = t % kTcStages, db = t & 1;
+        if (!mb_wait(&S.dempty[db], ((t >> 1) & 1) ^ 1, abort)) {
+          *abort = 1;
+          atomicExch(err, 2);
+          break;
         }
         if (!mb_wait(&S.conv[s], (t / kTcStages) & 1, abort)) {
           *abort = 1;
@@ -212,39 +241,77 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t dcol = tmem + (uint32_t)(db * 32);
-        const uint32_t ah = s32(&S.hi[s][0]), al = s32(&S.lo[s][0]);
-        const uint32_t bh = ah + (uint32_t)(boff * 128), bl = al + (uint32_t)(boff * 128);
+        const uint32_t a = s32(&S.tile[s][0]);
+        const uint32_t b = a + (uint32_t)(YOFF * 128);
 #pragma unroll
-        for (int kk = 0; kk < kTcK / 8; ++kk) {
-          const int first = (t % kTcFlush == 0 && kk == 0) ? 0 : 1;
-          const uint32_t off = (uint32_t)(kk * 32);
-          mma_tf32(dcol, sw128_desc(ah + off), sw128_desc(bh + off), first);
-          mma_tf32(dcol, sw128_desc(ah + off), sw128_desc(bl + off), 1);
-          mma_tf32(dcol, sw128_desc(al + off), sw128_desc(bh + off), 1);
-        }
+        for (int kk = 0; kk < kTcK / 8; ++kk)
+          mma_tf32(tmem + (uint32_t)(db * 128), sw128_desc(a + 32 * kk), sw128_desc(b + 32 * kk), IDESC, kk);
         mma_commit(&S.empty[s]);  // the stage is free once these MMAs have read it
-        if (t % kTcFlush == kTcFlush - 1 || t + 1 == ntile) {
-          mma_commit(&S.dfull[db]);
-          ++committed_groups;
-        }
+        mma_commit(&S.dfull[db]);
+        ++done;
       }
       // MMAs in flight must finish before TMEM and shared memory are released
-      if (ntile > 0)
-        for (long long i = 0; i < kTcSpin && !mb_try(&S.empty[(ntile - 1) % kTcStages], ((ntile - 1) / kTcStages) & 1); ++i) {
-        }
-      (void)committed_groups;
+      if (done > 0) mb_drain(&S.empty[(done - 1) % kTcStages], ((done - 1) / kTcStages) & 1);
     }
   } else if (warp >= 4) {
-    // ---- split x = hi + lo, and flush D to FP64 (warp 4 + q reads TMEM lanes 32 q .. 32 q + 31)
+    // ---- split x = h + l and read the accumulators (warp 4 + q reads TMEM lanes 32 q .. 32 q + 31)
     const int tid = threadIdx.x - 128;
     const int q = warp - 4;
-    double acc[16];
+    const int r = 32 * q + lane;          // TMEM lane = tile row of this thread
+    const int rl = r & 63;                // row within the head (or tail) half
+    const int kt_me = rl / R;             // stacked K-tile of this row (>= KT: unused row)
+    const int ra = (32 * q & 63) / R;     // first stacked K-tile this warp's lanes cover
+    float s_h[16], c_h[16], x_l[16];
+    double x_d[16];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) acc[j] = 0.0;
+    for (int j = 0; j < 16; ++j) s_h[j] = c_h[j] = x_l[j] = 0.f, x_d[j] = 0.0;
     bool ok = true;
-    // every wait's outcome is made warp-uniform: tcgen05.ld below is a warp-collective instruction
-    for (int t = 0; t < ntile && ok; ++t) {
+
+    auto flush = [&](int u) -> bool {
+      const int db = u & 1;
+      // every wait's outcome is made warp-uniform: tcgen05.ld is a warp-collective instruction
+      if (!__all_sync(0xffffffffu, mb_wait(&S.dfull[db], (u >> 1) & 1, abort))) return false;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(db * 128);
+      float vh[16], vl[16];
+      if constexpr (R == 16) {
+        float ah[16], al[16], bh[16], bl[16];
+        tmem_ld16(base + (uint32_t)(16 * ra), ah);
+        tmem_ld16(base + (uint32_t)(64 + 16 * ra), al);
+        tmem_ld16(base + (uint32_t)(16 * ra + 16), bh);
+        tmem_ld16(base + (uint32_t)(64 + 16 * ra + 16), bl);
+        tmem_wait_ld();
+        const bool second = lane >= 16;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          vh[j] = second ? bh[j] : ah[j];
+          vl[j] = second ? bl[j] : al[j];
+        }
+      } else {
+        tmem_ld16(base + (uint32_t)(R * ra), vh);
+        tmem_ld16(base + (uint32_t)(64 + R * ra), vl);
+        tmem_wait_ld();
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mb_arrive(&S.dempty[db]);
+      if (kt_me < KT && u * KT + kt_me < ntile) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {  // Kahan-compensated head products, plain tail products
+          const float y = vh[j] - c_h[j];
+          const float t2 = s_h[j] + y;
+          c_h[j] = (t2 - s_h[j]) - y;
+          s_h[j] = t2;
+          x_l[j] += vl[j];
+        }
+      }
+      if (u % kTcX2Every == kTcX2Every - 1) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) x_d[j] += (double)x_l[j], x_l[j] = 0.f;
+      }
+      return true;
+    };
+
+    for (int t = 0; t < nst && ok; ++t) {
       const int s = t % kTcStages;
       if (!__all_sync(0xffffffffu, mb_wait(&S.full[s], (t / kTcStages) & 1, abort))) {
         *abort = 1;
@@ -252,37 +319,30 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         ok = false;
         break;
       }
-      float* hi = reinterpret_cast<float*>(&S.hi[s][0]);
-      float* lo = reinterpret_cast<float*>(&S.lo[s][0]);
-      for (int i = tid; i < rows * kTcK; i += 128) {
-        const float x = hi[i];
-        const float h = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
-        hi[i] = h;
-        lo[i] = x - h;
+      float4* tl = reinterpret_cast<float4*>(&S.tile[s][0]);
+#pragma unroll
+      for (int i = tid; i < 64 * 128 / 16; i += 128) {  // rows [0, 64): heads in place, tails 64 rows down
+        const float4 x = tl[i];
+        float4 h, l;
+        h.x = tf32_rn(x.x), h.y = tf32_rn(x.y), h.z = tf32_rn(x.z), h.w = tf32_rn(x.w);
+        l.x = tf32_rn(x.x - h.x), l.y = tf32_rn(x.y - h.y), l.z = tf32_rn(x.z - h.z), l.w = tf32_rn(x.w - h.w);
+        tl[i] = h;
+        tl[i + 64 * 128 / 16] = l;
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mb_arrive(&S.conv[s]);
-      if (t % kTcFlush == kTcFlush - 1 || t + 1 == ntile) {
-        const int g = t / kTcFlush, db = g & 1;
-        if (!__all_sync(0xffffffffu, mb_wait(&S.dfull[db], (g >> 1) & 1, abort))) {
-          *abort = 1;
-          atomicExch(err, 5);
-          ok = false;
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(db * 32), acc);
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        mb_arrive(&S.dempty[db]);
+      if (t > 0 && !flush(t - 1)) {
+        *abort = 1;
+        atomicExch(err, 5);
+        ok = false;
       }
     }
-    (void)ngroup;
-    const int r = 32 * q + lane;
-    if (r < rows) {
-      double* Pc = P + ((int64_t)blockIdx.x * rows + r) * 16;
-#pragma unroll
-      for (int j = 0; j < 16; ++j) Pc[j] = acc[j];
+    if (ok && nst > 0 && !flush(nst - 1)) {
+      *abort = 1;
+      atomicExch(err, 5);
     }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) S.red[r][j] = ((double)s_h[j] - (double)c_h[j]) + (x_d[j] + (double)x_l[j]);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -290,8 +350,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols) : "memory");
   }
+  // this CTA's partial: G_i,j = sum over the head and tail rows of row i in every stacked K-tile
+  for (int o = threadIdx.x; o < NOUT; o += blockDim.x) {
+    const int i = o >> 4, j = o & 15;
+    double v = 0.0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int kt = 0; kt < KT; ++kt) v += S.red[64 * h + kt * R + i][j];
+    P[(int64_t)blockIdx.x * NOUT + o] = v;
+  }
   // the last CTA adds the partials in CTA order
   __threadfence();
+  __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned tk = atomicAdd(ticket, 1u);
     s_last = (tk == gridDim.x - 1);
@@ -299,10 +370,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  for (int q = threadIdx.x; q < rows * 16; q += blockDim.x) {
-    double v = 0.0;
-    for (unsigned c = 0; c < gridDim.x; ++c) v += __ldcg(P + (int64_t)c * rows * 16 + q);
-    G[q] = v;
+  for (int o = threadIdx.x; o < NOUT; o += blockDim.x) {
+    double a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = 0.0;
+    const int G8 = (int)gridDim.x & ~7;
+    for (int c = 0; c < G8; c += 8) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) a[k] += __ldcg(P + (int64_t)(c + k) * NOUT + o);
+    }
+    for (int c = G8; c < (int)gridDim.x; ++c) a[0] += __ldcg(P + (int64_t)c * NOUT + o);
+    G[o] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
   }
   if (threadIdx.x == 0) *ticket = 0u;
 }
@@ -374,6 +452,22 @@ __global__ void k_gram_tc_pack(const double* __restrict__ Gfull, int nx, int px,
   }
 }
 
+template <int R>
+static void launch_gram_tc(const CUtensorMap& m0, const CUtensorMap& m1, const CUtensorMap& my, int64_t n, int grid,
+                           int64_t chunk, double* P, unsigned* tk, double* Gfull, int* err_dev, size_t smem,
+                           cudaStream_t s) {
+  static std::atomic<uint64_t> attr_set{0};  // one bit per device
+  int dev = 0;
+  ED_CUDA(cudaGetDevice(&dev));
+  const uint64_t bit = (uint64_t)1 << (dev & 63);
+  if (!(attr_set.load() & bit)) {
+    ED_CUDA(cudaFuncSetAttribute((const void*)k_gram_tc<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr_set.fetch_or(bit);
+  }
+  k_gram_tc<R><<<grid, kTcThreads, smem, s>>>(m0, m1, my, n, chunk, P, tk, Gfull, err_dev);
+  ED_CHECK_LAUNCH();
+}
+
 void gram_tc_f32(const float* X0, const float* X1, int nx, int px, const float* Y, int py, bool sym, int64_t vstride,
                  int64_t n, DevBuf<double>& P, DevBuf<unsigned>& tk, DevBuf<double>& Gfull, double* G, int* err_dev,
                  cudaStream_t s) {
@@ -383,25 +477,28 @@ void gram_tc_f32(const float* X0, const float* X1, int nx, int px, const float* 
   int dev = 0, sms = 152;
   ED_CUDA(cudaGetDevice(&dev));
   ED_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  // one CTA per SM, contiguous chunks of a multiple of 4 K-tiles (full stages but in the last CTA)
   const int64_t ntile = n / kTcK;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntile / 4, sms));
-  const int64_t chunk = (ntile + grid - 1) / grid * kTcK;
-  const int rows = 16 * nx + (sym ? 0 : 16);
-  if (P.n < (size_t)grid * rows * 16) P.alloc((size_t)grid * rows * 16);
-  if (Gfull.n < (size_t)rows * 16) Gfull.alloc((size_t)rows * 16);
+  const int64_t per = ((ntile + sms - 1) / sms + 3) / 4 * 4;
+  const int grid = (int)((ntile + per - 1) / per);
+  const int64_t chunk = per * kTcK;
+  const int R = sym ? 16 : 16 * (nx + 1);
+  const int nout = 16 * (sym ? 1 : nx) * 16;
+  if (P.n < (size_t)grid * nout) P.alloc((size_t)grid * nout);
+  if (Gfull.n < (size_t)nout) Gfull.alloc((size_t)nout);
   if (tk.n < 1) {
     tk.alloc(1);
     ED_CUDA(cudaMemsetAsync(tk.p, 0, sizeof(unsigned), s));
   }
   const size_t smem = sizeof(TcShared) + 1024;
-  static std::once_flag attr_once;
-  std::call_once(attr_once, [&] {
-    ED_CUDA(cudaFuncSetAttribute((const void*)k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  });
   {
     ProfScope ps_(K_BAND, s, (double)(nx * px + (sym ? 0 : py)) * n * 4.0);
-    k_gram_tc<<<grid, kTcThreads, smem, s>>>(m0, m1, my, nx, sym ? 1 : 0, n, chunk, P.p, tk.p, Gfull.p, err_dev);
-    ED_CHECK_LAUNCH();
+    if (R == 16)
+      launch_gram_tc<16>(m0, m1, my, n, grid, chunk, P.p, tk.p, Gfull.p, err_dev, smem, s);
+    else if (R == 32)
+      launch_gram_tc<32>(m0, m1, my, n, grid, chunk, P.p, tk.p, Gfull.p, err_dev, smem, s);
+    else
+      launch_gram_tc<48>(m0, m1, my, n, grid, chunk, P.p, tk.p, Gfull.p, err_dev, smem, s);
   }
   note_launch();
   k_gram_tc_pack<<<1, 256, 0, s>>>(Gfull.p, sym ? 1 : nx, px, sym ? px : py, G);
