@@ -416,6 +416,53 @@ ed_status ed_cdmft_fit(int n_sites, int n_bath, double* eps, double* theta, cons
 ed_status ed_gram_f32(const float* X, int nx, const float* Y, int ny, int64_t vstride, int64_t n, int method,
                       double* G_out);
 
+/* ---- cluster symmetries (Sec. 4.5) ----------------------------------------------------------
+ * The Hamiltonian of one irreducible representation of an Abelian symmetry group of the cluster,
+ * in the basis of symmetrized states, stored on the device (CSR), and its ground state.
+ * The group is generated by n_gen (1..5) commuting, independent involutions of the L orbitals:
+ * perm[j * L + i] is the image of orbital i under generator j (host array), applied to both
+ * spins; the irrep is named by the characters signs[j] = +1 or -1 of the generators (every
+ * irrep of such a group is one-dimensional with characters +-1).  The one-body matrix and U of
+ * the cluster must be invariant under every generator (else ED_ERR_INVALID).
+ * Basis: one representative per orbit of the binary states (b_up, b_dn) of the cluster's
+ * (N_up, N_dn) sector, the one with the smallest key b_up * 2^L + b_dn, kept unless its
+ * symmetrized state vanishes; keys ascending.  Matrix elements follow Eq. matrixElement for
+ * normalized states (sqrt(|S_r2| / |S_r1|) with S_r the stabilizer), real symmetric; entries of
+ * magnitude below 1e-13 after the cancellations of Sec. 4.5 are dropped.
+ * The handle borrows the cluster (which must outlive it) and its stream. */
+typedef struct ed_sym ed_sym;
+
+/* Builds the basis and the matrix of the irrep.  ED_ERR_INVALID (bad group, non-invariant H,
+ * more than 2^31 states), ED_ERR_OOM, ED_ERR_CUDA.  Synchronous. */
+ed_status ed_sym_create(ed_cluster* c, int n_gen, const int* perm, const int* signs, ed_sym** out);
+
+/* Dimension of the symmetrized sector and number of stored matrix entries (either may be NULL). */
+ed_status ed_sym_info(const ed_sym* s, int64_t* dim, int64_t* nnz);
+
+/* Host copies of the representatives' keys (dim uint64) and stabilizer sizes (dim bytes); either
+ * may be NULL.  Synchronous. */
+ed_status ed_sym_basis(const ed_sym* s, uint64_t* keys, uint8_t* stab);
+
+/* Host copies of the CSR matrix: rowptr (dim + 1 int64), col (nnz int32, ascending per row),
+ * val (nnz doubles); any may be NULL.  Synchronous. */
+ed_status ed_sym_matrix(const ed_sym* s, int64_t* rowptr, int32_t* col, double* val);
+
+/* y = H x in the symmetrized basis; x, y: device arrays of dim doubles on the cluster's device
+ * (y must not alias x).  Synchronous. */
+ed_status ed_sym_hpsi(ed_sym* s, const double* x, double* y);
+
+/* Lowest eigenvalue of the irrep's H by FP64 Lanczos (Sec. 4.2) with the cluster's tol, max_iter
+ * and seed; the ground vector is kept in the handle.  residual = |H w - E0 w| of the normalized
+ * vector; ED_WARN_NOT_CONVERGED when it stays above 1e-12 max(1, |E0|) (results still written).
+ * ED_ERR_INVALID for an empty irrep.  Any output pointer may be NULL.  Synchronous. */
+ed_status ed_sym_ground_state(ed_sym* s, double* E0, double* residual, int* iters);
+
+/* Host copy of the ground vector (dim doubles, normalized).  ED_ERR_STATE before
+ * ed_sym_ground_state. */
+ed_status ed_sym_ground_vector(const ed_sym* s, double* out);
+
+void ed_sym_destroy(ed_sym* s);
+
 /* ---- measurement of the library's own kernels (no counterpart in the paper) --------------- */
 
 /* Kernel families. */

@@ -1,0 +1,729 @@
+// Cluster symmetries (Sec. 4.5): the Hamiltonian restricted to one irreducible representation of
+// an Abelian symmetry group, in the basis of symmetrized states, and its ground state.
+//
+// The group is generated by commuting, independent involutions of the orbitals (mirrors, two-fold
+// rotations, half translations of a periodic cluster), so it has 2^k elements, each its own
+// inverse, and every irreducible representation has characters +-1; the caller names the irrep
+// by the signs it gives the generators.
+//
+// Basis (Sec. 4.5): the binary states (b_up, b_dn) of the sector are grouped into orbits; the
+// member with the smallest key b_up 2^L + b_dn represents its orbit, and its symmetrized state
+// sum_g chi_g g|r> is kept unless it vanishes (chi_g phi_g(r) = -1 for some g of the stabilizer).
+// phi_g(b) is the fermionic sign of moving the creation operators of b to their images: the
+// parity of the inversions of the permutation among the occupied orbitals of each spin.  One
+// thread tests one binary state; blocks own contiguous ranges of the sector and write their
+// representatives in order, so the list comes out sorted by key (the index function of Sec. 4.5
+// is then a binary search in it).
+//
+// Matrix (Eq. matrixElement for normalized states): applying every term of H to a representative
+// r gives binary states b_k with amplitudes h_k; with g_k b_k = r_k,
+//   <psi(r_k)| H |psi(r)> += h_k phi_{g_k}(b_k) chi_{g_k} sqrt(|S_{r_k}| / |S_r|).
+// The matrix is real symmetric, so the entries generated from r are stored as row r.  A row's
+// terms are merged in a thread's local buffer before they are stored, which carries out the
+// cancellations that Sec. 4.5 mentions; entries below 1e-13 in magnitude are dropped.  The matrix
+// is built twice, counting then filling (the paper stores H once the basis is symmetrized).
+//
+// Ground state: FP64 Lanczos (Sec. 4.2) on the stored matrix, scalars on the device, checked every
+// kSymCheck steps with the block tridiagonal solver; the ground vector is rebuilt by retracing the
+// recursion, then restarted from itself until the FP64 residual |H w - E w| reaches
+// 1e-12 max(1, |E|).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <numeric>
+#include <vector>
+
+#include "ed_common.cuh"
+
+namespace ed {
+
+constexpr int kSymMaxGen = 5;        // |G| <= 32
+constexpr int kSymMaxTerms = 2 * kMaxHops + 1;
+constexpr int kSymThreads = 256;
+constexpr int kSymChunk = 64 * kSymThreads;  // binary states per block of the basis kernels
+constexpr int kSymCheck = 10;
+constexpr int kSymRounds = 6;
+
+// Device copy of the group and the model terms that the kernels read.
+struct SymDev {
+  int L, ng;
+  int n_pairs;
+  uint8_t perm[1 << kSymMaxGen][kMaxOrb];     // orbital images of every element
+  uint32_t inv[1 << kSymMaxGen][kMaxOrb];     // inv[g][i]: orbitals j > i with perm(j) < perm(i)
+  int chi[1 << kSymMaxGen];                   // character of every element in the irrep
+  double hdiag[kMaxOrb];
+  double U[kMaxOrb];
+  int pa[kMaxPairs], pb[kMaxPairs];           // ordered hopping pairs (a <- b), h_ab != 0
+  double pv[kMaxPairs];
+};
+
+__device__ __forceinline__ uint32_t sym_move(const uint8_t* p, uint32_t b) {
+  uint32_t o = 0;
+  while (b) {
+    const int i = __ffs(b) - 1;
+    b &= b - 1u;
+    o |= 1u << p[i];
+  }
+  return o;
+}
+__device__ __forceinline__ int sym_parity(const uint32_t* inv, uint32_t b) {
+  int par = 0;
+  uint32_t x = b;
+  while (x) {
+    const int i = __ffs(x) - 1;
+    x &= x - 1u;
+    par ^= __popc(b & inv[i]) & 1;
+  }
+  return par;
+}
+__device__ __forceinline__ uint64_t sym_key(uint32_t bu, uint32_t bd, int L) { return ((uint64_t)bu << L) | bd; }
+
+// Is (bu, bd) the representative of a non-vanishing symmetrized state?  Also its stabilizer size.
+__device__ bool sym_is_rep(const SymDev& G, uint32_t bu, uint32_t bd, int* stab) {
+  const uint64_t k = sym_key(bu, bd, G.L);
+  int s = 0;
+  for (int g = 0; g < G.ng; ++g) {
+    const uint64_t gk = sym_key(sym_move(G.perm[g], bu), sym_move(G.perm[g], bd), G.L);
+    if (gk < k) return false;
+    if (gk == k) {
+      ++s;
+      const int ph = sym_parity(G.inv[g], bu) ^ sym_parity(G.inv[g], bd);
+      if (G.chi[g] * (ph ? -1 : 1) != 1) return false;
+    }
+  }
+  *stab = s;
+  return true;
+}
+
+// Representative key of the orbit of (bu, bd) and the factor phi_g(b) chi_g of the first element
+// (in element order) that reaches it.
+__device__ void sym_rep(const SymDev& G, uint32_t bu, uint32_t bd, uint64_t* rk, int* factor) {
+  uint64_t best = ~0ull;
+  int f = 1;
+  for (int g = 0; g < G.ng; ++g) {
+    const uint32_t gu = sym_move(G.perm[g], bu), gd = sym_move(G.perm[g], bd);
+    const uint64_t gk = sym_key(gu, gd, G.L);
+    if (gk < best) {
+      best = gk;
+      const int ph = sym_parity(G.inv[g], bu) ^ sym_parity(G.inv[g], bd);
+      f = G.chi[g] * (ph ? -1 : 1);
+    }
+  }
+  *rk = best;
+  *factor = f;
+}
+
+// ---- basis: count, then write, the representatives of every chunk of the sector in order
+__global__ void __launch_bounds__(kSymThreads) k_sym_basis(const SymDev* __restrict__ Gp, const uint32_t* __restrict__ Bu,
+                                                          const uint32_t* __restrict__ Bd, int64_t du, int64_t dd,
+                                                          int64_t* __restrict__ count, const int64_t* __restrict__ offset,
+                                                          uint64_t* __restrict__ keys, uint8_t* __restrict__ stab) {
+  __shared__ SymDev G;
+  __shared__ int s_warp[kSymThreads / 32];
+  __shared__ int64_t s_base;
+  for (int i = threadIdx.x; i < (int)(sizeof(SymDev) / 4); i += blockDim.x)
+    reinterpret_cast<int*>(&G)[i] = reinterpret_cast<const int*>(Gp)[i];
+  if (threadIdx.x == 0) s_base = offset ? offset[blockIdx.x] : 0;
+  __syncthreads();
+  const int64_t n = du * dd;
+  const int64_t c0 = (int64_t)blockIdx.x * kSymChunk;
+  const int64_t c1 = c0 + kSymChunk < n ? c0 + kSymChunk : n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t total = 0;
+  for (int64_t i0 = c0; i0 < c1; i0 += kSymThreads) {
+    const int64_t i = i0 + threadIdx.x;
+    int st = 0;
+    bool rep = false;
+    uint32_t bu = 0, bd = 0;
+    if (i < c1) {
+      const int64_t u = i / dd, d = i - u * dd;
+      bu = Bu[u];
+      bd = Bd[d];
+      rep = sym_is_rep(G, bu, bd, &st);
+    }
+    // ordered compaction: ranks within the warp, then across warps
+    const unsigned m = __ballot_sync(0xffffffffu, rep);
+    if (lane == 0) s_warp[warp] = __popc(m);
+    __syncthreads();
+    int before = 0, tot = 0;
+    for (int w = 0; w < kSymThreads / 32; ++w) {
+      before += w < warp ? s_warp[w] : 0;
+      tot += s_warp[w];
+    }
+    if (offset && rep) {
+      const int64_t o = s_base + total + before + __popc(m & ((1u << lane) - 1u));
+      keys[o] = sym_key(bu, bd, G.L);
+      stab[o] = (uint8_t)st;
+    }
+    total += tot;
+    __syncthreads();
+  }
+  if (!offset && threadIdx.x == 0) count[blockIdx.x] = total;
+}
+
+__device__ __forceinline__ int64_t sym_find(const uint64_t* __restrict__ keys, int64_t dim, uint64_t k) {
+  int64_t lo = 0, hi = dim;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (keys[mid] < k)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return (lo < dim && keys[lo] == k) ? lo : -1;
+}
+
+// The merged entries of row r (columns ascending); returns their number.
+__device__ int sym_row(const SymDev& G, const uint64_t* __restrict__ keys, const uint8_t* __restrict__ stab, int64_t dim,
+                       int64_t r, int32_t* col, double* val) {
+  const uint64_t k = keys[r];
+  const uint32_t bu = (uint32_t)(k >> G.L), bd = (uint32_t)(k & ((G.L == 32) ? 0xFFFFFFFFull : ((1ull << G.L) - 1ull)));
+  const double sr = (double)stab[r];
+  int n = 0;
+  double diag = 0.0;
+  for (int a = 0; a < G.L; ++a) {
+    diag += G.hdiag[a] * (double)(((bu >> a) & 1u) + ((bd >> a) & 1u));
+    if ((bu >> a) & (bd >> a) & 1u) diag += G.U[a];
+  }
+  col[n] = (int32_t)r;
+  val[n++] = diag;
+  for (int p = 0; p < G.n_pairs; ++p) {
+    const int a = G.pa[p], b = G.pb[p];
+    const uint32_t lo = (uint32_t)min(a, b), hi = (uint32_t)max(a, b);
+    const uint32_t between = (hi >= 32 ? 0xFFFFFFFFu : ((1u << hi) - 1u)) ^ ((1u << lo) - 1u) ^ (1u << lo);
+    for (int spin = 0; spin < 2; ++spin) {
+      const uint32_t bs = spin ? bd : bu;
+      if (!((bs >> b) & 1u) || ((bs >> a) & 1u)) continue;
+      const uint32_t nb = bs ^ (1u << a) ^ (1u << b);
+      const int jw = __popc(bs & between) & 1;
+      uint64_t rk;
+      int f;
+      sym_rep(G, spin ? bu : nb, spin ? nb : bd, &rk, &f);
+      const int64_t c = sym_find(keys, dim, rk);
+      if (c < 0 || n >= kSymMaxTerms) continue;
+      col[n] = (int32_t)c;
+      val[n++] = G.pv[p] * (jw ? -1.0 : 1.0) * (double)f * sqrt((double)stab[c] / sr);
+    }
+  }
+  // sort by column (insertion: rows hold a few dozen terms), merge, drop cancelled entries
+  for (int i = 1; i < n; ++i) {
+    const int32_t cc = col[i];
+    const double vv = val[i];
+    int j = i - 1;
+    while (j >= 0 && col[j] > cc) {
+      col[j + 1] = col[j];
+      val[j + 1] = val[j];
+      --j;
+    }
+    col[j + 1] = cc;
+    val[j + 1] = vv;
+  }
+  int m = 0;
+  for (int i = 0; i < n;) {
+    const int32_t cc = col[i];
+    double s = 0.0;
+    while (i < n && col[i] == cc) s += val[i++];
+    if (fabs(s) >= 1e-13) {
+      col[m] = cc;
+      val[m++] = s;
+    }
+  }
+  return m;
+}
+
+__global__ void __launch_bounds__(128) k_sym_rows(const SymDev* __restrict__ Gp, const uint64_t* __restrict__ keys,
+                                                  const uint8_t* __restrict__ stab, int64_t dim,
+                                                  int64_t* __restrict__ rowptr, int32_t* __restrict__ colo,
+                                                  double* __restrict__ valo, int fill) {
+  __shared__ SymDev G;
+  for (int i = threadIdx.x; i < (int)(sizeof(SymDev) / 4); i += blockDim.x)
+    reinterpret_cast<int*>(&G)[i] = reinterpret_cast<const int*>(Gp)[i];
+  __syncthreads();
+  int32_t col[kSymMaxTerms];
+  double val[kSymMaxTerms];
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < dim; r += (int64_t)gridDim.x * blockDim.x) {
+    const int m = sym_row(G, keys, stab, dim, r, col, val);
+    if (!fill) {
+      rowptr[r] = m;
+    } else {
+      const int64_t o = rowptr[r];
+      for (int i = 0; i < m; ++i) {
+        colo[o + i] = col[i];
+        valo[o + i] = val[i];
+      }
+    }
+  }
+}
+
+// ---- y = H x - beta x_prev (x_prev may be NULL), warp per row; per-block partial <x, y>
+__global__ void __launch_bounds__(kSymThreads) k_sym_spmv(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                                         const double* __restrict__ val, int64_t dim,
+                                                         const double* __restrict__ x, double* __restrict__ y,
+                                                         const double* __restrict__ xprev, const double* __restrict__ beta,
+                                                         double* __restrict__ partial) {
+  __shared__ double s_part[kSymThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double b = (xprev && beta) ? *beta : 0.0;
+  double dot = 0.0;
+  for (int64_t r = (int64_t)blockIdx.x * (kSymThreads / 32) + warp; r < dim; r += (int64_t)gridDim.x * (kSymThreads / 32)) {
+    double s = 0.0;
+    for (int64_t k = rowptr[r] + lane; k < rowptr[r + 1]; k += 32) s += val[k] * __ldg(x + col[k]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (xprev) s -= b * xprev[r];
+    if (lane == 0) {
+      y[r] = s;
+      dot += s * x[r];
+    }
+  }
+  if (lane == 0) s_part[warp] = dot;
+  __syncthreads();
+  if (threadIdx.x == 0 && partial) {
+    double t = 0.0;
+    for (int w = 0; w < kSymThreads / 32; ++w) t += s_part[w];
+    partial[blockIdx.x] = t;
+  }
+}
+
+// out = sum of partials in a fixed order (one block); mode 0: out = s, 1: out = sqrt(max(s, 0))
+__global__ void k_sym_finish(const double* __restrict__ partial, int n, double* __restrict__ out, int mode) {
+  __shared__ double sm[kSymThreads];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += partial[i];
+  sm[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = mode ? sqrt(fmax(sm[0], 0.0)) : sm[0];
+}
+
+// w -= a x (a = *alpha, or 0 when alpha is NULL); per-block partial |w|^2
+__global__ void __launch_bounds__(kSymThreads) k_sym_axpy_norm(double* __restrict__ w, const double* __restrict__ x,
+                                                              const double* __restrict__ alpha, int64_t dim,
+                                                              double* __restrict__ partial) {
+  __shared__ double sm[kSymThreads];
+  const double a = alpha ? *alpha : 0.0;
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = alpha ? w[i] - a * x[i] : w[i];
+    if (alpha) w[i] = v;
+    s += v * v;
+  }
+  sm[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if ((int)threadIdx.x < k) sm[threadIdx.x] += sm[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = sm[0];
+}
+
+// v = w / *norm (written over v); omega += coef * v when omega is given
+__global__ void k_sym_scale(double* __restrict__ v, const double* __restrict__ w, const double* __restrict__ norm, int64_t dim,
+                            double* __restrict__ omega, const double* __restrict__ coef) {
+  const double nb = *norm;
+  const double f = nb > 0.0 ? 1.0 / nb : 0.0;
+  const double cf = omega ? *coef : 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = w[i] * f;
+    v[i] = x;
+    if (omega) omega[i] += cf * x;
+  }
+}
+
+__device__ __forceinline__ uint64_t sym_splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__global__ void k_sym_start(double* __restrict__ v, int64_t dim, uint64_t seed) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim; i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = 2.0 * ((double)(sym_splitmix64(seed ^ (uint64_t)i) >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+}
+
+}  // namespace ed
+
+// ---------------------------------------------------------------- the handle
+struct ed_sym {
+  ed_cluster* c = nullptr;
+  int n_gen = 0;
+  std::vector<int> signs;
+  ed::DevBuf<ed::SymDev> G;
+  int64_t dim = 0, nnz = 0;
+  ed::DevBuf<uint64_t> keys;
+  ed::DevBuf<uint8_t> stab;
+  ed::DevBuf<int64_t> rowptr;
+  ed::DevBuf<int32_t> col;
+  ed::DevBuf<double> val;
+  ed::DevBuf<double> omega;  // ground state in the symmetrized basis
+  bool have_gs = false;
+  double E0 = 0.0, residual = 0.0;
+  int iters = 0;             // Lanczos steps of the last ground-state search
+};
+
+namespace ed {
+
+static int sym_grid(int64_t n, int per) {
+  const int64_t b = (n + per - 1) / per;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
+}
+
+static void sym_build(ed_sym& S, const int* perm, cudaStream_t s) {
+  ed_cluster& c = *S.c;
+  const ModelHost& m = c.model;
+  const int L = m.L, k = S.n_gen;
+  SymDev h;
+  std::memset(&h, 0, sizeof(h));
+  h.L = L;
+  h.ng = 1 << k;
+  for (int g = 0; g < h.ng; ++g) {
+    std::vector<int> p(L);
+    std::iota(p.begin(), p.end(), 0);
+    int chi = 1;
+    for (int j = 0; j < k; ++j)
+      if (g >> j & 1) {
+        for (int i = 0; i < L; ++i) p[i] = perm[j * L + p[i]];
+        chi *= S.signs[j];
+      }
+    for (int i = 0; i < L; ++i) {
+      h.perm[g][i] = (uint8_t)p[i];
+      uint32_t inv = 0;
+      for (int jj = i + 1; jj < L; ++jj)
+        if (p[jj] < p[i]) inv |= 1u << jj;
+      h.inv[g][i] = inv;
+    }
+    h.chi[g] = chi;
+  }
+  for (int a = 0; a < L; ++a) {
+    h.hdiag[a] = m.h[(size_t)a * L + a];
+    h.U[a] = m.U[a];
+  }
+  h.n_pairs = (int)m.pair_a.size();
+  for (int p = 0; p < h.n_pairs; ++p) {
+    h.pa[p] = m.pair_a[p];
+    h.pb[p] = m.pair_b[p];
+    h.pv[p] = m.h[(size_t)m.pair_a[p] * L + m.pair_b[p]];
+  }
+  S.G.alloc(1);
+  ED_CUDA(cudaMemcpyAsync(S.G.p, &h, sizeof(SymDev), cudaMemcpyHostToDevice, s));
+
+  SpinTables& tu = c.tables(c.desc.n_up);
+  SpinTables& td = c.tables(c.desc.n_dn);
+  const int64_t du = tu.dim, dd = td.dim, n = du * dd;
+  const int nblk = (int)((n + kSymChunk - 1) / kSymChunk);
+  DevBuf<int64_t> cnt(nblk), off(nblk);
+  k_sym_basis<<<nblk, kSymThreads, 0, s>>>(S.G.p, tu.basis.p, td.basis.p, du, dd, cnt.p, nullptr, nullptr, nullptr);
+  ED_CHECK_LAUNCH();
+  std::vector<int64_t> hc(nblk), ho(nblk);
+  ED_CUDA(cudaMemcpyAsync(hc.data(), cnt.p, nblk * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  ED_CUDA(cudaStreamSynchronize(s));
+  int64_t tot = 0;
+  for (int b = 0; b < nblk; ++b) ho[b] = tot, tot += hc[b];
+  if (tot >= ((int64_t)1 << 31)) throw Error(ED_ERR_INVALID, "symmetrized sector larger than 2^31 states");
+  S.dim = tot;
+  S.keys.alloc(std::max<int64_t>(tot, 1));
+  S.stab.alloc(std::max<int64_t>(tot, 1));
+  ED_CUDA(cudaMemcpyAsync(off.p, ho.data(), nblk * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  k_sym_basis<<<nblk, kSymThreads, 0, s>>>(S.G.p, tu.basis.p, td.basis.p, du, dd, nullptr, off.p, S.keys.p, S.stab.p);
+  ED_CHECK_LAUNCH();
+  S.rowptr.alloc(tot + 1);
+  if (tot == 0) {
+    ED_CUDA(cudaMemsetAsync(S.rowptr.p, 0, sizeof(int64_t), s));
+    S.nnz = 0;
+    return;
+  }
+  k_sym_rows<<<sym_grid(tot, 128), 128, 0, s>>>(S.G.p, S.keys.p, S.stab.p, tot, S.rowptr.p, nullptr, nullptr, 0);
+  ED_CHECK_LAUNCH();
+  std::vector<int64_t> rp(tot + 1);
+  ED_CUDA(cudaMemcpyAsync(rp.data(), S.rowptr.p, tot * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  ED_CUDA(cudaStreamSynchronize(s));
+  int64_t acc = 0;
+  for (int64_t r = 0; r < tot; ++r) {
+    const int64_t v = rp[r];
+    rp[r] = acc;
+    acc += v;
+  }
+  rp[tot] = acc;
+  S.nnz = acc;
+  ED_CUDA(cudaMemcpyAsync(S.rowptr.p, rp.data(), (tot + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  S.col.alloc(std::max<int64_t>(acc, 1));
+  S.val.alloc(std::max<int64_t>(acc, 1));
+  k_sym_rows<<<sym_grid(tot, 128), 128, 0, s>>>(S.G.p, S.keys.p, S.stab.p, tot, S.rowptr.p, S.col.p, S.val.p, 1);
+  ED_CHECK_LAUNCH();
+  ED_CUDA(cudaStreamSynchronize(s));
+}
+
+// y = H x in the symmetrized basis (device vectors of S.dim doubles)
+static void sym_spmv(ed_sym& S, const double* x, double* y, const double* xprev, const double* beta, double* partial,
+                     int nblk, cudaStream_t s) {
+  ProfScope ps_(K_HPSI, s, (double)S.nnz * 12.0 + (double)S.dim * 16.0);
+  k_sym_spmv<<<nblk, kSymThreads, 0, s>>>(S.rowptr.p, S.col.p, S.val.p, S.dim, x, y, xprev, beta, partial);
+  ED_CHECK_LAUNCH();
+}
+
+// FP64 Lanczos ground state of the symmetrized sector (see the header).
+static void sym_ground_state(ed_sym& S, double tol, int max_iter, uint64_t seed) {
+  cudaStream_t s = S.c->stream;
+  const int64_t dim = S.dim;
+  if (dim == 0) throw Error(ED_ERR_INVALID, "the irrep has no state in this sector");
+  const int M = std::max(2, (int)std::min<int64_t>(max_iter > 0 ? max_iter : 600, dim));
+  const int nb = sym_grid(dim, kSymThreads / 32 * 4), nv = sym_grid(dim, kSymThreads * 4);
+  const int np = std::max(nb, nv);
+  DevBuf<double> V0(dim), V1(dim), W(dim), start(dim), alpha(M + 1), beta(M + 2), evals(3), svec(M + 1), part(np);
+  S.omega.alloc(dim);
+  const double tol_ritz = std::max(tol, 1e-14);
+  ED_CUDA(cudaMemsetAsync(beta.p, 0, (M + 2) * sizeof(double), s));
+  k_sym_start<<<nv, kSymThreads, 0, s>>>(start.p, dim, seed);
+  ED_CHECK_LAUNCH();
+  double host[3] = {0, 0, 0};
+  std::vector<double> hb(M + 2);
+  S.have_gs = false;
+  S.iters = 0;
+  for (int round = 0; round < kSymRounds; ++round) {
+    // normalize the start vector into V0
+    k_sym_axpy_norm<<<nv, kSymThreads, 0, s>>>(start.p, nullptr, nullptr, dim, part.p);
+    k_sym_finish<<<1, kSymThreads, 0, s>>>(part.p, nv, beta.p, 1);
+    k_sym_scale<<<nv, kSymThreads, 0, s>>>(V0.p, start.p, beta.p, dim, nullptr, nullptr);
+    ED_CHECK_LAUNCH();
+    ED_CUDA(cudaMemsetAsync(beta.p, 0, sizeof(double), s));
+    int m = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+      double* v = V0.p;
+      double* vp = V1.p;
+      if (pass == 1) {
+        k_sym_axpy_norm<<<nv, kSymThreads, 0, s>>>(start.p, nullptr, nullptr, dim, part.p);
+        k_sym_finish<<<1, kSymThreads, 0, s>>>(part.p, nv, W.p, 1);
+        ED_CUDA(cudaMemsetAsync(S.omega.p, 0, dim * sizeof(double), s));
+        k_sym_scale<<<nv, kSymThreads, 0, s>>>(V0.p, start.p, W.p, dim, S.omega.p, svec.p);
+        ED_CHECK_LAUNCH();
+      }
+      ED_CUDA(cudaMemsetAsync(vp, 0, dim * sizeof(double), s));
+      const int nmax = pass == 0 ? M : m - 1;
+      for (int n = 0; n < nmax; ++n) {
+        // W = H v - b_n v_prev, alpha_n = <v, W>; W -= alpha_n v, b_{n+1} = |W|; v_prev = W / b_{n+1}
+        sym_spmv(S, v, W.p, vp, beta.p + n, part.p, nb, s);
+        k_sym_finish<<<1, kSymThreads, 0, s>>>(part.p, nb, alpha.p + n, 0);
+        k_sym_axpy_norm<<<nv, kSymThreads, 0, s>>>(W.p, v, alpha.p + n, dim, part.p);
+        k_sym_finish<<<1, kSymThreads, 0, s>>>(part.p, nv, beta.p + n + 1, 1);
+        k_sym_scale<<<nv, kSymThreads, 0, s>>>(vp, W.p, beta.p + n + 1, dim, pass == 1 ? S.omega.p : nullptr, svec.p + n + 1);
+        ED_CHECK_LAUNCH();
+        std::swap(v, vp);
+        if (pass == 0 && ((n + 1) % kSymCheck == 0 || n + 1 == M)) {
+          ED_CUDA(cudaMemcpyAsync(hb.data(), beta.p, (n + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
+          ED_CUDA(cudaStreamSynchronize(s));
+          int levels = n + 1;
+          bool brk = false;
+          for (int j = 1; j <= n + 1; ++j)
+            if (!(hb[j] > 1e-12)) {
+              levels = j;
+              brk = true;
+              break;
+            }
+          launch_tridiag_lowest(alpha.p, beta.p, levels, evals.p, svec.p, s);
+          ED_CUDA(cudaMemcpyAsync(host, evals.p, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+          ED_CUDA(cudaStreamSynchronize(s));
+          m = levels;
+          if (brk || host[2] < tol_ritz * std::max(1.0, std::fabs(host[0]))) break;
+        }
+      }
+    }
+    S.iters += m;
+    // residual of the rebuilt vector: normalize, E = <w, H w>, r = |H w - E w|
+    k_sym_axpy_norm<<<nv, kSymThreads, 0, s>>>(S.omega.p, nullptr, nullptr, dim, part.p);
+    k_sym_finish<<<1, kSymThreads, 0, s>>>(part.p, nv, W.p + 0, 1);
+    k_sym_scale<<<nv, kSymThreads, 0, s>>>(start.p, S.omega.p, W.p, dim, nullptr, nullptr);
+    ED_CHECK_LAUNCH();
+    ED_CUDA(cudaMemcpyAsync(S.omega.p, start.p, dim * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    sym_spmv(S, S.omega.p, W.p, nullptr, nullptr, part.p, nb, s);
+    k_sym_finish<<<1, kSymThreads, 0, s>>>(part.p, nb, evals.p, 0);
+    k_sym_axpy_norm<<<nv, kSymThreads, 0, s>>>(W.p, S.omega.p, evals.p, dim, part.p);
+    k_sym_finish<<<1, kSymThreads, 0, s>>>(part.p, nv, evals.p + 1, 1);
+    ED_CHECK_LAUNCH();
+    ED_CUDA(cudaMemcpyAsync(host, evals.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    ED_CUDA(cudaStreamSynchronize(s));
+    S.E0 = host[0];
+    S.residual = host[1];
+    if (S.residual <= 1e-12 * std::max(1.0, std::fabs(S.E0))) {
+      S.have_gs = true;
+      return;
+    }
+    // restart from the rebuilt vector (already normalized in `start`)
+    ED_CUDA(cudaMemsetAsync(beta.p, 0, (M + 2) * sizeof(double), s));
+  }
+}
+
+static void sym_validate(const ed_cluster* c, int n_gen, const int* perm, const int* signs) {
+  if (!c) throw Error(ED_ERR_INVALID, "cluster is NULL");
+  if (n_gen < 1 || n_gen > kSymMaxGen) throw Error(ED_ERR_INVALID, "need 1 to 5 generators");
+  if (!perm || !signs) throw Error(ED_ERR_INVALID, "perm and signs must not be NULL");
+  const ModelHost& m = c->model;
+  const int L = m.L;
+  for (int j = 0; j < n_gen; ++j) {
+    if (signs[j] != 1 && signs[j] != -1) throw Error(ED_ERR_INVALID, "irrep signs must be +1 or -1");
+    std::vector<int> seen(L, 0);
+    for (int i = 0; i < L; ++i) {
+      const int pi = perm[j * L + i];
+      if (pi < 0 || pi >= L || seen[pi]++) throw Error(ED_ERR_INVALID, "a generator is not a permutation of the orbitals");
+    }
+    for (int i = 0; i < L; ++i)
+      if (perm[j * L + perm[j * L + i]] != i) throw Error(ED_ERR_INVALID, "a generator is not an involution");
+  }
+  for (int j = 0; j < n_gen; ++j)
+    for (int k = j + 1; k < n_gen; ++k)
+      for (int i = 0; i < L; ++i)
+        if (perm[j * L + perm[k * L + i]] != perm[k * L + perm[j * L + i]])
+          throw Error(ED_ERR_INVALID, "generators do not commute");
+  // independence: the 2^n_gen products are distinct
+  std::vector<std::vector<int>> els;
+  for (int g = 0; g < (1 << n_gen); ++g) {
+    std::vector<int> p(L);
+    std::iota(p.begin(), p.end(), 0);
+    for (int j = 0; j < n_gen; ++j)
+      if (g >> j & 1)
+        for (int i = 0; i < L; ++i) p[i] = perm[j * L + p[i]];
+    for (auto& q : els)
+      if (q == p) throw Error(ED_ERR_INVALID, "generators are not independent");
+    els.push_back(p);
+  }
+  double scale = 0.0;
+  for (double v : m.h) scale = std::max(scale, std::fabs(v));
+  for (int j = 0; j < n_gen; ++j)
+    for (int a = 0; a < L; ++a) {
+      const int pa = perm[j * L + a];
+      if (std::fabs(m.U[pa] - m.U[a]) > 1e-12 * std::max(1.0, std::fabs(m.U[a])))
+        throw Error(ED_ERR_INVALID, "the interaction is not invariant under a generator");
+      for (int b = 0; b < L; ++b) {
+        const int pb = perm[j * L + b];
+        if (std::fabs(m.h[(size_t)pa * L + pb] - m.h[(size_t)a * L + b]) > 1e-12 * std::max(1.0, scale))
+          throw Error(ED_ERR_INVALID, "the one-body matrix is not invariant under a generator");
+      }
+    }
+}
+
+}  // namespace ed
+
+using namespace ed;
+
+template <typename F>
+static ed_status sym_guard(F&& f) {
+  try {
+    return f();
+  } catch (const Error& e) {
+    set_last_error(e.what());
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    set_last_error("host allocation failed");
+    return ED_ERR_OOM;
+  } catch (const std::exception& e) {
+    set_last_error(e.what());
+    return ED_ERR_INVALID;
+  }
+}
+
+static void sym_require_device(const ed_cluster* c) {
+  int dev = -1;
+  ED_CUDA(cudaGetDevice(&dev));
+  if (dev != c->device) throw Error(ED_ERR_INVALID, "the current device is not the cluster's device");
+}
+
+extern "C" {
+
+ed_status ed_sym_create(ed_cluster* c, int n_gen, const int* perm, const int* signs, ed_sym** out) {
+  return sym_guard([&]() -> ed_status {
+    if (!out) throw Error(ED_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    sym_validate(c, n_gen, perm, signs);
+    sym_require_device(c);
+    auto S = std::make_unique<ed_sym>();
+    S->c = c;
+    S->n_gen = n_gen;
+    S->signs.assign(signs, signs + n_gen);
+    AllocStreamScope as_(c->stream);
+    sym_build(*S, perm, c->stream);
+    *out = S.release();
+    return ED_OK;
+  });
+}
+
+ed_status ed_sym_info(const ed_sym* S, int64_t* dim, int64_t* nnz) {
+  return sym_guard([&]() -> ed_status {
+    if (!S) throw Error(ED_ERR_INVALID, "handle is NULL");
+    if (dim) *dim = S->dim;
+    if (nnz) *nnz = S->nnz;
+    return ED_OK;
+  });
+}
+
+ed_status ed_sym_basis(const ed_sym* S, uint64_t* keys, uint8_t* stab) {
+  return sym_guard([&]() -> ed_status {
+    if (!S) throw Error(ED_ERR_INVALID, "handle is NULL");
+    sym_require_device(S->c);
+    cudaStream_t s = S->c->stream;
+    if (keys && S->dim) ED_CUDA(cudaMemcpyAsync(keys, S->keys.p, S->dim * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    if (stab && S->dim) ED_CUDA(cudaMemcpyAsync(stab, S->stab.p, S->dim, cudaMemcpyDeviceToHost, s));
+    ED_CUDA(cudaStreamSynchronize(s));
+    return ED_OK;
+  });
+}
+
+ed_status ed_sym_matrix(const ed_sym* S, int64_t* rowptr, int32_t* col, double* val) {
+  return sym_guard([&]() -> ed_status {
+    if (!S) throw Error(ED_ERR_INVALID, "handle is NULL");
+    sym_require_device(S->c);
+    cudaStream_t s = S->c->stream;
+    if (rowptr) ED_CUDA(cudaMemcpyAsync(rowptr, S->rowptr.p, (S->dim + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    if (col && S->nnz) ED_CUDA(cudaMemcpyAsync(col, S->col.p, S->nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    if (val && S->nnz) ED_CUDA(cudaMemcpyAsync(val, S->val.p, S->nnz * sizeof(double), cudaMemcpyDeviceToHost, s));
+    ED_CUDA(cudaStreamSynchronize(s));
+    return ED_OK;
+  });
+}
+
+ed_status ed_sym_hpsi(ed_sym* S, const double* x, double* y) {
+  return sym_guard([&]() -> ed_status {
+    if (!S || !x || !y) throw Error(ED_ERR_INVALID, "handle and vectors must not be NULL");
+    sym_require_device(S->c);
+    if (S->dim == 0) return ED_OK;
+    sym_spmv(*S, x, y, nullptr, nullptr, nullptr, sym_grid(S->dim, kSymThreads / 32 * 4), S->c->stream);
+    ED_CUDA(cudaStreamSynchronize(S->c->stream));
+    return ED_OK;
+  });
+}
+
+ed_status ed_sym_ground_state(ed_sym* S, double* E0, double* residual, int* iters) {
+  return sym_guard([&]() -> ed_status {
+    if (!S) throw Error(ED_ERR_INVALID, "handle is NULL");
+    sym_require_device(S->c);
+    AllocStreamScope as_(S->c->stream);
+    sym_ground_state(*S, S->c->desc.tol, S->c->desc.max_iter, S->c->desc.seed);
+    if (E0) *E0 = S->E0;
+    if (residual) *residual = S->residual;
+    if (iters) *iters = S->iters;
+    return S->have_gs ? ED_OK : ED_WARN_NOT_CONVERGED;
+  });
+}
+
+ed_status ed_sym_ground_vector(const ed_sym* S, double* out) {
+  return sym_guard([&]() -> ed_status {
+    if (!S || !out) throw Error(ED_ERR_INVALID, "handle and out must not be NULL");
+    if (S->omega.n == 0) throw Error(ED_ERR_STATE, "no ground state yet");
+    sym_require_device(S->c);
+    ED_CUDA(cudaMemcpyAsync(out, S->omega.p, S->dim * sizeof(double), cudaMemcpyDeviceToHost, S->c->stream));
+    ED_CUDA(cudaStreamSynchronize(S->c->stream));
+    return ED_OK;
+  });
+}
+
+void ed_sym_destroy(ed_sym* S) {
+  if (!S) return;
+  try {
+    cudaStreamSynchronize(S->c->stream);
+    delete S;
+  } catch (...) {
+  }
+}
+
+}  // extern "C"

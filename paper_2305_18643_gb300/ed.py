@@ -78,6 +78,7 @@ def lib():
         }
         sig.update(_server_sigs)
         sig.update(_lattice_sigs)
+        sig.update(_sym_sigs)
         for name, (res, args) in sig.items():
             f = getattr(L, name)
             f.restype = res
@@ -611,3 +612,75 @@ def ed_cdmft_fit(theta, eps, z, weights, A, theta_free=None, gtol=0.0, max_iter=
                               A.view(np.float64).ctypes.data_as(_dp), float(gtol), int(max_iter), C.byref(d),
                               C.byref(it)))
     return theta, eps, d.value, it.value
+
+# ---- cluster symmetries (Sec. 4.5) -------------------------------------------------------------
+_ip = C.POINTER(C.c_int)
+_sym_sigs = {
+    "ed_sym_create": (C.c_int, [C.c_void_p, C.c_int, _ip, _ip, C.POINTER(C.c_void_p)]),
+    "ed_sym_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "ed_sym_basis": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ed_sym_matrix": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ed_sym_hpsi": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ed_sym_ground_state": (C.c_int, [C.c_void_p, _dp, _dp, C.POINTER(C.c_int)]),
+    "ed_sym_ground_vector": (C.c_int, [C.c_void_p, _dp]),
+    "ed_sym_destroy": (None, [C.c_void_p]),
+}
+
+
+def ed_sym_create(h, perms, signs):
+    """Handle of one irrep (generator signs `signs`, +-1) of the group generated by the orbital
+    involutions `perms` (n_gen x L images), for the cluster h's sector."""
+    P = np.ascontiguousarray(np.asarray(perms, dtype=np.int32).reshape(len(signs), -1))
+    sg = np.ascontiguousarray(np.asarray(signs, dtype=np.int32))
+    out = C.c_void_p()
+    _check(lib().ed_sym_create(h, int(len(sg)), P.ctypes.data_as(_ip), sg.ctypes.data_as(_ip), C.byref(out)))
+    return out
+
+
+def ed_sym_info(s):
+    """(dimension, stored entries) of the symmetrized sector."""
+    d, z = C.c_int64(), C.c_int64()
+    _check(lib().ed_sym_info(s, C.byref(d), C.byref(z)))
+    return d.value, z.value
+
+
+def ed_sym_basis(s):
+    """(keys b_up 2^L + b_dn, stabilizer sizes) of the representatives, ascending keys."""
+    d, _ = ed_sym_info(s)
+    keys = np.zeros(d, dtype=np.uint64)
+    st = np.zeros(d, dtype=np.uint8)
+    _check(lib().ed_sym_basis(s, keys.ctypes.data, st.ctypes.data))
+    return keys, st
+
+
+def ed_sym_matrix(s):
+    """(rowptr, col, val) of the stored matrix (host copies)."""
+    d, z = ed_sym_info(s)
+    rp = np.zeros(d + 1, dtype=np.int64)
+    col = np.zeros(z, dtype=np.int32)
+    val = np.zeros(z, dtype=np.float64)
+    _check(lib().ed_sym_matrix(s, rp.ctypes.data, col.ctypes.data, val.ctypes.data))
+    return rp, col, val
+
+
+def ed_sym_hpsi(s, x_ptr, y_ptr):
+    """y = H x in the symmetrized basis (device pointers)."""
+    _check(lib().ed_sym_hpsi(s, C.c_void_p(x_ptr), C.c_void_p(y_ptr)))
+
+
+def ed_sym_ground_state(s):
+    """(E0, residual, iterations, status)."""
+    E, r, it = C.c_double(), C.c_double(), C.c_int()
+    st = _check(lib().ed_sym_ground_state(s, C.byref(E), C.byref(r), C.byref(it)))
+    return E.value, r.value, it.value, st
+
+
+def ed_sym_ground_vector(s):
+    d, _ = ed_sym_info(s)
+    v = np.zeros(d)
+    _check(lib().ed_sym_ground_vector(s, v.ctypes.data_as(_dp)))
+    return v
+
+
+def ed_sym_destroy(s):
+    lib().ed_sym_destroy(s)

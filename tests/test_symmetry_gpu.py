@@ -1,0 +1,214 @@
+"""Symmetrized sectors (Sec. 4.5) on the GPU against the symmetry oracle: the representatives and
+their stabilizers bit for bit, the stored matrix entry by entry, H.psi, and the ground energy of
+every irrep; Table 1's counts straight from the device matrix; invalid groups are refused."""
+
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle.symmetry_oracle as S
+from oracle.ed_oracle import Model, ground_state, sector_hamiltonian
+from paper_2305_18643_gb300 import build, ed
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def libed():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build()
+    return ed.lib()
+
+
+def rect(W, H, t=-1.0):
+    L = W * H
+    h = np.zeros((L, L))
+    for y in range(H):
+        for x in range(W):
+            s = x + W * y
+            if x + 1 < W:
+                h[s, s + 1] = h[s + 1, s] = t
+            if y + 1 < H:
+                h[s, s + W] = h[s + W, s] = t
+    mx = [(W - 1 - s % W) + W * (s // W) for s in range(L)]
+    my = [s % W + W * (H - 1 - s // W) for s in range(L)]
+    return h, mx, my
+
+
+def _cluster(t, U, mu, nu, nd, eps=None, theta=None, seed=11):
+    t = np.asarray(t, dtype=np.float64)
+    ns = t.shape[0]
+    c = {"t": t, "U": np.full(ns, float(U)), "mu": float(mu), "n_up": nu, "n_dn": nd}
+    if eps is not None:
+        c["eps"] = np.asarray(eps, dtype=np.float64)
+        c["theta"] = np.asarray(theta, dtype=np.float64)
+    return ed.ed_cluster_create(c, precision=ed.ED_FP64, seed=seed, tol=1e-13, max_iter=600), \
+        Model(t, U, mu, eps, theta)
+
+
+def _cases():
+    out = []
+    h, mx, my = rect(3, 2)
+    out.append(("2x3 C2v U=4", (h, 4.0, 2.0, 3, 3), [mx, my]))
+    out.append(("2x3 mirror N_up != N_dn", (h, 3.0, 1.0, 2, 3), [mx]))
+    L = 6
+    t = np.zeros((L, L))
+    for i in range(L - 1):
+        t[i, i + 1] = t[i + 1, i] = -1.0
+    for i in range(L - 2):
+        t[i, i + 2] = t[i + 2, i] = 0.3
+    out.append(("chain6 inversion", (t, 5.0, 2.5, 3, 2), [[L - 1 - i for i in range(L)]]))
+    t = np.zeros((4, 4))
+    for i in range(4):
+        t[i, (i + 1) % 4] = t[(i + 1) % 4, i] = -1.0
+    out.append(("ring4 T2 x I", (t, 6.0, 3.0, 2, 2), [[(i + 2) % 4 for i in range(4)], [(-i) % 4 for i in range(4)]]))
+    h, mx, my = rect(4, 2)
+    h[0, 5] = h[5, 0] = h[1, 4] = h[4, 1] = h[1, 6] = h[6, 1] = h[2, 5] = h[5, 2] = 0.3
+    h[2, 7] = h[7, 2] = h[3, 6] = h[6, 3] = 0.3
+    out.append(("2x4 t' C2v", (h, 8.0, 4.0, 4, 4), [mx, my]))
+    return out
+
+
+def _bath_case():
+    h, mx, my = rect(2, 2)
+    h[0, 3] = h[3, 0] = h[1, 2] = h[2, 1] = 0.3
+    eps = np.full(4, -1.0)
+    theta = 0.5 * np.eye(4)
+    return (h, 8.0, 4.0, 3, 3, eps, theta), [mx + [4 + v for v in mx], my + [4 + v for v in my]]
+
+
+def _device_csr(s):
+    d, z = ed.ed_sym_info(s)
+    rp, col, val = ed.ed_sym_matrix(s)
+    return sp.csr_matrix((val, col, rp), shape=(d, d))
+
+
+def _check_irrep(hc, m, L, nu, nd, gens, ir):
+    s = ed.ed_sym_create(hc, np.array(gens), ir)
+    try:
+        bu, bd, st = S.symmetric_basis(L, nu, nd, gens, ir)
+        keys, stab = ed.ed_sym_basis(s)
+        okey = (bu.astype(np.uint64) << np.uint64(L)) | bd.astype(np.uint64)
+        assert np.array_equal(keys, okey)
+        assert np.array_equal(stab.astype(np.int64), st)
+        if len(keys) == 0:
+            return None
+        Ho, _ = S.symmetric_hamiltonian(m, nu, nd, gens, ir)
+        Hg = _device_csr(s)
+        assert Hg.nnz == Ho.nnz
+        assert np.array_equal(Hg.indptr, Ho.indptr) and np.array_equal(Hg.indices, Ho.indices)
+        assert np.max(np.abs(Hg.data - Ho.data)) <= 1e-14 * max(1.0, np.max(np.abs(Ho.data)))
+        # H.psi through the C ABI on device vectors
+        x = np.random.default_rng(len(keys)).standard_normal(len(keys))
+        xd = torch.tensor(x, device="cuda")
+        yd = torch.empty_like(xd)
+        ed.ed_sym_hpsi(s, xd.data_ptr(), yd.data_ptr())
+        y = yd.cpu().numpy()
+        assert np.max(np.abs(y - Ho @ x)) <= 1e-13 * max(1.0, np.max(np.abs(Ho @ x)))
+        E, res, it, st_ = ed.ed_sym_ground_state(s)
+        Eo = S.irrep_ground_energy(m, nu, nd, gens, ir)
+        assert abs(E - Eo) <= 1e-10 * max(1.0, abs(Eo)), (E, Eo)
+        assert res <= 1e-12 * max(1.0, abs(E))
+        w = ed.ed_sym_ground_vector(s)
+        assert abs(np.linalg.norm(w) - 1.0) < 1e-12
+        assert np.linalg.norm(Ho @ w - E * w) <= 1e-11 * max(1.0, abs(E))
+        return E
+    finally:
+        ed.ed_sym_destroy(s)
+
+
+@pytest.mark.parametrize("case", _cases(), ids=lambda c: c[0])
+def test_symmetrized_sector_matches_oracle(case):
+    name, (t, U, mu, nu, nd), gens = case
+    hc, m = _cluster(t, U, mu, nu, nd)
+    try:
+        Es = [e for ir in S.all_irreps(len(gens)) if (e := _check_irrep(hc, m, m.L, nu, nd, gens, ir)) is not None]
+        # the lowest irrep energy is the sector's ground energy
+        E0, _, _ = ground_state(sector_hamiltonian(m, nu, nd))
+        assert abs(min(Es) - E0) <= 1e-10 * max(1.0, abs(E0))
+    finally:
+        ed.ed_cluster_destroy(hc)
+
+
+def test_symmetrized_sector_with_bath_orbitals():
+    (t, U, mu, nu, nd, eps, theta), gens = _bath_case()
+    hc, m = _cluster(t, U, mu, nu, nd, eps, theta)
+    try:
+        for ir in S.all_irreps(2):
+            _check_irrep(hc, m, m.L, nu, nd, gens, ir)
+    finally:
+        ed.ed_cluster_destroy(hc)
+
+
+def test_table1_counts_from_the_device_matrix():
+    """Table 1 (Sec. 4.5): dimensions and value counts of the nearest-neighbour hopping operator on
+    the half-filled 3x4 cluster, read from the matrices the GPU builds."""
+    ref = json.load(open(os.path.join(HERE, "golden", "table1_c2v_3x4.json")))
+    h, mx, my = rect(4, 3)
+    hc, m = _cluster(h, 0.0, 0.0, 6, 6)
+    vals = {"-2": -2.0, "-sqrt2": -np.sqrt(2.0), "-1": -1.0, "1": 1.0, "sqrt2": np.sqrt(2.0), "2": 2.0}
+    try:
+        for label, signs in ref["irreps_by_generator_signs"].items():
+            s = ed.ed_sym_create(hc, np.array([mx, my]), signs)
+            try:
+                d, z = ed.ed_sym_info(s)
+                assert d == ref["dim"][label]
+                _, _, v = ed.ed_sym_matrix(s)
+                for name, x in vals.items():
+                    assert int(np.sum(np.abs(v - x) < 1e-12)) == ref["counts"][label][name], (label, name)
+                assert z == sum(ref["counts"][label].values())
+            finally:
+                ed.ed_sym_destroy(s)
+    finally:
+        ed.ed_cluster_destroy(hc)
+
+
+def test_3x4_ground_energy_in_a1_matches_the_full_sector():
+    """Interacting half-filled 3x4 cluster (U = 4): the A1 ground energy from the 213,840-state
+    symmetrized sector against ARPACK on the unsymmetrized 853,776-state sector (oracle), and the
+    device matrix against the oracle's."""
+    h, mx, my = rect(4, 3)
+    hc, m = _cluster(h, 4.0, 2.0, 6, 6)
+    try:
+        s = ed.ed_sym_create(hc, np.array([mx, my]), [1, 1])
+        try:
+            Ho, _ = S.symmetric_hamiltonian(m, 6, 6, [mx, my], (1, 1))
+            Hg = _device_csr(s)
+            assert np.array_equal(Hg.indices, Ho.indices)
+            assert np.max(np.abs(Hg.data - Ho.data)) <= 1e-13
+            E, res, it, st = ed.ed_sym_ground_state(s)
+            E0, _, _ = ground_state(sector_hamiltonian(m, 6, 6))
+            Ea1 = S.irrep_ground_energy(m, 6, 6, [mx, my], (1, 1))
+            assert abs(E - Ea1) <= 1e-10 * abs(Ea1)
+            assert E >= E0 - 1e-10 * abs(E0)
+            assert res <= 1e-12 * max(1.0, abs(E))
+        finally:
+            ed.ed_sym_destroy(s)
+    finally:
+        ed.ed_cluster_destroy(hc)
+
+
+def test_invalid_groups_are_refused():
+    h, mx, my = rect(3, 2)
+    hc, m = _cluster(h, 4.0, 2.0, 3, 3)
+    L = 6
+    try:
+        bad = [
+            ([[1, 2, 0, 4, 5, 3]], [1]),                 # not an involution
+            ([[1, 0, 2, 3, 4, 5]], [1]),                 # does not leave h invariant
+            ([mx, mx], [1, 1]),                          # dependent generators
+            ([mx], [2]),                                 # not a sign
+            ([[0, 0, 2, 3, 4, 5]], [1]),                 # not a permutation
+        ]
+        for perms, signs in bad:
+            with pytest.raises(ed.EDError) as e:
+                ed.ed_sym_create(hc, np.array(perms), signs)
+            assert e.value.status == ed.ED_ERR_INVALID
+    finally:
+        ed.ed_cluster_destroy(hc)
