@@ -137,11 +137,11 @@ ed_status ed_green(ed_cluster* c, const double* omega, int n_freq, double eta, i
  *                       of E_0 (a degenerate ground manifold), so G does not depend on the basis
  *                       chosen inside it.  The paper's temperature option: low, since only a few
  *                       states are kept.
- *  ED_OPT_TENSOR_GRAM   1 [default] or 0: with FP32 vectors, the Gram matrices of the band Lanczos
- *                       block recurrence (projections on the previous two blocks, W^T W) run on the
- *                       tensor cores (TMA tile loads, tcgen05 MMA with a 3xTF32 split, FP64 sums
- *                       beyond every 512 elements) where the layout allows it; 0 keeps the
- *                       CUDA-core FP32 kernel.  A bounded wait of that kernel that gives up makes
+ *  ED_OPT_TENSOR_GRAM   1 [default] or 0: with FP32 vectors, the Gram matrix W^T W of the band
+ *                       Lanczos orthogonalization runs on the tensor cores (TMA tile loads,
+ *                       tcgen05 MMA on TF32 head/tail splits, compensated sums per stage) where
+ *                       the layout allows it; the projections on the previous blocks stay on the
+ *                       CUDA cores (faster there); 0 keeps every Gram on the CUDA-core kernel.  A bounded wait of that kernel that gives up makes
  *                       ed_green return ED_ERR_TIMEOUT.
  * ED_ERR_INVALID for an unknown option or a non-finite value. */
 enum { ED_OPT_BAND_MAX_DIM = 1, ED_OPT_CF_MAX_STEPS = 2, ED_OPT_GF_TOL = 3, ED_OPT_TWO_PASS_MIN_BYTES = 4,

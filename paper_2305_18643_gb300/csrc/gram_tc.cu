@@ -7,8 +7,9 @@
 // swizzle).  A K-tile is 32 consecutive elements of the R vector rows involved (R = 16 for W^T W,
 // 32 for one X block and Y, 48 for two X blocks and Y); KT = 64 / R K-tiles are stacked in rows
 // [0, 64) of the stage (one for R = 48), so a stage always carries ~8 KB of vector data.
-// TMA loads them; warps 4-7 split every value x into a TF32 head h = rn(x) (in place) and a TF32
-// tail l = rn(x - h), written 64 rows further down.  One MMA per 8-element step then multiplies
+// TMA loads them; an epilogue warp group splits every value x into a TF32 head h = rn(x) (in
+// place) and a TF32 tail l = rn(x - h), written 64 rows further down (two groups of four warps
+// take alternate stages, so one splits while the other reads TMEM).  One MMA per 8-element step then multiplies
 // the whole tile (all heads and tails: M = 128) by the Y rows of every stacked K-tile, heads and
 // tails (N = 128, 112 or 80 rows of the same tile), so a single kind::tf32 MMA yields the four
 // products h h, h l, l h and l l of every (i, j) pair, each in its own TMEM cell: no accumulator
@@ -16,7 +17,8 @@
 //
 // Accuracy: x = h + l + r with |r| <= 2^-22 |x| (round-to-nearest, unbiased), products of TF32
 // values are exact in FP32, and each TMEM cell accumulates the 4 MMAs of one stage only; every
-// stage is then read (tcgen05.ld) and added to a Kahan-compensated FP32 sum (the head products)
+// stage is then read (tcgen05.ld; four D buffers, so the MMAs of a stage never wait for the
+// previous stage's read) and added to a Kahan-compensated FP32 sum (the head products)
 // or a plain FP32 sum moved to FP64 every 64 stages (the tail products).  CTAs take contiguous
 // element chunks; a CTA reduces its lanes in a fixed order, and the last CTA (a ticket) adds the
 // per-CTA partials in CTA order, so results are deterministic.
@@ -37,17 +39,18 @@ namespace ed {
 
 constexpr int kTcK = 32;         // elements per K-tile (a 128-byte row)
 constexpr int kTcStages = 8;
-constexpr int kTcThreads = 256;  // warp 0 TMA, warp 1 MMA + TMEM allocation, warps 4-7 split + flush
-constexpr int kTcTmemCols = 256; // two D buffers of up to 128 columns
+constexpr int kTcThreads = 384;  // warp 0 TMA, warp 1 MMA + TMEM, warps 4-7 and 8-11: split + flush
+constexpr int kTcDBuf = 4;       // D buffers of up to 128 columns (all of TMEM)
+constexpr int kTcTmemCols = 512;
 constexpr int kTcX2Every = 64;   // stages between moves of the tail sums to FP64
 constexpr long long kTcWaitNs = 2000000000ll;
 constexpr int kTcTile = 128 * 128;  // bytes of one stage
 
 struct TcShared {
   uint8_t tile[kTcStages][kTcTile];
-  double red[128][16];
+  double red[2][128][16];
   unsigned long long full[kTcStages], conv[kTcStages], empty[kTcStages];
-  unsigned long long dfull[2], dempty[2];
+  unsigned long long dfull[kTcDBuf], dempty[kTcDBuf];
   uint32_t tmem;
   int abort;
 };
@@ -179,7 +182,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       mb_init(&S.conv[s], 128);
       mb_init(&S.empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kTcDBuf; ++b) {
       mb_init(&S.dfull[b], 1);
       mb_init(&S.dempty[b], 128);
     }
@@ -229,8 +232,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (lane == 0) {
       int done = 0;
       for (int t = 0; t < nst; ++t) {
-        const int s = t % kTcStages, db = t & 1;
-        if (!mb_wait(&S.dempty[db], ((t >> 1) & 1) ^ 1, abort)) {
+        const int s = t % kTcStages, db = t % kTcDBuf;
+        if (!mb_wait(&S.dempty[db], ((t / kTcDBuf) & 1) ^ 1, abort)) {
           *abort = 1;
           atomicExch(err, 2);
           break;
@@ -254,23 +257,28 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (done > 0) mb_drain(&S.empty[(done - 1) % kTcStages], ((done - 1) / kTcStages) & 1);
     }
   } else if (warp >= 4) {
-    // ---- split x = h + l and read the accumulators (warp 4 + q reads TMEM lanes 32 q .. 32 q + 31)
-    const int tid = threadIdx.x - 128;
-    const int q = warp - 4;
+    // ---- split x = h + l and read the accumulators.  Two groups of four warps take alternate
+    // stages (group grp: stages grp, grp + 2, ...), so one group splits while the other waits on
+    // TMEM; warp 4 + 4 grp + q reads TMEM lanes 32 q .. 32 q + 31.
+    const int grp = (warp - 4) >> 2;
+    const int q = warp & 3;
+    const int tid = threadIdx.x - 128 - 128 * grp;
     const int r = 32 * q + lane;          // TMEM lane = tile row of this thread
     const int rl = r & 63;                // row within the head (or tail) half
     const int kt_me = rl / R;             // stacked K-tile of this row (>= KT: unused row)
     const int ra = (32 * q & 63) / R;     // first stacked K-tile this warp's lanes cover
+    constexpr int NF4 = KT * R * 128 / 16 / 128;  // float4 groups of data rows per thread and stage
     float s_h[16], c_h[16], x_l[16];
     double x_d[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) s_h[j] = c_h[j] = x_l[j] = 0.f, x_d[j] = 0.0;
     bool ok = true;
+    int nflush = 0;
 
     auto flush = [&](int u) -> bool {
-      const int db = u & 1;
+      const int db = u % kTcDBuf;
       // every wait's outcome is made warp-uniform: tcgen05.ld is a warp-collective instruction
-      if (!__all_sync(0xffffffffu, mb_wait(&S.dfull[db], (u >> 1) & 1, abort))) return false;
+      if (!__all_sync(0xffffffffu, mb_wait(&S.dfull[db], (u / kTcDBuf) & 1, abort))) return false;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(db * 128);
       float vh[16], vl[16];
@@ -304,14 +312,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           x_l[j] += vl[j];
         }
       }
-      if (u % kTcX2Every == kTcX2Every - 1) {
+      if (++nflush % kTcX2Every == 0) {
 #pragma unroll
         for (int j = 0; j < 16; ++j) x_d[j] += (double)x_l[j], x_l[j] = 0.f;
       }
       return true;
     };
 
-    for (int t = 0; t < nst && ok; ++t) {
+    int last = -1;
+    for (int t = grp; t < nst && ok; t += 2) {
       const int s = t % kTcStages;
       if (!__all_sync(0xffffffffu, mb_wait(&S.full[s], (t / kTcStages) & 1, abort))) {
         *abort = 1;
@@ -319,30 +328,35 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         ok = false;
         break;
       }
+      // data rows [0, KT R): heads in place, tails 64 rows down (loads first, then the stores)
       float4* tl = reinterpret_cast<float4*>(&S.tile[s][0]);
+      float4 xv[NF4];
 #pragma unroll
-      for (int i = tid; i < 64 * 128 / 16; i += 128) {  // rows [0, 64): heads in place, tails 64 rows down
-        const float4 x = tl[i];
+      for (int k = 0; k < NF4; ++k) xv[k] = tl[tid + 128 * k];
+#pragma unroll
+      for (int k = 0; k < NF4; ++k) {
+        const float4 x = xv[k];
         float4 h, l;
         h.x = tf32_rn(x.x), h.y = tf32_rn(x.y), h.z = tf32_rn(x.z), h.w = tf32_rn(x.w);
         l.x = tf32_rn(x.x - h.x), l.y = tf32_rn(x.y - h.y), l.z = tf32_rn(x.z - h.z), l.w = tf32_rn(x.w - h.w);
-        tl[i] = h;
-        tl[i + 64 * 128 / 16] = l;
+        tl[tid + 128 * k] = h;
+        tl[tid + 128 * k + 64 * 128 / 16] = l;
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mb_arrive(&S.conv[s]);
-      if (t > 0 && !flush(t - 1)) {
+      if (last >= 0 && !flush(last)) {
         *abort = 1;
         atomicExch(err, 5);
         ok = false;
       }
+      last = t;
     }
-    if (ok && nst > 0 && !flush(nst - 1)) {
+    if (ok && last >= 0 && !flush(last)) {
       *abort = 1;
       atomicExch(err, 5);
     }
 #pragma unroll
-    for (int j = 0; j < 16; ++j) S.red[r][j] = ((double)s_h[j] - (double)c_h[j]) + (x_d[j] + (double)x_l[j]);
+    for (int j = 0; j < 16; ++j) S.red[grp][r][j] = ((double)s_h[j] - (double)c_h[j]) + (x_d[j] + (double)x_l[j]);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -355,9 +369,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int i = o >> 4, j = o & 15;
     double v = 0.0;
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
+    for (int g = 0; g < 2; ++g)
 #pragma unroll
-      for (int kt = 0; kt < KT; ++kt) v += S.red[64 * h + kt * R + i][j];
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int kt = 0; kt < KT; ++kt) v += S.red[g][64 * h + kt * R + i][j];
     P[(int64_t)blockIdx.x * NOUT + o] = v;
   }
   // the last CTA adds the partials in CTA order
