@@ -461,6 +461,18 @@ ed_status ed_sym_ground_state(ed_sym* s, double* E0, double* residual, int* iter
  * ed_sym_ground_state. */
 ed_status ed_sym_ground_vector(const ed_sym* s, double* out);
 
+/* Green function of the cluster's physical sites for one spin (0 = up, 1 = down) from the irrep's
+ * ground state (Sec. 4.6): the site operators are symmetrized (c_rho = sum_a M_rho,a c_a, the
+ * projections of every site orbit onto every irrep beta; M orthogonal), c+_rho Omega and
+ * c_rho Omega land in the N +- 1 sectors of the product irrep alpha beta, where continued
+ * fractions (Eq. jacobi; off-diagonal pairs as in Sec. 4.3) run on the stored matrices until they
+ * change by less than the cluster's ED_OPT_GF_TOL (0: 1e-12) at two successive checks, and
+ * G_ab = sum M_rho,a M_sigma,b G_rho,sigma.  z_k = omega[k] + i eta (ED_AXIS_REAL) or i omega[k]
+ * (ED_AXIS_MATSUBARA).  G_out: host, interleaved complex128 [n_freq][n_sites][n_sites].  The group
+ * must map cluster sites to cluster sites.  ED_ERR_STATE before ed_sym_ground_state.  G is the
+ * ground-state G when the irrep holds the sector's (non-degenerate) ground state.  Synchronous. */
+ed_status ed_sym_green(ed_sym* s, const double* omega, int n_freq, double eta, int axis, int spin, double* G_out);
+
 void ed_sym_destroy(ed_sym* s);
 
 /* ---- measurement of the library's own kernels (no counterpart in the paper) --------------- */

@@ -30,6 +30,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <numeric>
 #include <vector>
@@ -344,13 +345,79 @@ __global__ void k_sym_start(double* __restrict__ v, int64_t dim, uint64_t seed) 
     v[i] = 2.0 * ((double)(sym_splitmix64(seed ^ (uint64_t)i) >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
 }
 
+// ---- Green functions with symmetrized operators (Sec. 4.6)
+//
+// phi = c+_rho Omega (create = 1) or c_rho Omega (create = 0) for c_rho = sum_a m[a] c_{a spin}, in
+// pull form over the target irrep's representatives r': the binary state b = c_a r' (create) or
+// c+_a r' (annihilate) has the Jordan-Wigner sign (-1)^(occupied modes before mode a), its
+// representative r in the source irrep (of Omega) carries phi_g(b) chi_g, and
+//   phi[r'] = sum_a m[a] sign_a phi_g(b) chi_g sqrt(|S_r| / |S_r'|) Omega[r]
+// (the projector relation c_rho P_alpha' = P_alpha c_rho for +-1 characters, alpha' = alpha beta).
+__global__ void __launch_bounds__(128) k_sym_apply(const SymDev* __restrict__ Gsrc, const uint64_t* __restrict__ src_keys,
+                                                   const uint8_t* __restrict__ src_stab, int64_t src_dim,
+                                                   const double* __restrict__ omega, const uint64_t* __restrict__ tgt_keys,
+                                                   const uint8_t* __restrict__ tgt_stab, int64_t tgt_dim,
+                                                   const double* __restrict__ m, int create, int spin,
+                                                   double* __restrict__ out) {
+  __shared__ SymDev G;
+  for (int i = threadIdx.x; i < (int)(sizeof(SymDev) / 4); i += blockDim.x)
+    reinterpret_cast<int*>(&G)[i] = reinterpret_cast<const int*>(Gsrc)[i];
+  __syncthreads();
+  const uint64_t lmask = (G.L == 32) ? 0xFFFFFFFFull : ((1ull << G.L) - 1ull);
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < tgt_dim; r += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = tgt_keys[r];
+    const uint32_t bu = (uint32_t)(k >> G.L), bd = (uint32_t)(k & lmask);
+    const double st = (double)tgt_stab[r];
+    double acc = 0.0;
+    for (int a = 0; a < G.L; ++a) {
+      const double w = m[a];
+      if (w == 0.0) continue;
+      const uint32_t bs = spin ? bd : bu;
+      const bool occ = (bs >> a) & 1u;
+      if (create ? !occ : occ) continue;
+      const uint32_t nb = bs ^ (1u << a);
+      const int before = spin ? __popc(bu) + __popc(bd & ((1u << a) - 1u)) : __popc(bu & ((1u << a) - 1u));
+      uint64_t rk;
+      int f;
+      sym_rep(G, spin ? bu : nb, spin ? nb : bd, &rk, &f);
+      const int64_t c = sym_find(src_keys, src_dim, rk);
+      if (c < 0) continue;
+      acc += w * ((before & 1) ? -1.0 : 1.0) * (double)f * sqrt((double)src_stab[c] / st) * omega[c];
+    }
+    out[r] = acc;
+  }
+}
+
+// out[iz] += coef * b0sq / (z - s (a_0 - E0) - b_1^2 / (z - s (a_1 - E0) - ...)), n levels, s = +1
+// for the electron part and -1 for the hole part (Eq. jacobi with the E0 shift); z = zr + i zi.
+__global__ void k_sym_cf_eval(const double* __restrict__ alpha, const double* __restrict__ beta, int n, double E0,
+                              double b0sq, double s, const double* __restrict__ zr, const double* __restrict__ zi,
+                              int nz, double coef, double2* __restrict__ out) {
+  for (int iz = blockIdx.x * blockDim.x + threadIdx.x; iz < nz; iz += gridDim.x * blockDim.x) {
+    double gr = 0.0, gi = 0.0;  // the tail 1 / (z - ...) built from the last level up
+    for (int j = n - 1; j >= 0; --j) {
+      const double b2 = j + 1 < n ? beta[j + 1] * beta[j + 1] : 0.0;
+      const double dr = zr[iz] - s * (alpha[j] - E0) - b2 * gr;
+      const double di = zi[iz] - b2 * gi;
+      const double den = dr * dr + di * di;
+      gr = dr / den;
+      gi = -di / den;
+    }
+    out[iz].x += coef * b0sq * gr;
+    out[iz].y += coef * b0sq * gi;
+  }
+}
+
 }  // namespace ed
 
 // ---------------------------------------------------------------- the handle
 struct ed_sym {
   ed_cluster* c = nullptr;
   int n_gen = 0;
+  int n_up = 0, n_dn = 0;     // the sector
   std::vector<int> signs;
+  std::vector<int> perm;     // n_gen x L generator images
+  ed::SymDev host;           // host copy of the group (characters of this irrep)
   ed::DevBuf<ed::SymDev> G;
   int64_t dim = 0, nnz = 0;
   ed::DevBuf<uint64_t> keys;
@@ -407,11 +474,12 @@ static void sym_build(ed_sym& S, const int* perm, cudaStream_t s) {
     h.pb[p] = m.pair_b[p];
     h.pv[p] = m.h[(size_t)m.pair_a[p] * L + m.pair_b[p]];
   }
+  S.host = h;
   S.G.alloc(1);
-  ED_CUDA(cudaMemcpyAsync(S.G.p, &h, sizeof(SymDev), cudaMemcpyHostToDevice, s));
+  ED_CUDA(cudaMemcpyAsync(S.G.p, &S.host, sizeof(SymDev), cudaMemcpyHostToDevice, s));
 
-  SpinTables& tu = c.tables(c.desc.n_up);
-  SpinTables& td = c.tables(c.desc.n_dn);
+  SpinTables& tu = c.tables(S.n_up);
+  SpinTables& td = c.tables(S.n_dn);
   const int64_t du = tu.dim, dd = td.dim, n = du * dd;
   const int nblk = (int)((n + kSymChunk - 1) / kSymChunk);
   DevBuf<int64_t> cnt(nblk), off(nblk);
@@ -555,6 +623,235 @@ static void sym_ground_state(ed_sym& S, double tol, int max_iter, uint64_t seed)
   }
 }
 
+// The sector of the same group for another particle number and irrep.
+static std::unique_ptr<ed_sym> sym_sibling(const ed_sym& S, int n_up, int n_dn, const std::vector<int>& signs,
+                                           cudaStream_t s) {
+  auto T = std::make_unique<ed_sym>();
+  T->c = S.c;
+  T->n_gen = S.n_gen;
+  T->n_up = n_up;
+  T->n_dn = n_dn;
+  T->signs = signs;
+  T->perm = S.perm;
+  sym_build(*T, T->perm.data(), s);
+  return T;
+}
+
+constexpr int kSymCfCheck = 40;      // levels between convergence checks on the grid
+constexpr int kSymCfMax = 20000;     // preset maximum of a continued fraction
+
+// Lanczos levels a_n, b_n of the sector T from the (unnormalized) vector phi, run until the
+// fraction (electron s = +1 or hole s = -1) changes on the grid by less than tol between two
+// checks, b_n vanishes, or the preset maximum; then coef * fraction is added to out[nz].
+// Returns the number of levels.
+static int sym_cf(ed_sym& T, const double* phi, double E0, double s_eh, const DevBuf<double>& zr,
+                  const DevBuf<double>& zi, int nz, double tol, double coef, double2* out, cudaStream_t s) {
+  const int64_t dim = T.dim;
+  const int nb = sym_grid(dim, kSymThreads / 32 * 4), nv = sym_grid(dim, kSymThreads * 4);
+  const int maxn = (int)std::min<int64_t>(kSymCfMax, 2 * dim + 16);
+  DevBuf<double> V0(dim), V1(dim), W(dim), alpha(maxn + 1), beta(maxn + 2), part(std::max(nb, nv)), nrm(1);
+  DevBuf<double2> g0(nz), g1(nz);
+  ED_CUDA(cudaMemsetAsync(beta.p, 0, (maxn + 2) * sizeof(double), s));
+  k_sym_axpy_norm<<<nv, kSymThreads, 0, s>>>(const_cast<double*>(phi), nullptr, nullptr, dim, part.p);
+  k_sym_finish<<<1, kSymThreads, 0, s>>>(part.p, nv, nrm.p, 1);
+  k_sym_scale<<<nv, kSymThreads, 0, s>>>(V0.p, phi, nrm.p, dim, nullptr, nullptr);
+  ED_CHECK_LAUNCH();
+  double b0 = 0.0;
+  ED_CUDA(cudaMemcpyAsync(&b0, nrm.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+  ED_CUDA(cudaMemsetAsync(V1.p, 0, dim * sizeof(double), s));
+  ED_CUDA(cudaStreamSynchronize(s));
+  if (!(b0 > 0.0)) return 0;
+  const double b0sq = b0 * b0;
+  std::vector<double2> h0(nz), h1(nz);
+  std::vector<double> hb(maxn + 2);
+  double* v = V0.p;
+  double* vp = V1.p;
+  int levels = 0, quiet = 0;
+  bool have_prev = false;
+  for (int n = 0; n < maxn; ++n) {
+    sym_spmv(T, v, W.p, vp, beta.p + n, part.p, nb, s);
+    k_sym_finish<<<1, kSymThreads, 0, s>>>(part.p, nb, alpha.p + n, 0);
+    k_sym_axpy_norm<<<nv, kSymThreads, 0, s>>>(W.p, v, alpha.p + n, dim, part.p);
+    k_sym_finish<<<1, kSymThreads, 0, s>>>(part.p, nv, beta.p + n + 1, 1);
+    k_sym_scale<<<nv, kSymThreads, 0, s>>>(vp, W.p, beta.p + n + 1, dim, nullptr, nullptr);
+    ED_CHECK_LAUNCH();
+    std::swap(v, vp);
+    levels = n + 1;
+    if ((n + 1) % kSymCfCheck == 0 || n + 1 == maxn) {
+      ED_CUDA(cudaMemsetAsync(g1.p, 0, nz * sizeof(double2), s));
+      k_sym_cf_eval<<<(nz + 127) / 128, 128, 0, s>>>(alpha.p, beta.p, levels, E0, b0sq, s_eh, zr.p, zi.p, nz, 1.0, g1.p);
+      ED_CHECK_LAUNCH();
+      ED_CUDA(cudaMemcpyAsync(h1.data(), g1.p, nz * sizeof(double2), cudaMemcpyDeviceToHost, s));
+      ED_CUDA(cudaMemcpyAsync(hb.data(), beta.p, (n + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
+      ED_CUDA(cudaStreamSynchronize(s));
+      // an invariant subspace: stop at the first vanishing b_j
+      int brk = -1;
+      for (int j = 1; j <= n + 1; ++j)
+        if (!(hb[j] > 1e-10 * std::max(1.0, std::fabs(E0)))) {
+          brk = j;
+          break;
+        }
+      if (brk > 0) {
+        levels = brk;
+        break;
+      }
+      double d = 0.0;
+      for (int i = 0; i < nz && have_prev; ++i)
+        d = std::max(d, std::hypot(h1[i].x - h0[i].x, h1[i].y - h0[i].y));
+      quiet = (have_prev && d < tol) ? quiet + 1 : 0;
+      if (quiet >= 2) break;  // two successive checks below the tolerance
+      h0.swap(h1);
+      have_prev = true;
+    }
+  }
+  k_sym_cf_eval<<<(nz + 127) / 128, 128, 0, s>>>(alpha.p, beta.p, levels, E0, b0sq, s_eh, zr.p, zi.p, nz, coef, out);
+  ED_CHECK_LAUNCH();
+  ED_CUDA(cudaStreamSynchronize(s));
+  return levels;
+}
+
+__global__ void k_sym_add(const double* __restrict__ x, const double* __restrict__ y, int64_t n, double* __restrict__ z) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    z[i] = x[i] + y[i];
+}
+
+// G_ab(z) = sum over rows rho, sigma of the same irrep of M_rho,a M_sigma,b G_rho,sigma(z), with
+// G_rho,rho = D_rho and G_rho,sigma = (P_rho,sigma - D_rho - D_sigma) / 2 (the pair combination
+// of Sec. 4.3 for a real Hamiltonian).  M: [nrow][ns] (orthonormal rows); pidx[rho][sigma]: the
+// pair's slot in P, or -1 when the rows belong to different irreps.  Out: [nz][ns][ns].
+__global__ void k_sym_assemble(int nz, int ns, int nrow, const double* __restrict__ M, const int* __restrict__ pidx,
+                               const double2* __restrict__ D, const double2* __restrict__ P, double2* __restrict__ G) {
+  const int64_t total = (int64_t)nz * ns * ns;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int iz = (int)(t / (ns * ns)), a = (int)((t / ns) % ns), b = (int)(t % ns);
+    double gr = 0.0, gi = 0.0;
+    for (int r = 0; r < nrow; ++r) {
+      const double mra = M[r * ns + a];
+      if (mra == 0.0) continue;
+      for (int q = 0; q < nrow; ++q) {
+        const double w = mra * M[q * ns + b];
+        if (w == 0.0) continue;
+        double2 g;
+        if (q == r) {
+          g = D[(int64_t)r * nz + iz];
+        } else {
+          const int k = pidx[r * nrow + q];
+          if (k < 0) continue;
+          const double2 p = P[(int64_t)k * nz + iz], d1 = D[(int64_t)r * nz + iz], d2 = D[(int64_t)q * nz + iz];
+          g = make_double2(0.5 * (p.x - d1.x - d2.x), 0.5 * (p.y - d1.y - d2.y));
+        }
+        gr += w * g.x;
+        gi += w * g.y;
+      }
+    }
+    G[t] = make_double2(gr, gi);
+  }
+}
+
+// Green function of the cluster's physical sites for one spin from the irrep ground state of S
+// (Sec. 4.6): symmetrized site operators of every irrep beta, continued fractions in the N +- 1
+// sectors of the product irrep alpha beta, recombined with the orthogonal matrix M of the
+// operators (Q_ar = (M^-1)_a,rho Q_rho,r, here with M^-1 = M^T).
+static void sym_green(ed_sym& S, const double* omega, int nz, double eta, int axis, int spin, double* G_out) {
+  ed_cluster& c = *S.c;
+  cudaStream_t s = c.stream;
+  if (!S.have_gs) throw Error(ED_ERR_STATE, "no ground state of this irrep yet (ed_sym_ground_state)");
+  const int L = c.model.L, ns = c.model.ns, ng = 1 << S.n_gen;
+  for (int g = 0; g < ng; ++g)
+    for (int a = 0; a < ns; ++a)
+      if (S.host.perm[g][a] >= ns) throw Error(ED_ERR_INVALID, "the group maps a cluster site to a bath orbital");
+  // rows: the projection of each site orbit onto each irrep beta (generator signs), normalized
+  std::vector<std::vector<int>> row_sig;
+  std::vector<std::vector<double>> row_m;
+  for (int bm = 0; bm < ng; ++bm) {
+    std::vector<int> sig(S.n_gen);
+    for (int j = 0; j < S.n_gen; ++j) sig[j] = (bm >> j & 1) ? -1 : 1;
+    std::vector<char> seen(ns, 0);
+    for (int a = 0; a < ns; ++a) {
+      if (seen[a]) continue;
+      std::vector<double> v(L, 0.0);
+      for (int g = 0; g < ng; ++g) {
+        int chi = 1;
+        for (int j = 0; j < S.n_gen; ++j)
+          if (g >> j & 1) chi *= sig[j];
+        v[S.host.perm[g][a]] += (double)chi / ng;
+        seen[S.host.perm[g][a]] = 1;
+      }
+      double nn = 0.0;
+      for (double x : v) nn += x * x;
+      if (nn < 1e-20) continue;
+      for (double& x : v) x /= std::sqrt(nn);
+      row_sig.push_back(sig);
+      row_m.push_back(v);
+    }
+  }
+  const int nrow = (int)row_m.size();
+  if (nrow != ns) throw Error(ED_ERR_INVALID, "symmetrized site operators do not span the sites");
+  std::vector<double> zr_h(nz), zi_h(nz);
+  for (int i = 0; i < nz; ++i) {
+    zr_h[i] = axis == ED_AXIS_MATSUBARA ? 0.0 : omega[i];
+    zi_h[i] = axis == ED_AXIS_MATSUBARA ? omega[i] : eta;
+  }
+  DevBuf<double> zr(nz), zi(nz), Md(L);
+  ED_CUDA(cudaMemcpyAsync(zr.p, zr_h.data(), nz * sizeof(double), cudaMemcpyHostToDevice, s));
+  ED_CUDA(cudaMemcpyAsync(zi.p, zi_h.data(), nz * sizeof(double), cudaMemcpyHostToDevice, s));
+  std::vector<int> pidx(nrow * nrow, -1);
+  int npair = 0;
+  for (int r = 0; r < nrow; ++r)
+    for (int q = r + 1; q < nrow; ++q)
+      if (row_sig[r] == row_sig[q]) pidx[r * nrow + q] = pidx[q * nrow + r] = npair++;
+  DevBuf<double2> D((size_t)std::max(1, nrow) * nz), P((size_t)std::max(1, npair) * nz);
+  ED_CUDA(cudaMemsetAsync(D.p, 0, D.n * sizeof(double2), s));
+  ED_CUDA(cudaMemsetAsync(P.p, 0, P.n * sizeof(double2), s));
+  const double tol = c.gf_tol > 0.0 ? c.gf_tol : 1e-12;
+  const double E0 = S.E0;
+  const int nu = S.n_up, nd = S.n_dn;
+  for (int part = 0; part < 2; ++part) {  // 0: electron (c+ Omega, N + 1), 1: hole (c Omega, N - 1)
+    const int du = spin == 0 ? (part == 0 ? 1 : -1) : 0, dd = spin == 1 ? (part == 0 ? 1 : -1) : 0;
+    if (nu + du < 0 || nu + du > L || nd + dd < 0 || nd + dd > L) continue;
+    const double s_eh = part == 0 ? 1.0 : -1.0;
+    std::map<std::vector<int>, std::unique_ptr<ed_sym>> sectors;
+    std::vector<DevBuf<double>> phi(nrow);
+    std::vector<ed_sym*> tgt(nrow, nullptr);
+    for (int r = 0; r < nrow; ++r) {
+      std::vector<int> sig(S.n_gen);
+      for (int j = 0; j < S.n_gen; ++j) sig[j] = S.signs[j] * row_sig[r][j];
+      auto& T = sectors[sig];
+      if (!T) T = sym_sibling(S, nu + du, nd + dd, sig, s);
+      tgt[r] = T.get();
+      if (T->dim == 0) continue;
+      phi[r].alloc(T->dim);
+      ED_CUDA(cudaMemcpyAsync(Md.p, row_m[r].data(), L * sizeof(double), cudaMemcpyHostToDevice, s));
+      k_sym_apply<<<sym_grid(T->dim, 128), 128, 0, s>>>(S.G.p, S.keys.p, S.stab.p, S.dim, S.omega.p, T->keys.p,
+                                                        T->stab.p, T->dim, Md.p, part == 0 ? 1 : 0, spin, phi[r].p);
+      ED_CHECK_LAUNCH();
+      ED_CUDA(cudaStreamSynchronize(s));  // Md is rewritten for the next row
+      sym_cf(*T, phi[r].p, E0, s_eh, zr, zi, nz, tol, 1.0, D.p + (size_t)r * nz, s);
+    }
+    for (int r = 0; r < nrow; ++r)
+      for (int q = r + 1; q < nrow; ++q) {
+        const int k = pidx[r * nrow + q];
+        if (k < 0 || tgt[r]->dim == 0) continue;
+        DevBuf<double> sum(tgt[r]->dim);
+        k_sym_add<<<sym_grid(tgt[r]->dim, kSymThreads * 4), kSymThreads, 0, s>>>(phi[r].p, phi[q].p, tgt[r]->dim, sum.p);
+        ED_CHECK_LAUNCH();
+        sym_cf(*tgt[r], sum.p, E0, s_eh, zr, zi, nz, tol, 1.0, P.p + (size_t)k * nz, s);
+      }
+  }
+  std::vector<double> Mh((size_t)nrow * ns);
+  for (int r = 0; r < nrow; ++r)
+    for (int a = 0; a < ns; ++a) Mh[(size_t)r * ns + a] = row_m[r][a];
+  DevBuf<double> Mdev(Mh.size());
+  DevBuf<int> Pd(pidx.size());
+  DevBuf<double2> G((size_t)nz * ns * ns);
+  ED_CUDA(cudaMemcpyAsync(Mdev.p, Mh.data(), Mh.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  ED_CUDA(cudaMemcpyAsync(Pd.p, pidx.data(), pidx.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  k_sym_assemble<<<sym_grid((int64_t)nz * ns * ns, 256), 256, 0, s>>>(nz, ns, nrow, Mdev.p, Pd.p, D.p, P.p, G.p);
+  ED_CHECK_LAUNCH();
+  ED_CUDA(cudaMemcpyAsync(G_out, G.p, (size_t)nz * ns * ns * sizeof(double2), cudaMemcpyDeviceToHost, s));
+  ED_CUDA(cudaStreamSynchronize(s));
+}
+
 static void sym_validate(const ed_cluster* c, int n_gen, const int* perm, const int* signs) {
   if (!c) throw Error(ED_ERR_INVALID, "cluster is NULL");
   if (n_gen < 1 || n_gen > kSymMaxGen) throw Error(ED_ERR_INVALID, "need 1 to 5 generators");
@@ -640,7 +937,10 @@ ed_status ed_sym_create(ed_cluster* c, int n_gen, const int* perm, const int* si
     auto S = std::make_unique<ed_sym>();
     S->c = c;
     S->n_gen = n_gen;
+    S->n_up = c->desc.n_up;
+    S->n_dn = c->desc.n_dn;
     S->signs.assign(signs, signs + n_gen);
+    S->perm.assign(perm, perm + n_gen * c->model.L);
     AllocStreamScope as_(c->stream);
     sym_build(*S, perm, c->stream);
     *out = S.release();
@@ -713,6 +1013,22 @@ ed_status ed_sym_ground_vector(const ed_sym* S, double* out) {
     sym_require_device(S->c);
     ED_CUDA(cudaMemcpyAsync(out, S->omega.p, S->dim * sizeof(double), cudaMemcpyDeviceToHost, S->c->stream));
     ED_CUDA(cudaStreamSynchronize(S->c->stream));
+    return ED_OK;
+  });
+}
+
+ed_status ed_sym_green(ed_sym* S, const double* omega, int n_freq, double eta, int axis, int spin, double* G_out) {
+  return sym_guard([&]() -> ed_status {
+    if (!S || !omega || !G_out) throw Error(ED_ERR_INVALID, "handle, omega and G_out must not be NULL");
+    if (n_freq < 1) throw Error(ED_ERR_INVALID, "n_freq must be positive");
+    if (axis != ED_AXIS_REAL && axis != ED_AXIS_MATSUBARA) throw Error(ED_ERR_INVALID, "unknown axis");
+    if (spin != 0 && spin != 1) throw Error(ED_ERR_INVALID, "spin must be 0 or 1");
+    for (int i = 0; i < n_freq; ++i)
+      if (!std::isfinite(omega[i])) throw Error(ED_ERR_INVALID, "non-finite frequency");
+    if (!std::isfinite(eta)) throw Error(ED_ERR_INVALID, "non-finite eta");
+    sym_require_device(S->c);
+    AllocStreamScope as_(S->c->stream);
+    sym_green(*S, omega, n_freq, eta, axis, spin, G_out);
     return ED_OK;
   });
 }

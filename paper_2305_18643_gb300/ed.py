@@ -623,6 +623,7 @@ _sym_sigs = {
     "ed_sym_hpsi": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "ed_sym_ground_state": (C.c_int, [C.c_void_p, _dp, _dp, C.POINTER(C.c_int)]),
     "ed_sym_ground_vector": (C.c_int, [C.c_void_p, _dp]),
+    "ed_sym_green": (C.c_int, [C.c_void_p, _dp, C.c_int, C.c_double, C.c_int, C.c_int, _dp]),
     "ed_sym_destroy": (None, [C.c_void_p]),
 }
 
@@ -680,6 +681,15 @@ def ed_sym_ground_vector(s):
     v = np.zeros(d)
     _check(lib().ed_sym_ground_vector(s, v.ctypes.data_as(_dp)))
     return v
+
+
+def ed_sym_green(s, omega, n_sites, eta=0.05, axis=ED_AXIS_REAL, spin=0):
+    """G[n_freq, n_sites, n_sites] (complex, host) from the irrep's ground state (symmetrized operators)."""
+    om = np.ascontiguousarray(np.asarray(omega, dtype=np.float64))
+    G = np.zeros((len(om), n_sites, n_sites), dtype=np.complex128)
+    _check(lib().ed_sym_green(s, om.ctypes.data_as(_dp), len(om), float(eta), int(axis), int(spin),
+                              G.ctypes.data_as(_dp)))
+    return G
 
 
 def ed_sym_destroy(s):

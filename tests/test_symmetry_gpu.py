@@ -1,6 +1,7 @@
 """Symmetrized sectors (Sec. 4.5) on the GPU against the symmetry oracle: the representatives and
 their stabilizers bit for bit, the stored matrix entry by entry, H.psi, and the ground energy of
-every irrep; Table 1's counts straight from the device matrix; invalid groups are refused."""
+every irrep; Table 1's counts straight from the device matrix; invalid groups are refused; the
+Green function with symmetrized operators (Sec. 4.6) against the exact Lehmann sum."""
 
 import json
 import os
@@ -210,5 +211,90 @@ def test_invalid_groups_are_refused():
             with pytest.raises(ed.EDError) as e:
                 ed.ed_sym_create(hc, np.array(perms), signs)
             assert e.value.status == ed.ED_ERR_INVALID
+    finally:
+        ed.ed_cluster_destroy(hc)
+
+
+def _ground_irrep(hc, gens):
+    """The irrep holding the sector's ground state: (signs, handle with its ground state, E)."""
+    best = None
+    for ir in S.all_irreps(len(gens)):
+        s = ed.ed_sym_create(hc, np.array(gens), ir)
+        d, _ = ed.ed_sym_info(s)
+        if d == 0:
+            ed.ed_sym_destroy(s)
+            continue
+        E = ed.ed_sym_ground_state(s)[0]
+        if best is None or E < best[2]:
+            if best is not None:
+                ed.ed_sym_destroy(best[1])
+            best = (ir, s, E)
+        else:
+            ed.ed_sym_destroy(s)
+    return best
+
+
+def _gf_cases():
+    out = [c for c in _cases()]
+    (t, U, mu, nu, nd, eps, theta), gens = _bath_case()
+    out.append(("plaquette + bath C2v", (t, U, mu, nu, nd, eps, theta), gens))
+    return out
+
+
+@pytest.mark.parametrize("case", _gf_cases(), ids=lambda c: c[0])
+def test_symmetrized_green_function_matches_oracle(case):
+    """Sec. 4.6: G from the irrep ground state with symmetrized site operators, continued
+    fractions in the N +- 1 irrep sectors and the M^-1 recombination, against the exact Lehmann
+    sum of the unsymmetrized sectors (real axis, eta = 0.1, and Matsubara axis, beta = 50), for
+    both spins when N_up != N_dn.  Clusters whose ground state is degenerate are skipped (G is
+    then not unique)."""
+    name, params, gens = case
+    t, U, mu, nu, nd = params[:5]
+    eps, theta = (params[5], params[6]) if len(params) > 5 else (None, None)
+    hc, m = _cluster(t, U, mu, nu, nd, eps, theta)
+    try:
+        ir, s, E = _ground_irrep(hc, gens)
+        try:
+            om_r = np.linspace(-8.0, 8.0, 64)
+            om_m = (2 * np.arange(32) + 1) * np.pi / 50.0
+            for spin in ((0, 1) if nu != nd else (0,)):
+                Gr, _, _, E0o, gap = O_green_exact(m, nu, nd, om_r + 0.1j, spin)
+                if gap < 1e-6:
+                    pytest.skip("degenerate ground state")
+                assert abs(E - E0o) <= 1e-10 * max(1.0, abs(E0o))
+                G = ed.ed_sym_green(s, om_r, m.ns, eta=0.1, axis=ed.ED_AXIS_REAL, spin=spin)
+                assert np.max(np.abs(G - Gr)) <= 1e-8, np.max(np.abs(G - Gr))
+                Gm = O_green_exact(m, nu, nd, 1j * om_m, spin)[0]
+                G = ed.ed_sym_green(s, om_m, m.ns, axis=ed.ED_AXIS_MATSUBARA, spin=spin)
+                assert np.max(np.abs(G - Gm)) <= 1e-8, np.max(np.abs(G - Gm))
+        finally:
+            ed.ed_sym_destroy(s)
+    finally:
+        ed.ed_cluster_destroy(hc)
+
+
+def O_green_exact(m, nu, nd, z, spin):
+    from oracle.ed_oracle import green_exact
+
+    return green_exact(m, nu, nd, np.asarray(z), spin=spin)
+
+
+def test_symmetrized_green_function_3x4_matches_the_unsymmetrized_path():
+    """The interacting half-filled 3x4 cluster (853,776 states): G of the A1 ground state from the
+    symmetrized sectors against the library's own continued-fraction G on the full sectors
+    (itself oracle-pinned), Matsubara axis."""
+    h, mx, my = rect(4, 3)
+    t = h
+    c = {"t": t, "U": np.full(12, 4.0), "mu": 2.0, "n_up": 6, "n_dn": 6}
+    hc = ed.ed_cluster_create(c, precision=ed.ED_FP64, gf_method=ed.ED_GF_CF, seed=5, tol=1e-13)
+    try:
+        om = (2 * np.arange(16) + 1) * np.pi / 50.0
+        G_full = ed.ed_green(hc, om, 0.0, 12, spin=0, axis=ed.ED_AXIS_MATSUBARA)[1]
+        ir, s, E = _ground_irrep(hc, [mx, my])
+        try:
+            G = ed.ed_sym_green(s, om, 12, axis=ed.ED_AXIS_MATSUBARA)
+            assert np.max(np.abs(G - G_full)) <= 1e-8, np.max(np.abs(G - G_full))
+        finally:
+            ed.ed_sym_destroy(s)
     finally:
         ed.ed_cluster_destroy(hc)
