@@ -296,6 +296,107 @@ __device__ void block_hx(const BTable& tu, const BTable& td, const T* sval, cons
   sxx = c;
 }
 
+// Four vectors of one sector interleaved element by element (x[4 o + q] is vector q's element o):
+// the continued fractions of one (cluster, spin, part) advance together, so every table entry and
+// every gather serves four runs.
+template <typename T>
+struct alignas(4 * sizeof(T)) Q4 {
+  T v[4];
+};
+
+// W4 = H X4 - bcoef[q] W4 (in place) for four interleaved vectors, with the per-vector partial sums
+// of <x,w>, <w,w>, <x,x> reduced over the block into out[3 q + i].
+template <typename T>
+__device__ void block_hx4(const BTable& tu, const BTable& td, const T* sval, const T* sU, uint32_t umask, T u0, bool uni,
+                          const Q4<T>* X, Q4<T>* W, const T (&bcoef)[4], int mode, double (&out)[12],
+                          double (*red)[32], double* bcast) {
+  const int64_t du = tu.dim, dd = td.dim;
+  const T* eu = BP<T>::e(tu);
+  const T* ed = BP<T>::e(td);
+  BPart3<T> part[4];
+  auto element = [&](int64_t u, int64_t d) {
+    const int64_t o = u * dd + d;
+    const uint32_t bu = tu.basis[u], bd = td.basis[d];
+    T diag = eu[u] + ed[d];
+    uint32_t dbl = bu & bd & umask;
+    if (uni) {
+      diag += u0 * (T)__popc(dbl);
+    } else {
+      while (dbl) {
+        diag += sU[__ffs(dbl) - 1];
+        dbl &= dbl - 1u;
+      }
+    }
+    const Q4<T> x = X[o];
+    T acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = diag * x.v[q];
+    const Q4<T>* xr = X + u * dd;
+    const int nd = td.cnt[d];
+    for (int k = 0; k < nd; ++k) {
+      const uint32_t e = td.ell[(int64_t)k * dd + d];
+      const T v = ent_neg(e) ? -sval[ent_vidx(e)] : sval[ent_vidx(e)];
+      const Q4<T> g = xr[ent_col(e)];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] += v * g.v[q];
+    }
+    const int nu = tu.cnt[u];
+    for (int k = 0; k < nu; ++k) {
+      const uint32_t e = tu.ell[(int64_t)k * du + u];
+      const T v = ent_neg(e) ? -sval[ent_vidx(e)] : sval[ent_vidx(e)];
+      const Q4<T> g = X[(int64_t)ent_col(e) * dd + d];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] += v * g.v[q];
+    }
+    Q4<T> w = W[o];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      w.v[q] = acc[q] - bcoef[q] * w.v[q];
+      part[q].add(x.v[q], w.v[q]);
+    }
+    W[o] = w;
+  };
+  if (mode == 1 && dd >= 16) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t u = warp; u < du; u += nw)
+      for (int64_t d = lane; d < dd; d += 32) element(u, d);
+  } else {
+    const int64_t su = blockDim.x / dd, sd = blockDim.x - su * dd;
+    int64_t u = threadIdx.x / dd, d = threadIdx.x - u * dd;
+    for (; u < du; u += su, d += sd) {
+      if (d >= dd) {
+        d -= dd;
+        ++u;
+        if (u >= du) break;
+      }
+      element(u, d);
+    }
+  }
+  // block sums of the twelve partials (fixed order: warps in order, then one thread)
+  double v[12];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) v[3 * q + i] = part[q].get(i);
+#pragma unroll
+  for (int i = 0; i < 12; ++i)
+    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
+  const int wi = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (l == 0)
+#pragma unroll
+    for (int i = 0; i < 12; ++i) red[i][wi] = v[i];
+  __syncthreads();
+  if (threadIdx.x < 12) {
+    double s = 0.0;
+    for (int k = 0; k < nw; ++k) s += red[threadIdx.x][k];
+    bcast[threadIdx.x] = s;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 12; ++i) out[i] = bcast[i];
+}
+
 __device__ __forceinline__ uint64_t b_splitmix64(uint64_t x) {
   uint64_t z = x + 0x9E3779B97F4A7C15ull;
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -522,7 +623,9 @@ __global__ void k_batch_gs(BCluster* __restrict__ C, const int* __restrict__ ord
 // -------------------------------------------------------------------------------- continued fractions
 struct CFShared {
   BlockShared bs;
-  double2 prev[64];
+  double2 prev[4][64];
+  double red12[12][32];
+  double bcast12[12];
   double maxdiff;
   float svalf[kMaxVals];
   double svald[kMaxVals];
@@ -704,23 +807,27 @@ __device__ void warp_cf_run(BRun& r, const BCluster& c, const BTable* tabs, T* V
 // queue[0]; once those are gone, every warp takes runs order[n_block, n) from queue[1] and does
 // each alone in its slice of the block's workspace.
 template <typename T>
-__global__ void k_batch_cf(BRun* __restrict__ R, const int* __restrict__ order, int n_block, int n,
-                           const BCluster* __restrict__ C, const BTable* __restrict__ tabs, int* __restrict__ queue,
-                           BWork w, const double2* __restrict__ z, int nz, double tol, int mode) {
+__global__ void __launch_bounds__(512) k_batch_cf(BRun* __restrict__ R, const int* __restrict__ order, int n_block, int n,
+                           const int4* __restrict__ groups, int n_groups, const BCluster* __restrict__ C,
+                           const BTable* __restrict__ tabs, int* __restrict__ queue, BWork w,
+                           const double2* __restrict__ z, int nz, double tol, int mode) {
   __shared__ CFShared g;
   char* ws = w.base + (int64_t)blockIdx.x * w.stride;
-  T* V0 = (T*)ws;
-  T* V1 = V0 + w.maxd;
   const int zstride = max(1, (nz + 63) / 64);  // at most 64 check frequencies (g.prev)
   const int nzs = (nz + zstride - 1) / zstride;
+  // block phase: groups of up to four runs of one (cluster, spin, part), interleaved
   while (true) {
     __syncthreads();
     if (threadIdx.x == 0) g.flag = atomicAdd(queue, 1);
     __syncthreads();
     const int item = g.flag;
-    if (item >= n_block) break;
-    BRun& r = R[order[item]];
-    const BCluster& c = C[r.cluster];
+    if (item >= n_groups) break;
+    const int4 gi = groups[item];
+    const int rid[4] = {gi.x, gi.y, gi.z, gi.w};
+    int m = 0;
+    while (m < 4 && rid[m] >= 0) ++m;
+    const BRun& r0 = R[rid[0]];
+    const BCluster& c = C[r0.cluster];
     for (int i = threadIdx.x; i < kMaxVals; i += blockDim.x) {
       g.svalf[i] = c.hp.valf[i];
       g.svald[i] = c.hp.val[i];
@@ -729,91 +836,160 @@ __global__ void k_batch_cf(BRun* __restrict__ R, const int* __restrict__ order, 
       g.sUf[i] = c.hp.Uf[i];
       g.sUd[i] = c.hp.U[i];
     }
-    for (int i = threadIdx.x; i < 64; i += blockDim.x) g.prev[i] = make_double2(0.0, 0.0);
-    const BTable tu = tabs[r.tu], td = tabs[r.td], src = tabs[r.src];
-    const BTable dst = r.spin == 0 ? tu : td;
-    const int64_t du = tu.dim, dd = td.dim, nel = r.d;
+    for (int i = threadIdx.x; i < 4 * 64; i += blockDim.x) g.prev[i >> 6][i & 63] = make_double2(0.0, 0.0);
+    const BTable tu = tabs[r0.tu], td = tabs[r0.td], src = tabs[r0.src];
+    const BTable dst = r0.spin == 0 ? tu : td;
+    const int64_t dd = td.dim, nel = r0.d;
     const int64_t dd_s = tabs[c.t_dn].dim;
     const uint32_t lomask = (1u << src.split) - 1u;
-    const int create = r.part == 0;
-    const int extra = r.spin == 1 ? (c.n_up & 1) : 0;
-    double s2 = 0.0, z1 = 0.0, z2 = 0.0;
+    const int create = r0.part == 0;
+    const int extra = r0.spin == 1 ? (c.n_up & 1) : 0;
+    int si[4], sj[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      si[q] = q < m ? R[rid[q]].i : -1;
+      sj[q] = q < m ? R[rid[q]].j : -1;
+    }
+    Q4<T>* X = reinterpret_cast<Q4<T>*>(ws);
+    Q4<T>* P = X + w.maxd;
+    double s2[4] = {0.0, 0.0, 0.0, 0.0};
     __syncthreads();
-    // phi = (c_i [+ c_j])^(+) W in the target sector (pull form, sign of Eq. basis)
+    // phi_q = (c_i [+ c_j])^(+) Omega for every run q in the target sector (pull form, sign of
+    // Eq. basis)
     for (int64_t idx = threadIdx.x; idx < nel; idx += blockDim.x) {
       const int64_t u = idx / dd, d = idx - u * dd;
-      const uint32_t bt = r.spin == 0 ? dst.basis[u] : dst.basis[d];
-      double acc = 0.0;
-      for (int k = 0; k < 2; ++k) {
-        const int site = k == 0 ? r.i : r.j;
-        if (site < 0) continue;
-        const uint32_t bit = 1u << site;
-        if (create ? !(bt & bit) : (bt & bit)) continue;
-        const uint32_t sb = bt ^ bit;
-        const int64_t rr = src.rank_lo[sb & lomask] + src.rank_hi[sb >> src.split];
-        const int neg = (__popc(bt & (bit - 1u)) + extra) & 1;
-        const double v = r.spin == 0 ? c.omega[rr * dd_s + d] : c.omega[u * dd_s + rr];
-        acc += neg ? -v : v;
+      const uint32_t bt = r0.spin == 0 ? dst.basis[u] : dst.basis[d];
+      Q4<T> ph;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        double acc = 0.0;
+        for (int k = 0; k < 2; ++k) {
+          const int site = k == 0 ? si[q] : sj[q];
+          if (site < 0) continue;
+          const uint32_t bit = 1u << site;
+          if (create ? !(bt & bit) : (bt & bit)) continue;
+          const uint32_t sb = bt ^ bit;
+          const int64_t rr = src.rank_lo[sb & lomask] + src.rank_hi[sb >> src.split];
+          const int neg = (__popc(bt & (bit - 1u)) + extra) & 1;
+          const double v = r0.spin == 0 ? c.omega[rr * dd_s + d] : c.omega[u * dd_s + rr];
+          acc += neg ? -v : v;
+        }
+        ph.v[q] = (T)acc;
+        s2[q] += acc * acc;
       }
-      V0[idx] = (T)acc;
-      V1[idx] = T(0);
-      s2 += acc * acc;
+      X[idx] = ph;
+      P[idx] = Q4<T>{};
     }
-    bred3(s2, z1, z2, g.bs);
-    const double b0 = sqrt(s2);
-    int steps = 0;
-    if (s2 > 1e-28) {
-      const T f = (T)(1.0 / b0);
-      for (int64_t idx = threadIdx.x; idx < nel; idx += blockDim.x) V0[idx] *= f;
+    {
+      double v4[4] = {s2[0], s2[1], s2[2], s2[3]};
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        for (int o = 16; o > 0; o >>= 1) v4[q] += __shfl_down_sync(0xffffffffu, v4[q], o);
+      const int wi = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
       __syncthreads();
-      T* X = V0;
-      T* P = V1;
-      double bprev = 0.0;
-      int next_check = 32, hits = 0;
-      const double sgn = create ? -1.0 : 1.0;
-      for (int k = 0; k < r.mmax; ++k) {
-        double sxw, sww, sxx;
-        block_hx<T>(tu, td, sval_of<T>(g), sU_of<T>(g), c.hp.umask, (T)c.hp.u0, c.hp.uniform_u != 0, X, P, (T)bprev,
-                    mode, sxw, sww, sxx, g.bs);
+      if (l == 0)
+        for (int q = 0; q < 4; ++q) g.red12[q][wi] = v4[q];
+      __syncthreads();
+      if (threadIdx.x < 4) {
+        double t = 0.0;
+        for (int k = 0; k < nw; ++k) t += g.red12[threadIdx.x][k];
+        g.bcast12[threadIdx.x] = t;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < 4; ++q) s2[q] = g.bcast12[q];
+      __syncthreads();
+    }
+    bool active[4];
+    int steps[4], next_check[4], hits[4];
+    double bprev[4];
+    T f[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      active[q] = q < m && s2[q] > 1e-28;
+      f[q] = active[q] ? (T)(1.0 / sqrt(s2[q])) : T(0);
+      steps[q] = 0;
+      next_check[q] = 32;
+      hits[q] = 0;
+      bprev[q] = 0.0;
+    }
+    for (int64_t idx = threadIdx.x; idx < nel; idx += blockDim.x) {
+      Q4<T> x = X[idx];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) x.v[q] *= f[q];
+      X[idx] = x;
+    }
+    __syncthreads();
+    const double sgn = create ? -1.0 : 1.0;
+    for (int k = 0; k < r0.mmax && (active[0] || active[1] || active[2] || active[3]); ++k) {
+      T bc[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) bc[q] = (T)bprev[q];
+      double sums[12];
+      block_hx4<T>(tu, td, sval_of<T>(g), sU_of<T>(g), c.hp.umask, (T)c.hp.u0, c.hp.uniform_u != 0, X, P, bc, mode,
+                   sums, g.red12, g.bcast12);
+      T aT[4], ibT[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        aT[q] = T(0);
+        ibT[q] = T(0);
+        if (!active[q]) continue;
+        const double sxw = sums[3 * q], sww = sums[3 * q + 1], sxx = sums[3 * q + 2];
         const double alpha = sxx > 0.0 ? sxw / sxx : 0.0;
         const double b2 = sxx > 0.0 ? sww - sxw * sxw / sxx : 0.0;
         const double bn = b2 > 0.0 ? sqrt(b2) : 0.0;
         if (threadIdx.x == 0) {
-          r.alpha[k] = alpha;
-          r.beta[k + 1] = bn;
+          R[rid[q]].alpha[k] = alpha;
+          R[rid[q]].beta[k + 1] = bn;
         }
-        steps = k + 1;
-        if (!(bn > 1e-10)) break;
-        const T aT = (T)alpha, ibT = (T)(1.0 / bn);
-        for (int64_t idx = threadIdx.x; idx < nel; idx += blockDim.x) P[idx] = (P[idx] - aT * X[idx]) * ibT;
-        bprev = bn;
-        T* t = X;
-        X = P;
-        P = t;
+        steps[q] = k + 1;
+        if (!(bn > 1e-10)) {
+          active[q] = false;
+          bprev[q] = 0.0;
+          continue;
+        }
+        aT[q] = (T)alpha;
+        ibT[q] = (T)(1.0 / bn);
+        bprev[q] = bn;
+      }
+      for (int64_t idx = threadIdx.x; idx < nel; idx += blockDim.x) {
+        const Q4<T> x = X[idx];
+        Q4<T> pv = P[idx];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) pv.v[q] = (pv.v[q] - aT[q] * x.v[q]) * ibT[q];
+        P[idx] = pv;
+      }
+      Q4<T>* t = X;
+      X = P;
+      P = t;
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (!active[q] || steps[q] != next_check[q]) continue;
+        // the continued fraction of run q on every zstride-th frequency, against its last check
+        if (threadIdx.x == 0) g.maxdiff = 0.0;
         __syncthreads();
-        if (steps == next_check) {
-          // the continued fraction on every zstride-th frequency, compared with the last check
-          if (threadIdx.x == 0) g.maxdiff = 0.0;
-          __syncthreads();
-          double mx = 0.0;
-          for (int q = threadIdx.x; q < nzs; q += blockDim.x) {
-            const double2 gv = b_cf_eval(r.alpha, r.beta, steps, s2, z[q * zstride], c.E0, sgn);
-            mx = fmax(mx, hypot(gv.x - g.prev[q].x, gv.y - g.prev[q].y));
-            g.prev[q] = gv;
-          }
-          for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
-          if ((threadIdx.x & 31) == 0) atomicMax((unsigned long long*)&g.maxdiff, __double_as_longlong(mx));
-          __syncthreads();
-          hits = g.maxdiff < tol ? hits + 1 : 0;
-          if (hits >= 2) break;
-          next_check = steps + max(32, steps / 8);
+        const BRun& rq = R[rid[q]];
+        double mx = 0.0;
+        for (int qq = threadIdx.x; qq < nzs; qq += blockDim.x) {
+          const double2 gv = b_cf_eval(rq.alpha, rq.beta, steps[q], s2[q], z[qq * zstride], c.E0, sgn);
+          mx = fmax(mx, hypot(gv.x - g.prev[q][qq].x, gv.y - g.prev[q][qq].y));
+          g.prev[q][qq] = gv;
         }
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        if ((threadIdx.x & 31) == 0) atomicMax((unsigned long long*)&g.maxdiff, __double_as_longlong(mx));
+        __syncthreads();
+        hits[q] = g.maxdiff < tol ? hits[q] + 1 : 0;
+        if (hits[q] >= 2) active[q] = false;
+        next_check[q] = steps[q] + max(32, steps[q] / 8);
+        __syncthreads();
       }
     }
-    if (threadIdx.x == 0) {
-      r.b0sq = s2;
-      r.nsteps = steps;
-    }
+    if (threadIdx.x == 0)
+      for (int q = 0; q < m; ++q) {
+        R[rid[q]].b0sq = s2[q];
+        R[rid[q]].nsteps = steps[q];
+      }
     __syncthreads();
   }
   // warp phase
@@ -912,8 +1088,9 @@ struct BatchResult {
 // (prof: time each launch with the profiler; off while the launches are captured into a graph)
 template <typename T>
 static void run_batch_kernels(int threads, int mode, BCluster* C, const int* corder, int nclu, const BTable* tabs,
-                              BRun* R, const int* rorder, int nblock_runs, int nruns, int* queues, const BWork& w, int blocks,
-                              const double2* z, int nz, double tol, bool do_gf, cudaStream_t s, bool prof = true) {
+                              BRun* R, const int* rorder, int nblock_runs, int nruns, const int4* groups, int ngroups,
+                              int* queues, const BWork& w, int blocks, const double2* z, int nz, double tol, bool do_gf,
+                              cudaStream_t s, bool prof = true) {
   ED_CUDA(cudaMemsetAsync(queues, 0, 3 * sizeof(int), s));
   {
     std::unique_ptr<ProfScope> ps_(prof ? new ProfScope(K_BATCH, s, 0.0) : nullptr);
@@ -922,7 +1099,8 @@ static void run_batch_kernels(int threads, int mode, BCluster* C, const int* cor
   }
   if (do_gf && nruns > 0) {
     std::unique_ptr<ProfScope> ps_(prof ? new ProfScope(K_BATCH, s, 0.0) : nullptr);
-    k_batch_cf<T><<<blocks, threads, 0, s>>>(R, rorder, nblock_runs, nruns, C, tabs, queues + 1, w, z, nz, tol, mode);
+    k_batch_cf<T><<<blocks, threads, 0, s>>>(R, rorder, nblock_runs, nruns, groups, ngroups, C, tabs, queues + 1, w, z,
+                                             nz, tol, mode);
     ED_CHECK_LAUNCH();
   }
 }
@@ -993,7 +1171,9 @@ size_t batch_device_bytes(const ed_cluster_desc* descs, int n, int precision, in
   bytes += r256((size_t)std::max<int64_t>(nruns, 1) * std::max(nz, 0) * 16);
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(n + nruns, (int64_t)sms * 4));
   const int64_t wmax = std::min<int64_t>(maxd, kWarpRunMax);
-  const size_t stride = std::max<size_t>(((3 * maxd * es + 255) / 256) * 256 + 4 * maxd * 8, (size_t)16 * 2 * wmax * es) + 256;
+  const size_t stride = std::max<size_t>(std::max<size_t>(((3 * maxd * es + 255) / 256) * 256 + 4 * maxd * 8,
+                                                          (size_t)16 * 2 * wmax * es),
+                                         (size_t)8 * maxd * es) + 256;
   return bytes + (size_t)blocks * stride + (size_t(1) << 20);
 }
 
@@ -1146,6 +1326,20 @@ void batch_solve(const ed_cluster_desc* descs, int n, int precision, const doubl
   std::stable_sort(rorder.begin(), rorder.end(), [&](int a, int b) { return R[a].d > R[b].d; });
   int nblock_runs = 0;  // runs done by whole blocks (the rest by single warps)
   while (nblock_runs < nruns && R[rorder[nblock_runs]].d > kWarpRunMax) ++nblock_runs;
+  // block-level runs in groups of up to four of one (cluster, spin, part): one target sector,
+  // advanced together (interleaved vectors); the largest-first order keeps each group contiguous
+  std::vector<int4> grp;
+  for (int i = 0; i < nblock_runs;) {
+    int g4[4] = {-1, -1, -1, -1};
+    const BRun& a = R[rorder[i]];
+    for (int k = 0; k < 4 && i < nblock_runs; ++k) {
+      const BRun& b = R[rorder[i]];
+      if (k > 0 && (b.cluster != a.cluster || b.spin != a.spin || b.part != a.part)) break;
+      g4[k] = rorder[i++];
+    }
+    grp.push_back(make_int4(g4[0], g4[1], g4[2], g4[3]));
+  }
+  const int ngroups = (int)grp.size();
   // ---- device descriptors
   DevBuf<BTable> dT(T.size());
   DevBuf<BPair> dP(std::max<size_t>(pairs.size(), 1));
@@ -1154,6 +1348,8 @@ void batch_solve(const ed_cluster_desc* descs, int n, int precision, const doubl
   DevBuf<BCluster> dC(n);
   DevBuf<BRun> dR(std::max(nruns, 1));
   DevBuf<double2> dz(std::max(nz, 1));
+  DevBuf<int4> dG(std::max(ngroups, 1));
+  if (ngroups) ED_CUDA(cudaMemcpyAsync(dG.p, grp.data(), ngroups * sizeof(int4), cudaMemcpyHostToDevice, s));
   ED_CUDA(cudaMemcpyAsync(dT.p, T.data(), T.size() * sizeof(BTable), cudaMemcpyHostToDevice, s));
   if (!pairs.empty()) ED_CUDA(cudaMemcpyAsync(dP.p, pairs.data(), pairs.size() * sizeof(BPair), cudaMemcpyHostToDevice, s));
   ED_CUDA(cudaMemcpyAsync(dPoff.p, pair_off.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
@@ -1189,7 +1385,10 @@ void batch_solve(const ed_cluster_desc* descs, int n, int precision, const doubl
   // per block: 3 + 4 vectors of the largest sector, or 2 vectors per warp (at most 16) of the
   // largest warp-level run, whichever is more
   const int64_t wmax = std::min<int64_t>(maxd, kWarpRunMax);
-  const size_t stride = std::max<size_t>(((3 * maxd * es + 255) / 256) * 256 + 4 * maxd * 8, (size_t)16 * 2 * wmax * es) + 256;
+  // (or two sets of four interleaved vectors of a group of block-level continued fractions)
+  const size_t stride = std::max<size_t>(std::max<size_t>(((3 * maxd * es + 255) / 256) * 256 + 4 * maxd * 8,
+                                                          (size_t)16 * 2 * wmax * es),
+                                         (size_t)8 * maxd * es) + 256;
   int dev = 0, sms = 0;
   ED_CUDA(cudaGetDevice(&dev));
   ED_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1227,10 +1426,10 @@ void batch_solve(const ed_cluster_desc* descs, int n, int precision, const doubl
       ED_CUDA(cudaMemcpyAsync(dC.p, C.data(), n * sizeof(BCluster), cudaMemcpyHostToDevice, s));
       ED_CUDA(cudaEventRecord(e0, s));
       if (precision == ED_FP64)
-        run_batch_kernels<double>(cd.first, cd.second, dC.p, dCo.p, sample, dT.p, dR.p, dRo.p, 0, 0, dQ.p, w, blocks,
+        run_batch_kernels<double>(cd.first, cd.second, dC.p, dCo.p, sample, dT.p, dR.p, dRo.p, 0, 0, nullptr, 0, dQ.p, w, blocks,
                                   dz.p, nz, 0.0, false, s);
       else
-        run_batch_kernels<float>(cd.first, cd.second, dC.p, dCo.p, sample, dT.p, dR.p, dRo.p, 0, 0, dQ.p, w, blocks,
+        run_batch_kernels<float>(cd.first, cd.second, dC.p, dCo.p, sample, dT.p, dR.p, dRo.p, 0, 0, nullptr, 0, dQ.p, w, blocks,
                                  dz.p, nz, 0.0, false, s);
       ED_CUDA(cudaEventRecord(e1, s));
       ED_CUDA(cudaEventSynchronize(e1));
@@ -1260,10 +1459,10 @@ void batch_solve(const ed_cluster_desc* descs, int n, int precision, const doubl
     CaptureGuard cg{s};
     ED_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     if (precision == ED_FP64)
-      run_batch_kernels<double>(cfg.first, cfg.second, dC.p, dCo.p, n, dT.p, dR.p, dRo.p, nblock_runs, nruns, dQ.p, w, blocks,
+      run_batch_kernels<double>(cfg.first, cfg.second, dC.p, dCo.p, n, dT.p, dR.p, dRo.p, nblock_runs, nruns, dG.p, ngroups, dQ.p, w, blocks,
                                 dz.p, nz, gtol, do_gf, s, false);
     else
-      run_batch_kernels<float>(cfg.first, cfg.second, dC.p, dCo.p, n, dT.p, dR.p, dRo.p, nblock_runs, nruns, dQ.p, w, blocks,
+      run_batch_kernels<float>(cfg.first, cfg.second, dC.p, dCo.p, n, dT.p, dR.p, dRo.p, nblock_runs, nruns, dG.p, ngroups, dQ.p, w, blocks,
                                dz.p, nz, gtol, do_gf, s, false);
     if (gf) {
       k_bcf_eval<<<dim3((nz + 255) / 256, std::min(nruns, 32768)), 256, 0, s>>>(dR.p, nruns, dC.p, dz.p, nz, Gk);

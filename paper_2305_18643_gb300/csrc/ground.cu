@@ -157,25 +157,55 @@ __global__ void k_ritz_sum(const T* const* __restrict__ vecs, int m, const doubl
     for (int64_t d0 = (int64_t)threadIdx.x * VN; d0 < dd; d0 += (int64_t)blockDim.x * VN) {
       const int64_t o = u * ld + d0;
       double s[VN];
+      if constexpr (sizeof(T) == 4) {
+        // FP32 vectors: FP32 products with Kahan-compensated FP32 sums (FP64 runs at a small
+        // fraction of the FP32 rate here; the products' rounding, 2^-24 relative, is the order
+        // of the vectors' own FP32 storage, and the FP64 refinement that follows removes both)
+        float sf[VN], cf[VN];
 #pragma unroll
-      for (int j = 0; j < VN; ++j) s[j] = 0.0;
-      int n = 0;
-      for (; n + 4 <= m; n += 4) {
-        V a[4];
+        for (int j = 0; j < VN; ++j) sf[j] = cf[j] = 0.f;
+        auto add = [&](float c, const V& a) {
+          const float* e = reinterpret_cast<const float*>(&a);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) a[q] = __ldg(reinterpret_cast<const V*>(sp[n + q] + o));
+          for (int j = 0; j < VN; ++j) {
+            const float y = fmaf(c, e[j], -cf[j]);
+            const float t = sf[j] + y;
+            cf[j] = (t - sf[j]) - y;
+            sf[j] = t;
+          }
+        };
+        int n = 0;
+        for (; n + 4 <= m; n += 4) {
+          V a[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const T* e = reinterpret_cast<const T*>(&a[q]);
+          for (int q = 0; q < 4; ++q) a[q] = __ldg(reinterpret_cast<const V*>(sp[n + q] + o));
 #pragma unroll
-          for (int j = 0; j < VN; ++j) s[j] += sc[n + q] * (double)e[j];
+          for (int q = 0; q < 4; ++q) add((float)sc[n + q], a[q]);
         }
-      }
-      for (; n < m; ++n) {
-        const V a = __ldg(reinterpret_cast<const V*>(sp[n] + o));
-        const T* e = reinterpret_cast<const T*>(&a);
+        for (; n < m; ++n) add((float)sc[n], __ldg(reinterpret_cast<const V*>(sp[n] + o)));
 #pragma unroll
-        for (int j = 0; j < VN; ++j) s[j] += sc[n] * (double)e[j];
+        for (int j = 0; j < VN; ++j) s[j] = (double)sf[j] - (double)cf[j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < VN; ++j) s[j] = 0.0;
+        int n = 0;
+        for (; n + 4 <= m; n += 4) {
+          V a[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) a[q] = __ldg(reinterpret_cast<const V*>(sp[n + q] + o));
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const T* e = reinterpret_cast<const T*>(&a[q]);
+#pragma unroll
+            for (int j = 0; j < VN; ++j) s[j] += sc[n + q] * (double)e[j];
+          }
+        }
+        for (; n < m; ++n) {
+          const V a = __ldg(reinterpret_cast<const V*>(sp[n] + o));
+          const T* e = reinterpret_cast<const T*>(&a);
+#pragma unroll
+          for (int j = 0; j < VN; ++j) s[j] += sc[n] * (double)e[j];
+        }
       }
 #pragma unroll
       for (int j = 0; j < VN; ++j) {
@@ -398,10 +428,25 @@ GroundResult run_ground_state(ed_cluster& c, int dtype, double tol, int max_iter
     // FP64 polish: normalize omega, Rayleigh quotient E and explicit residual r = H omega - E omega
     // (left in y64), all with the FP64 operator.
     double E = 0.0, res_abs = 0.0;
+    // H omega through rows padded to ld (zero padding), so that large sectors take the two-pass
+    // kernels (the contiguous layout would force the one-pass kernel, ~2x slower in FP64)
+    DevBuf<double> om_pad, y_pad;
+    if (ld != dd) {
+      om_pad.alloc((size_t)du * ld);
+      y_pad.alloc((size_t)du * ld);
+      ED_CUDA(cudaMemsetAsync(om_pad.p, 0, (size_t)du * ld * sizeof(double), s));
+      ED_CUDA(cudaMemsetAsync(y_pad.p, 0, (size_t)du * ld * sizeof(double), s));
+    }
     auto polish = [&]() {
       launch_dot(ED_FP64, c.omega.p, ED_FP64, c.omega.p, du, dd, dd, part.p, nblk + 8, scal.p + 1, s);
       axpby_inv_sqrt(ED_FP64, c.omega.p, scal.p + 1, du, dd, dd, s);
-      launch_hpsi(svc, c.hp, ED_FP64, c.omega.p, y64.p, s);
+      if (ld != dd) {
+        launch_copy_ld(ED_FP64, om_pad.p, ld, ED_FP64, c.omega.p, dd, nullptr, du, dd, s);
+        launch_hpsi(sv, c.hp, ED_FP64, om_pad.p, y_pad.p, s);
+        launch_copy_ld(ED_FP64, y64.p, dd, ED_FP64, y_pad.p, ld, nullptr, du, dd, s);
+      } else {
+        launch_hpsi(svc, c.hp, ED_FP64, c.omega.p, y64.p, s);
+      }
       launch_dot(ED_FP64, c.omega.p, ED_FP64, y64.p, du, dd, dd, part.p, nblk + 8, scal.p + 2, s);
       axpy_neg(y64.p, scal.p + 2, c.omega.p, dim, s);  // y <- y - E omega
       launch_dot(ED_FP64, y64.p, ED_FP64, y64.p, du, dd, dd, part.p, nblk + 8, scal.p + 3, s);
