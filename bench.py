@@ -53,6 +53,16 @@ WORKLOADS = {
     "batch": (lambda instance=0: W.batched_family(512, instance=instance),
               "512 seeded clusters of 4-12 orbitals (chains, 2-leg ladders, 2x2 plaquettes + 0-8 bath), "
               "|t| ~ U[0.5,1.5], U ~ U[2,10], mu = U/2, random fillings; both spins", "fp32", "cf", 512),
+    "sym": (lambda instance=0: W.open_3x4_c2v()[0],
+            "3x4 open Hubbard, t=-1, U=4, mu=2, N_up=N_dn=6 (d=853,776) in its C2v irrep sectors (213,248-213,840 "
+            "states); ground state + G of the 12 sites on 64 Matsubara frequencies (beta=50)", "fp64", "cf", 64),
+    "lattice": (W.cdmft_2x2_bath,
+                "lattice steps fed by the 2x2 plaquette + 8 bath impurity (U=8, mu=4, N_up=N_dn=6): CPT of the "
+                "square lattice (t=-1, t'=0.3) periodized on a 64x64 k grid x 256 Matsubara frequencies, CDMFT "
+                "target on a 16x16 reduced zone, distance + gradient for 64 trial baths", "fp64", "cf", 256),
+    "davidson": (W.cdmft_2x2_bath,
+                 "2x2 plaquette + 8 bath, U=8, mu=4, N_up=N_dn=6 (d=924^2): the 4 lowest states (block Davidson) "
+                 "and the mixed-state G at T=0.05 on 256 Matsubara frequencies (beta=50), FP64", "fp64", "cf", 256),
     "served": (None, "stream of solve requests: open 2xW clusters of 8/10/12/14 orbitals (uniform), t=-1, "
                "t'=+-0.3 seeded per bond, U=8, mu=4, half filling; ground state + G on 2048 Matsubara "
                "frequencies (beta=50); continued fractions up to 10 orbitals, band Lanczos from 12",
@@ -219,6 +229,12 @@ def run_ours(args, rank, world, local_rank):
         return run_served(args, rank, world, local_rank, torch, ed)
     if args.workload == "hpsi":
         return run_hpsi(args, rank, world, local_rank, torch, ed)
+    if args.workload == "sym":
+        return run_sym(args, rank, world, local_rank, torch, ed)
+    if args.workload == "lattice":
+        return run_lattice(args, rank, world, local_rank, torch, ed)
+    if args.workload == "davidson":
+        return run_davidson(args, rank, world, local_rank, torch, ed)
     c = gen(instance=rank)
     ns = c["t"].shape[0]
     axis_name = AXIS.get(args.workload, "real")
@@ -409,6 +425,226 @@ def run_hpsi(args, rank, world, local_rank, torch, ed):
                      "traffic": ncu_traffic("hpsi.cu", "band_hpsi_4x4.md"),
                      "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
                      "launches": n_l, "avg_launch_ms": ms_l / max(n_l, 1), "alg_bytes_per_launch": by_l / max(n_l, 1)},
+        "e2e": None,
+    }
+
+
+def run_sym(args, rank, world, local_rank, torch, ed):
+    """Symmetrized sectors (Sec. 4.5-4.6): a step is one solve of the 3x4 cluster in the C2v irrep
+    that holds its ground state (basis, stored matrix, FP64 Lanczos ground state, G of the 12
+    sites by continued fractions in the N +- 1 product irreps); value = solves/s.  Beside it, the
+    same solve on the unsymmetrized sectors (ed_ground_state + ed_green, FP64 continued fractions)
+    and the largest difference of the two G.  Roofline: the stored-matrix product (12 bytes per
+    entry + 16 per row) over its profiled time; the irrep matrices (~46 MB) sit in L2, so the rate
+    is an effective one."""
+    gen, label, prec_d, gf_d, nfreq = WORKLOADS["sym"]
+    c, gens = W.open_3x4_c2v()
+    ns = c["t"].shape[0]
+    omega = W.matsubara_grid(nfreq, BETA)
+    h = ed.ed_cluster_create(c, precision=ed.ED_FP64, gf_method=ed.ED_GF_CF, seed=1234, tol=1e-12)
+    # the irrep of the ground state (lowest irrep energy), found once before timing
+    best = None
+    for ir in ((1, 1), (1, -1), (-1, 1), (-1, -1)):
+        s = ed.ed_sym_create(h, np.array(gens), ir)
+        try:
+            E = ed.ed_sym_ground_state(s)[0]
+        finally:
+            ed.ed_sym_destroy(s)
+        if best is None or E < best[1]:
+            best = (ir, E)
+    info = {}
+
+    def solve():
+        s = ed.ed_sym_create(h, np.array(gens), best[0])
+        try:
+            E, r, it, st = ed.ed_sym_ground_state(s)
+            info.update(E0=E, residual=r, iters=it, dim=ed.ed_sym_info(s)[0], nnz=ed.ed_sym_info(s)[1])
+            info["G"] = ed.ed_sym_green(s, omega, ns, axis=ed.ED_AXIS_MATSUBARA)
+        finally:
+            ed.ed_sym_destroy(s)
+
+    for _ in range(args.warmup):
+        solve()
+    torch.cuda.synchronize()
+    ed.ed_profile_enable(1)
+    l0 = ed.ed_launch_count()
+    with ClockSampler(local_rank) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            solve()
+        e1.record()
+        torch.cuda.synchronize()
+    launches = ed.ed_launch_count() - l0
+    ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
+    n_l, ms_l, by_l = ed.ed_profile_read(ed.ED_K_HPSI)
+    ed.ed_profile_enable(0)
+    # the same solve on the unsymmetrized sectors
+    e0.record()
+    h2 = ed.ed_cluster_create(c, precision=ed.ED_FP64, gf_method=ed.ED_GF_CF, seed=1234, tol=1e-12)
+    try:
+        st, E_full, r_full, _ = ed.ed_ground_state(h2)
+        G_full = ed.ed_green(h2, omega, 0.0, ns, axis=ed.ED_AXIS_MATSUBARA)[1]
+    finally:
+        ed.ed_cluster_destroy(h2)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_full = e0.elapsed_time(e1)
+    ed.ed_cluster_destroy(h)
+    peak, peak_kind = measured_peak_hbm()
+    ach = (by_l / 1e9) / (ms_l / 1e3) if ms_l > 0 else None
+    return {
+        "metric": "ED solves/s in the ground state's irrep sectors (Sec. 4.5-4.6)",
+        "value": whole_job_rate(args.steps, world, ms), "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (fixed cluster parameters)",
+        "config": {"workload": "sym: " + label, "irrep_generator_signs": list(best[0]), "irrep_dim": info["dim"],
+                   "stored_entries": info["nnz"], "n_freq": nfreq, "axis": "matsubara", "beta": BETA,
+                   "l2": "irrep matrices L2-resident (%.0f MB)" % (info["nnz"] * 12 / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "clocks": clk.summary(), "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "kernel": "k_sym_spmv (stored irrep matrix times a vector)", "achieved": ach,
+                     "peak": peak, "unit": "GB/s", "frac": (ach / peak) if ach else None, "traffic": None,
+                     "peak_source": peak_kind, "launches": n_l, "avg_launch_ms": ms_l / max(n_l, 1),
+                     "alg_bytes_per_launch": by_l / max(n_l, 1),
+                     "note": "effective rate: the matrix and vectors of an irrep fit in L2"},
+        "solve": {"E0": info["E0"], "residual": info["residual"], "gs_iters": info["iters"]},
+        "unsymmetrized_fp64": {"value": 1e3 / ms_full, "unit": "solves/s", "ms": ms_full, "E0": E_full,
+                               "E0_minus_irrep": E_full - info["E0"],
+                               "G_max_abs_diff": float(np.max(np.abs(G_full - info["G"]))),
+                               "how": "ed_cluster_create, ed_ground_state, ed_green (continued fractions) on the "
+                                      "853,776-state sector and its N +- 1 sectors, FP64"},
+        "speedup_vs_unsymmetrized": (1e3 / (ms / args.steps)) / (1e3 / ms_full),
+        "e2e": None,
+    }
+
+
+def run_lattice(args, rank, world, local_rank, torch, ed):
+    """The lattice steps that consume the solver's G (Secs. 3 and 6): the impurity's G_c on the
+    Matsubara grid is computed once (untimed); a step is CPT periodized on a 64 x 64 grid of wave
+    vectors (Eqs. CPT1, CPT3, with the bath's Gamma), the CDMFT target on a 16 x 16 reduced zone
+    and the distance with its gradient for 64 trial baths.  value = CPT (k, omega) points per
+    second of the whole step; the kernels are FP64 complex arithmetic on small matrices."""
+    gen, label, prec_d, gf_d, nfreq = WORKLOADS["lattice"]
+    c = gen(instance=rank)
+    ns = c["t"].shape[0]
+    om = W.matsubara_grid(nfreq, BETA)
+    z = 1j * om
+    h = ed.ed_cluster_create(c, precision=ed.ED_FP64, gf_method=ed.ED_GF_CF, seed=1234)
+    try:
+        Gc = ed.ed_green(h, om, 0.0, ns, axis=ed.ED_AXIS_MATSUBARA)[1]
+    finally:
+        ed.ed_cluster_destroy(h)
+    lat = W.square_superlattice(2, 2, t=-1.0, tp=0.3)
+    Gam = ed.ed_hybridization(c["theta"], c["eps"], z)
+    k_cpt = W.reduced_zone(lat["E"], (64, 64))
+    k_cdmft = W.reduced_zone(lat["E"], (16, 16))
+    rng = np.random.default_rng(7 + rank)
+    nb = c["eps"].size
+    th = np.asarray(c["theta"])[None] * (1.0 + 0.05 * rng.standard_normal((64, ns, nb)))
+    ep = np.asarray(c["eps"])[None] + 0.05 * rng.standard_normal((64, nb))
+    wts = np.ones(nfreq) / nfreq
+
+    def step():
+        ed.ed_cpt_green(lat, Gc, k_cpt, mode=ed.ED_CPT_PERIODIZED, Gamma=Gam)
+        A = ed.ed_cdmft_target(lat, Gc, k_cdmft, Gamma=Gam)
+        ed.ed_cdmft_distance(th, ep, z, wts, A, grad=True)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ed.ed_profile_enable(1)
+    l0 = ed.ed_launch_count()
+    with ClockSampler(local_rank) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+    launches = ed.ed_launch_count() - l0
+    ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
+    n_l, ms_l, by_l = ed.ed_profile_read(ed.ED_K_LATTICE)
+    ed.ed_profile_enable(0)
+    npts = len(k_cpt) * nfreq
+    return {
+        "metric": "CPT (k, omega) points/s of the lattice step (CPT + CDMFT target + distance)",
+        "value": whole_job_rate(args.steps * npts, world, ms), "unit": "points/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64 complex", "data": "synthetic (seeded bath)",
+        "config": {"workload": "lattice: " + label, "cpt_points": npts, "cdmft_k": len(k_cdmft),
+                   "trial_baths": 64, "n_freq": nfreq, "beta": BETA,
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "clocks": clk.summary(), "gpu_launches": int(launches),
+        "roofline": None,
+        "roofline_note": "FP64 complex Gauss-Jordan on 4x4 matrices (warp per matrix): bound by FP64 "
+                         "arithmetic and latency, not HBM; no measured FP64 peak is committed, so no fraction "
+                         "is quoted",
+        "kernels_ms": {"lattice": round(ms_l, 3), "launches": n_l},
+        "e2e": None,
+    }
+
+
+def run_davidson(args, rank, world, local_rank, torch, ed):
+    """Several low states (Sec. 4.2; the Davidson_states and temperature options of Sec. 9): a step
+    is one solve of the impurity cluster for its 4 lowest states by block Davidson plus the
+    mixed-state G at T = 0.05 (continued fractions from each state); value = solves/s.  Beside it,
+    the single-state solve (Lanczos ground state + G) of the same cluster."""
+    gen, label, prec_d, gf_d, nfreq = WORKLOADS["davidson"]
+    c = gen(instance=rank)
+    ns = c["t"].shape[0]
+    om = W.matsubara_grid(nfreq, BETA)
+    info = {}
+
+    def solve(states):
+        h = ed.ed_cluster_create(c, precision=ed.ED_FP64, gf_method=ed.ED_GF_CF, seed=1234)
+        try:
+            if states > 1:
+                ed.ed_set_option(h, ed.ED_OPT_DAVIDSON_STATES, states)
+                ed.ed_set_option(h, ed.ED_OPT_TEMPERATURE, 0.05)
+            st, E0, r, it = ed.ed_ground_state(h)
+            info.update(E0=E0, residual=r, iters=it, status=st)
+            info["G"] = ed.ed_green(h, om, 0.0, ns, axis=ed.ED_AXIS_MATSUBARA)[1]
+            if states > 1:
+                E, wts = ed.ed_low_states(h)
+                info.update(E=E.tolist(), weights=wts.tolist())
+        finally:
+            ed.ed_cluster_destroy(h)
+
+    for _ in range(args.warmup):
+        solve(4)
+    torch.cuda.synchronize()
+    l0 = ed.ed_launch_count()
+    with ClockSampler(local_rank) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            solve(4)
+        e1.record()
+        torch.cuda.synchronize()
+    launches = ed.ed_launch_count() - l0
+    ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
+    mixed = dict(info)
+    e0.record()
+    solve(1)
+    e1.record()
+    torch.cuda.synchronize()
+    ms1 = e0.elapsed_time(e1)
+    return {
+        "metric": "ED solves/s with 4 low states and the mixed-state G (block Davidson)",
+        "value": whole_job_rate(args.steps, world, ms), "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded bath)",
+        "config": {"workload": "davidson: " + label, "states": 4, "temperature": 0.05, "n_freq": nfreq,
+                   "beta": BETA, "parallelism": "replicas" if world > 1 else "single GPU"},
+        "clocks": clk.summary(), "gpu_launches": int(launches),
+        "roofline": None,
+        "roofline_note": "the FP64 H.psi of the Davidson basis is the FP64 path's kernel (FP64-ALU-bound); the "
+                         "sector (6.8 MB per vector) is L2-resident",
+        "solve": {"E": mixed.get("E"), "weights": mixed.get("weights"), "max_residual": mixed["residual"],
+                  "iters": mixed["iters"], "status": mixed["status"]},
+        "single_state": {"value": 1e3 / ms1, "unit": "solves/s", "ms": ms1, "E0": info["E0"],
+                         "how": "ed_ground_state (Lanczos) + ed_green on the same cluster, FP64"},
         "e2e": None,
     }
 

@@ -84,6 +84,17 @@ def plain_2x4(U=4.0):
     return _cluster("2x4 open, U=4, half filling", T, U, U / 2, 4, 4)
 
 
+def open_3x4_c2v(U=4.0):
+    """12-site 3x4 open Hubbard cluster (W = 4, H = 3, s = x + 4 y), t = -1, U = 4, mu = U/2,
+    N_up = N_dn = 6 (d = 853,776): the cluster of Table 1 with an interaction.  Also returns its
+    two mirror generators m_x: x -> 3 - x and m_y: y -> 2 - y (orbital images), whose group C2v
+    leaves H invariant."""
+    T = lattice_hopping(4, 3)
+    mx = [(3 - s % 4) + 4 * (s // 4) for s in range(12)]
+    my = [s % 4 + 4 * (2 - s // 4) for s in range(12)]
+    return _cluster("3x4 open, U=4, half filling", T, U, U / 2, 6, 6), [mx, my]
+
+
 def cdmft_2x2_bath(instance=0):
     """2x2 plaquette (t = -1, t' = +0.3, U = 8, mu = 4) plus 8 bath orbitals, N_up = N_dn = 6.
 
