@@ -257,33 +257,70 @@ __global__ void __launch_bounds__(128) k_sym_rows(const SymDev* __restrict__ Gp,
   }
 }
 
-// ---- y = H x - beta x_prev (x_prev may be NULL), warp per row; per-block partial <x, y>
+// The last block of a launch to finish (a ticket) sums the per-block partials in a fixed order
+// (thread t takes blocks t, t + blockDim.x, ..., then a tree in shared memory) into *out (mode 1:
+// its square root) and resets the ticket, so a reduction needs no second launch.
+__device__ void sym_finish_last(const double* partial, double* out, int mode, unsigned* ticket) {
+  __shared__ bool s_last;
+  __shared__ double sm[kSymThreads];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double t = 0.0;
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) t += __ldcg(partial + b);
+  sm[threadIdx.x] = t;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *out = mode ? sqrt(fmax(sm[0], 0.0)) : sm[0];
+    *ticket = 0u;
+  }
+}
+
+// ---- y = H x - beta x_prev (x_prev may be NULL); per-block partial <x, y>.  Rows hold ~20
+// entries, so a row goes to a group of kSymRowLanes lanes (four rows per warp), each lane taking
+// every kSymRowLanes-th entry, summed by a fixed butterfly.
+constexpr int kSymRowLanes = 8;
+constexpr int kSymRowsPerBlock = kSymThreads / kSymRowLanes;
+
 __global__ void __launch_bounds__(kSymThreads) k_sym_spmv(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                                          const double* __restrict__ val, int64_t dim,
                                                          const double* __restrict__ x, double* __restrict__ y,
                                                          const double* __restrict__ xprev, const double* __restrict__ beta,
-                                                         double* __restrict__ partial) {
-  __shared__ double s_part[kSymThreads / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+                                                         double* __restrict__ partial, unsigned* ticket, double* out) {
+  __shared__ double s_part[kSymRowsPerBlock];
+  const int sub = threadIdx.x & (kSymRowLanes - 1), grp = threadIdx.x / kSymRowLanes;
   const double b = (xprev && beta) ? *beta : 0.0;
   double dot = 0.0;
-  for (int64_t r = (int64_t)blockIdx.x * (kSymThreads / 32) + warp; r < dim; r += (int64_t)gridDim.x * (kSymThreads / 32)) {
+  for (int64_t r0 = (int64_t)blockIdx.x * kSymRowsPerBlock; r0 < dim; r0 += (int64_t)gridDim.x * kSymRowsPerBlock) {
+    const int64_t r = r0 + grp;
     double s = 0.0;
-    for (int64_t k = rowptr[r] + lane; k < rowptr[r + 1]; k += 32) s += val[k] * __ldg(x + col[k]);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (xprev) s -= b * xprev[r];
-    if (lane == 0) {
+    if (r < dim) {
+      const int64_t e = rowptr[r + 1];
+      for (int64_t k = rowptr[r] + sub; k < e; k += kSymRowLanes) s += val[k] * __ldg(x + col[k]);
+    }
+#pragma unroll
+    for (int o = kSymRowLanes / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (r < dim && sub == 0) {
+      if (xprev) s -= b * xprev[r];
       y[r] = s;
       dot += s * x[r];
     }
   }
-  if (lane == 0) s_part[warp] = dot;
+  if (sub == 0) s_part[grp] = dot;
   __syncthreads();
   if (threadIdx.x == 0 && partial) {
     double t = 0.0;
-    for (int w = 0; w < kSymThreads / 32; ++w) t += s_part[w];
+    for (int w = 0; w < kSymRowsPerBlock; ++w) t += s_part[w];
     partial[blockIdx.x] = t;
   }
+  if (ticket) sym_finish_last(partial, out, 0, ticket);
 }
 
 // out = sum of partials in a fixed order (one block); mode 0: out = s, 1: out = sqrt(max(s, 0))
@@ -303,7 +340,8 @@ __global__ void k_sym_finish(const double* __restrict__ partial, int n, double* 
 // w -= a x (a = *alpha, or 0 when alpha is NULL); per-block partial |w|^2
 __global__ void __launch_bounds__(kSymThreads) k_sym_axpy_norm(double* __restrict__ w, const double* __restrict__ x,
                                                               const double* __restrict__ alpha, int64_t dim,
-                                                              double* __restrict__ partial) {
+                                                              double* __restrict__ partial, unsigned* ticket = nullptr,
+                                                              double* out = nullptr) {
   __shared__ double sm[kSymThreads];
   const double a = alpha ? *alpha : 0.0;
   double s = 0.0;
@@ -319,6 +357,7 @@ __global__ void __launch_bounds__(kSymThreads) k_sym_axpy_norm(double* __restric
     __syncthreads();
   }
   if (threadIdx.x == 0) partial[blockIdx.x] = sm[0];
+  if (ticket) sym_finish_last(partial, out, 1, ticket);
 }
 
 // v = w / *norm (written over v); omega += coef * v when omega is given
@@ -526,9 +565,9 @@ static void sym_build(ed_sym& S, const int* perm, cudaStream_t s) {
 
 // y = H x in the symmetrized basis (device vectors of S.dim doubles)
 static void sym_spmv(ed_sym& S, const double* x, double* y, const double* xprev, const double* beta, double* partial,
-                     int nblk, cudaStream_t s) {
+                     int nblk, cudaStream_t s, unsigned* ticket = nullptr, double* out = nullptr) {
   ProfScope ps_(K_HPSI, s, (double)S.nnz * 12.0 + (double)S.dim * 16.0);
-  k_sym_spmv<<<nblk, kSymThreads, 0, s>>>(S.rowptr.p, S.col.p, S.val.p, S.dim, x, y, xprev, beta, partial);
+  k_sym_spmv<<<nblk, kSymThreads, 0, s>>>(S.rowptr.p, S.col.p, S.val.p, S.dim, x, y, xprev, beta, partial, ticket, out);
   ED_CHECK_LAUNCH();
 }
 
@@ -538,9 +577,12 @@ static void sym_ground_state(ed_sym& S, double tol, int max_iter, uint64_t seed)
   const int64_t dim = S.dim;
   if (dim == 0) throw Error(ED_ERR_INVALID, "the irrep has no state in this sector");
   const int M = std::max(2, (int)std::min<int64_t>(max_iter > 0 ? max_iter : 600, dim));
-  const int nb = sym_grid(dim, kSymThreads / 32 * 4), nv = sym_grid(dim, kSymThreads * 4);
+  const int nb = sym_grid(dim, kSymRowsPerBlock), nv = sym_grid(dim, kSymThreads * 4);
   const int np = std::max(nb, nv);
-  DevBuf<double> V0(dim), V1(dim), W(dim), start(dim), alpha(M + 1), beta(M + 2), evals(3), svec(M + 1), part(np);
+  DevBuf<double> V0(dim), V1(dim), W(dim), start(dim), alpha(M + 1), beta(M + 2), evals(3), svec(M + 1), part(np),
+      part2(np);
+  DevBuf<unsigned> tk(2);
+  ED_CUDA(cudaMemsetAsync(tk.p, 0, 2 * sizeof(unsigned), s));
   S.omega.alloc(dim);
   const double tol_ritz = std::max(tol, 1e-14);
   ED_CUDA(cudaMemsetAsync(beta.p, 0, (M + 2) * sizeof(double), s));
@@ -572,10 +614,8 @@ static void sym_ground_state(ed_sym& S, double tol, int max_iter, uint64_t seed)
       const int nmax = pass == 0 ? M : m - 1;
       for (int n = 0; n < nmax; ++n) {
         // W = H v - b_n v_prev, alpha_n = <v, W>; W -= alpha_n v, b_{n+1} = |W|; v_prev = W / b_{n+1}
-        sym_spmv(S, v, W.p, vp, beta.p + n, part.p, nb, s);
-        k_sym_finish<<<1, kSymThreads, 0, s>>>(part.p, nb, alpha.p + n, 0);
-        k_sym_axpy_norm<<<nv, kSymThreads, 0, s>>>(W.p, v, alpha.p + n, dim, part.p);
-        k_sym_finish<<<1, kSymThreads, 0, s>>>(part.p, nv, beta.p + n + 1, 1);
+        sym_spmv(S, v, W.p, vp, beta.p + n, part.p, nb, s, tk.p, alpha.p + n);
+        k_sym_axpy_norm<<<nv, kSymThreads, 0, s>>>(W.p, v, alpha.p + n, dim, part2.p, tk.p + 1, beta.p + n + 1);
         k_sym_scale<<<nv, kSymThreads, 0, s>>>(vp, W.p, beta.p + n + 1, dim, pass == 1 ? S.omega.p : nullptr, svec.p + n + 1);
         ED_CHECK_LAUNCH();
         std::swap(v, vp);
@@ -647,9 +687,12 @@ constexpr int kSymCfMax = 20000;     // preset maximum of a continued fraction
 static int sym_cf(ed_sym& T, const double* phi, double E0, double s_eh, const DevBuf<double>& zr,
                   const DevBuf<double>& zi, int nz, double tol, double coef, double2* out, cudaStream_t s) {
   const int64_t dim = T.dim;
-  const int nb = sym_grid(dim, kSymThreads / 32 * 4), nv = sym_grid(dim, kSymThreads * 4);
+  const int nb = sym_grid(dim, kSymRowsPerBlock), nv = sym_grid(dim, kSymThreads * 4);
   const int maxn = (int)std::min<int64_t>(kSymCfMax, 2 * dim + 16);
-  DevBuf<double> V0(dim), V1(dim), W(dim), alpha(maxn + 1), beta(maxn + 2), part(std::max(nb, nv)), nrm(1);
+  DevBuf<double> V0(dim), V1(dim), W(dim), alpha(maxn + 1), beta(maxn + 2), part(std::max(nb, nv)),
+      part2(std::max(nb, nv)), nrm(1);
+  DevBuf<unsigned> tk(2);
+  ED_CUDA(cudaMemsetAsync(tk.p, 0, 2 * sizeof(unsigned), s));
   DevBuf<double2> g0(nz), g1(nz);
   ED_CUDA(cudaMemsetAsync(beta.p, 0, (maxn + 2) * sizeof(double), s));
   k_sym_axpy_norm<<<nv, kSymThreads, 0, s>>>(const_cast<double*>(phi), nullptr, nullptr, dim, part.p);
@@ -669,10 +712,8 @@ static int sym_cf(ed_sym& T, const double* phi, double E0, double s_eh, const De
   int levels = 0, quiet = 0;
   bool have_prev = false;
   for (int n = 0; n < maxn; ++n) {
-    sym_spmv(T, v, W.p, vp, beta.p + n, part.p, nb, s);
-    k_sym_finish<<<1, kSymThreads, 0, s>>>(part.p, nb, alpha.p + n, 0);
-    k_sym_axpy_norm<<<nv, kSymThreads, 0, s>>>(W.p, v, alpha.p + n, dim, part.p);
-    k_sym_finish<<<1, kSymThreads, 0, s>>>(part.p, nv, beta.p + n + 1, 1);
+    sym_spmv(T, v, W.p, vp, beta.p + n, part.p, nb, s, tk.p, alpha.p + n);
+    k_sym_axpy_norm<<<nv, kSymThreads, 0, s>>>(W.p, v, alpha.p + n, dim, part2.p, tk.p + 1, beta.p + n + 1);
     k_sym_scale<<<nv, kSymThreads, 0, s>>>(vp, W.p, beta.p + n + 1, dim, nullptr, nullptr);
     ED_CHECK_LAUNCH();
     std::swap(v, vp);
@@ -987,7 +1028,7 @@ ed_status ed_sym_hpsi(ed_sym* S, const double* x, double* y) {
     if (!S || !x || !y) throw Error(ED_ERR_INVALID, "handle and vectors must not be NULL");
     sym_require_device(S->c);
     if (S->dim == 0) return ED_OK;
-    sym_spmv(*S, x, y, nullptr, nullptr, nullptr, sym_grid(S->dim, kSymThreads / 32 * 4), S->c->stream);
+    sym_spmv(*S, x, y, nullptr, nullptr, nullptr, sym_grid(S->dim, kSymRowsPerBlock), S->c->stream);
     ED_CUDA(cudaStreamSynchronize(S->c->stream));
     return ED_OK;
   });
