@@ -194,18 +194,29 @@ def kernel_source_hash(kernel_file):
 
 
 def ncu_traffic(kernel_file, summary_file):
-    """Per-launch DRAM bytes from a committed ncu summary, if it was taken on this kernel source."""
+    """(DRAM bytes, algorithmic bytes) of one captured launch from a committed ncu summary, if it
+    was taken on this kernel source, else None."""
     p = os.path.join(ROOT, "profiles", summary_file)
     try:
         txt = open(p).read()
         sha = kernel_source_hash(kernel_file)
         m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
         t = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", txt)
-        if m and t and m.group(1) == sha:
-            return float(t.group(1))
+        a = re.search(r"alg_bytes_per_launch_full_size:\s*([0-9.eE+]+)", txt)
+        if m and t and a and m.group(1) == sha:
+            return float(t.group(1)), float(a.group(1))
     except OSError:
         pass
     return None
+
+
+def scaled_traffic(captured, alg_bytes_per_launch):
+    """DRAM bytes per launch of the timed kernel from a captured launch of the same kernels:
+    traffic grows in proportion to the elements processed, so it is scaled by the algorithmic
+    bytes (a timed launch may carry 16 products, or another sector, than the captured one)."""
+    if not captured or not alg_bytes_per_launch:
+        return None
+    return captured[0] * alg_bytes_per_launch / captured[1]
 
 
 # ----------------------------------------------------------------------------- GPU arm
@@ -299,9 +310,10 @@ def run_ours(args, rank, world, local_rank):
     peak, peak_kind = measured_peak_hbm()
     peak_src = peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind
 
-    def roofline_of(kid, name, traffic):
+    def roofline_of(kid, name, captured):
         n_l, ms_l, by_l = prof[kid]
         ach = (by_l / 1e9) / (ms_l / 1e3) if ms_l > 0 else None
+        traffic = scaled_traffic(captured, by_l / max(n_l, 1))
         return {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peak, "unit": "GB/s",
                 "frac": (ach / peak) if ach else None, "traffic": traffic, "peak_source": peak_src,
                 "launches": n_l, "total_ms": ms_l, "avg_launch_ms": ms_l / max(n_l, 1),
@@ -422,7 +434,7 @@ def run_hpsi(args, rank, world, local_rank, torch, ed):
         "clocks": clk.summary(), "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "kernel": "hpsi (two-pass: k_down_rows + k_up_cols)", "achieved": ach,
                      "peak": peak, "unit": "GB/s", "frac": (ach / peak) if ach else None,
-                     "traffic": ncu_traffic("hpsi.cu", "band_hpsi_4x4.md"),
+                     "traffic": scaled_traffic(ncu_traffic("hpsi.cu", "band_hpsi_4x4.md"), by_l / max(n_l, 1)),
                      "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
                      "launches": n_l, "avg_launch_ms": ms_l / max(n_l, 1), "alg_bytes_per_launch": by_l / max(n_l, 1)},
         "e2e": None,

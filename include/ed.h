@@ -436,6 +436,20 @@ typedef struct ed_sym ed_sym;
  * more than 2^31 states), ED_ERR_OOM, ED_ERR_CUDA.  Synchronous. */
 ed_status ed_sym_create(ed_cluster* c, int n_gen, const int* perm, const int* signs, ed_sym** out);
 
+/* General Abelian groups (Sec. 4.5): generators of orders orders[j] >= 2 (perm as above, each
+ * g_j^{orders[j]} = identity; commuting, independent; at most 32 elements), the irrep named by
+ * integers irrep[j] in [0, orders[j]): the element prod_j g_j^{a_j} has the character
+ * exp(2 pi i sum_j irrep[j] a_j / orders[j]).  With a complex character (a four-fold rotation, a
+ * translation of a ring) the irrep's matrix is complex Hermitian and every vector of the handle
+ * (ed_sym_hpsi, ed_sym_ground_vector) and every matrix value (ed_sym_matrix) is an interleaved
+ * complex128 pair; ed_sym_is_complex tells.  ed_sym_create is this call with every order 2 and
+ * irrep[j] = (signs[j] == -1).  Errors as ed_sym_create. */
+ed_status ed_sym_create_abelian(ed_cluster* c, int n_gen, const int* perm, const int* orders, const int* irrep,
+                                ed_sym** out);
+
+/* 1 when some character of the irrep is complex (complex matrix and vectors), else 0. */
+ed_status ed_sym_is_complex(const ed_sym* s, int* is_complex);
+
 /* Dimension of the symmetrized sector and number of stored matrix entries (either may be NULL). */
 ed_status ed_sym_info(const ed_sym* s, int64_t* dim, int64_t* nnz);
 
@@ -444,11 +458,12 @@ ed_status ed_sym_info(const ed_sym* s, int64_t* dim, int64_t* nnz);
 ed_status ed_sym_basis(const ed_sym* s, uint64_t* keys, uint8_t* stab);
 
 /* Host copies of the CSR matrix: rowptr (dim + 1 int64), col (nnz int32, ascending per row),
- * val (nnz doubles); any may be NULL.  Synchronous. */
+ * val (nnz doubles, or nnz interleaved complex128 pairs for a complex irrep); any may be NULL.
+ * Synchronous. */
 ed_status ed_sym_matrix(const ed_sym* s, int64_t* rowptr, int32_t* col, double* val);
 
-/* y = H x in the symmetrized basis; x, y: device arrays of dim doubles on the cluster's device
- * (y must not alias x).  Synchronous. */
+/* y = H x in the symmetrized basis; x, y: device arrays of dim doubles (dim complex128 pairs for
+ * a complex irrep) on the cluster's device (y must not alias x).  Synchronous. */
 ed_status ed_sym_hpsi(ed_sym* s, const double* x, double* y);
 
 /* Lowest eigenvalue of the irrep's H by FP64 Lanczos (Sec. 4.2) with the cluster's tol, max_iter
@@ -457,19 +472,22 @@ ed_status ed_sym_hpsi(ed_sym* s, const double* x, double* y);
  * ED_ERR_INVALID for an empty irrep.  Any output pointer may be NULL.  Synchronous. */
 ed_status ed_sym_ground_state(ed_sym* s, double* E0, double* residual, int* iters);
 
-/* Host copy of the ground vector (dim doubles, normalized).  ED_ERR_STATE before
- * ed_sym_ground_state. */
+/* Host copy of the ground vector (dim doubles, or dim complex128 pairs for a complex irrep;
+ * normalized).  ED_ERR_STATE before ed_sym_ground_state. */
 ed_status ed_sym_ground_vector(const ed_sym* s, double* out);
 
 /* Green function of the cluster's physical sites for one spin (0 = up, 1 = down) from the irrep's
- * ground state (Sec. 4.6): the site operators are symmetrized (c_rho = sum_a M_rho,a c_a, the
- * projections of every site orbit onto every irrep beta; M orthogonal), c+_rho Omega and
- * c_rho Omega land in the N +- 1 sectors of the product irrep alpha beta, where continued
- * fractions (Eq. jacobi; off-diagonal pairs as in Sec. 4.3) run on the stored matrices until they
+ * ground state (Sec. 4.6): the site operators are symmetrized (c+_rho = sum_a M_rho,a c+_a, the
+ * projections of every site orbit onto every irrep beta; M orthogonal, or unitary for complex
+ * characters), c+_rho Omega lands in the N + 1 sector of the irrep alpha + beta and c_rho Omega in
+ * the N - 1 sector of alpha - beta (exponents modulo the orders; the same irrep for involutions),
+ * where continued fractions (Eq. jacobi; off-diagonal pairs as in Sec. 4.3, with the pair
+ * phi_rho + i phi_sigma added when characters are complex) run on the stored matrices until they
  * change by less than the cluster's ED_OPT_GF_TOL (0: 1e-12) at two successive checks, and
- * G_ab = sum M_rho,a M_sigma,b G_rho,sigma.  z_k = omega[k] + i eta (ED_AXIS_REAL) or i omega[k]
- * (ED_AXIS_MATSUBARA).  G_out: host, interleaved complex128 [n_freq][n_sites][n_sites].  The group
- * must map cluster sites to cluster sites.  ED_ERR_STATE before ed_sym_ground_state.  G is the
+ * G_ab = sum M_rho,a conj(M_sigma,b) G_rho,sigma.  z_k = omega[k] + i eta (ED_AXIS_REAL) or
+ * i omega[k] (ED_AXIS_MATSUBARA).  G_out: host, interleaved complex128 [n_freq][n_sites][n_sites].
+ * The group must map cluster sites to cluster sites (else ED_ERR_INVALID).  ED_ERR_STATE before
+ * ed_sym_ground_state.  G is the
  * ground-state G when the irrep holds the sector's (non-degenerate) ground state.  Synchronous. */
 ed_status ed_sym_green(ed_sym* s, const double* omega, int n_freq, double eta, int axis, int spin, double* G_out);
 

@@ -1,10 +1,12 @@
 // Cluster symmetries (Sec. 4.5): the Hamiltonian restricted to one irreducible representation of
 // an Abelian symmetry group, in the basis of symmetrized states, and its ground state.
 //
-// The group is generated by commuting, independent involutions of the orbitals (mirrors, two-fold
-// rotations, half translations of a periodic cluster), so it has 2^k elements, each its own
-// inverse, and every irreducible representation has characters +-1; the caller names the irrep
-// by the signs it gives the generators.
+// The group is Abelian, generated by commuting, independent permutations g_j of the orbitals of
+// orders n_j (mirrors and two-fold rotations: n_j = 2; four-fold rotations, translations of a
+// periodic cluster: n_j = 4, 6, ...), at most 32 elements.  An irrep is named by exponents m_j;
+// the element prod_j g_j^{a_j} has the character exp(2 pi i sum_j m_j a_j / n_j).  With only
+// +-1 characters the irrep's matrix is real symmetric; otherwise it is complex Hermitian and the
+// matrix and every vector hold interleaved (real, imaginary) pairs.
 //
 // Basis (Sec. 4.5): the binary states (b_up, b_dn) of the sector are grouped into orbits; the
 // member with the smallest key b_up 2^L + b_dn represents its orbit, and its symmetrized state
@@ -17,8 +19,8 @@
 //
 // Matrix (Eq. matrixElement for normalized states): applying every term of H to a representative
 // r gives binary states b_k with amplitudes h_k; with g_k b_k = r_k,
-//   <psi(r_k)| H |psi(r)> += h_k phi_{g_k}(b_k) chi_{g_k} sqrt(|S_{r_k}| / |S_r|).
-// The matrix is real symmetric, so the entries generated from r are stored as row r.  A row's
+//   <psi(r_k)| H |psi(r)> += h_k phi_{g_k}(b_k) chi_{g_k}^* sqrt(|S_{r_k}| / |S_r|).
+// The entries generated from r are stored, conjugated (H is Hermitian), as row r.  A row's
 // terms are merged in a thread's local buffer before they are stored, which carries out the
 // cancellations that Sec. 4.5 mentions; entries below 1e-13 in magnitude are dropped.  The matrix
 // is built twice, counting then filling (the paper stores H once the basis is symmetrized).
@@ -29,6 +31,7 @@
 // 1e-12 max(1, |E|).
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -52,7 +55,7 @@ struct SymDev {
   int n_pairs;
   uint8_t perm[1 << kSymMaxGen][kMaxOrb];     // orbital images of every element
   uint32_t inv[1 << kSymMaxGen][kMaxOrb];     // inv[g][i]: orbitals j > i with perm(j) < perm(i)
-  int chi[1 << kSymMaxGen];                   // character of every element in the irrep
+  double chr[1 << kSymMaxGen], chi[1 << kSymMaxGen];  // character of every element: real, imaginary part
   double hdiag[kMaxOrb];
   double U[kMaxOrb];
   int pa[kMaxPairs], pb[kMaxPairs];           // ordered hopping pairs (a <- b), h_ab != 0
@@ -89,30 +92,34 @@ __device__ bool sym_is_rep(const SymDev& G, uint32_t bu, uint32_t bd, int* stab)
     if (gk < k) return false;
     if (gk == k) {
       ++s;
+      // non-vanishing iff chi_g = phi_g(r) on the stabilizer
       const int ph = sym_parity(G.inv[g], bu) ^ sym_parity(G.inv[g], bd);
-      if (G.chi[g] * (ph ? -1 : 1) != 1) return false;
+      if (fabs(G.chr[g] - (ph ? -1.0 : 1.0)) > 1e-9 || fabs(G.chi[g]) > 1e-9) return false;
     }
   }
   *stab = s;
   return true;
 }
 
-// Representative key of the orbit of (bu, bd) and the factor phi_g(b) chi_g of the first element
-// (in element order) that reaches it.
-__device__ void sym_rep(const SymDev& G, uint32_t bu, uint32_t bd, uint64_t* rk, int* factor) {
+// Representative key of the orbit of (bu, bd) and the factor phi_g(b) chi_g^* (real fr, imaginary
+// fi) of the first element (in element order) that reaches it (P g = chi_g P for the projector
+// P = (1/|G|) sum_g chi_g^* g).
+__device__ void sym_rep(const SymDev& G, uint32_t bu, uint32_t bd, uint64_t* rk, double* fr, double* fi) {
   uint64_t best = ~0ull;
-  int f = 1;
+  double r = 1.0, i = 0.0;
   for (int g = 0; g < G.ng; ++g) {
     const uint32_t gu = sym_move(G.perm[g], bu), gd = sym_move(G.perm[g], bd);
     const uint64_t gk = sym_key(gu, gd, G.L);
     if (gk < best) {
       best = gk;
-      const int ph = sym_parity(G.inv[g], bu) ^ sym_parity(G.inv[g], bd);
-      f = G.chi[g] * (ph ? -1 : 1);
+      const double ph = (sym_parity(G.inv[g], bu) ^ sym_parity(G.inv[g], bd)) ? -1.0 : 1.0;
+      r = ph * G.chr[g];
+      i = -ph * G.chi[g];
     }
   }
   *rk = best;
-  *factor = f;
+  *fr = r;
+  *fi = i;
 }
 
 // ---- basis: count, then write, the representatives of every chunk of the sector in order
@@ -175,9 +182,12 @@ __device__ __forceinline__ int64_t sym_find(const uint64_t* __restrict__ keys, i
   return (lo < dim && keys[lo] == k) ? lo : -1;
 }
 
-// The merged entries of row r (columns ascending); returns their number.
+// The merged entries of row r (columns ascending); returns their number.  CPLX: val holds
+// interleaved (real, imaginary) pairs.
+template <bool CPLX>
 __device__ int sym_row(const SymDev& G, const uint64_t* __restrict__ keys, const uint8_t* __restrict__ stab, int64_t dim,
                        int64_t r, int32_t* col, double* val) {
+  constexpr int W = CPLX ? 2 : 1;
   const uint64_t k = keys[r];
   const uint32_t bu = (uint32_t)(k >> G.L), bd = (uint32_t)(k & ((G.L == 32) ? 0xFFFFFFFFull : ((1ull << G.L) - 1ull)));
   const double sr = (double)stab[r];
@@ -188,7 +198,9 @@ __device__ int sym_row(const SymDev& G, const uint64_t* __restrict__ keys, const
     if ((bu >> a) & (bd >> a) & 1u) diag += G.U[a];
   }
   col[n] = (int32_t)r;
-  val[n++] = diag;
+  val[W * n] = diag;
+  if (CPLX) val[W * n + 1] = 0.0;
+  ++n;
   for (int p = 0; p < G.n_pairs; ++p) {
     const int a = G.pa[p], b = G.pb[p];
     const uint32_t lo = (uint32_t)min(a, b), hi = (uint32_t)max(a, b);
@@ -199,59 +211,74 @@ __device__ int sym_row(const SymDev& G, const uint64_t* __restrict__ keys, const
       const uint32_t nb = bs ^ (1u << a) ^ (1u << b);
       const int jw = __popc(bs & between) & 1;
       uint64_t rk;
-      int f;
-      sym_rep(G, spin ? bu : nb, spin ? nb : bd, &rk, &f);
+      double fr, fi;
+      sym_rep(G, spin ? bu : nb, spin ? nb : bd, &rk, &fr, &fi);
       const int64_t c = sym_find(keys, dim, rk);
       if (c < 0 || n >= kSymMaxTerms) continue;
+      const double amp = G.pv[p] * (jw ? -1.0 : 1.0) * sqrt((double)stab[c] / sr);
+      // this term is <psi(c)| H |psi(r)>; row r stores its conjugate <psi(r)| H |psi(c)>
       col[n] = (int32_t)c;
-      val[n++] = G.pv[p] * (jw ? -1.0 : 1.0) * (double)f * sqrt((double)stab[c] / sr);
+      val[W * n] = amp * fr;
+      if (CPLX) val[W * n + 1] = -amp * fi;
+      ++n;
     }
   }
   // sort by column (insertion: rows hold a few dozen terms), merge, drop cancelled entries
   for (int i = 1; i < n; ++i) {
     const int32_t cc = col[i];
-    const double vv = val[i];
+    const double vr = val[W * i], vi = CPLX ? val[W * i + 1] : 0.0;
     int j = i - 1;
     while (j >= 0 && col[j] > cc) {
       col[j + 1] = col[j];
-      val[j + 1] = val[j];
+      val[W * (j + 1)] = val[W * j];
+      if (CPLX) val[W * (j + 1) + 1] = val[W * j + 1];
       --j;
     }
     col[j + 1] = cc;
-    val[j + 1] = vv;
+    val[W * (j + 1)] = vr;
+    if (CPLX) val[W * (j + 1) + 1] = vi;
   }
   int m = 0;
   for (int i = 0; i < n;) {
     const int32_t cc = col[i];
-    double s = 0.0;
-    while (i < n && col[i] == cc) s += val[i++];
-    if (fabs(s) >= 1e-13) {
+    double sr_ = 0.0, si_ = 0.0;
+    while (i < n && col[i] == cc) {
+      sr_ += val[W * i];
+      if (CPLX) si_ += val[W * i + 1];
+      ++i;
+    }
+    if (hypot(sr_, si_) >= 1e-13) {
       col[m] = cc;
-      val[m++] = s;
+      val[W * m] = sr_;
+      if (CPLX) val[W * m + 1] = si_;
+      ++m;
     }
   }
   return m;
 }
 
+template <bool CPLX>
 __global__ void __launch_bounds__(128) k_sym_rows(const SymDev* __restrict__ Gp, const uint64_t* __restrict__ keys,
                                                   const uint8_t* __restrict__ stab, int64_t dim,
                                                   int64_t* __restrict__ rowptr, int32_t* __restrict__ colo,
                                                   double* __restrict__ valo, int fill) {
+  constexpr int W = CPLX ? 2 : 1;
   __shared__ SymDev G;
   for (int i = threadIdx.x; i < (int)(sizeof(SymDev) / 4); i += blockDim.x)
     reinterpret_cast<int*>(&G)[i] = reinterpret_cast<const int*>(Gp)[i];
   __syncthreads();
   int32_t col[kSymMaxTerms];
-  double val[kSymMaxTerms];
+  double val[W * kSymMaxTerms];
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < dim; r += (int64_t)gridDim.x * blockDim.x) {
-    const int m = sym_row(G, keys, stab, dim, r, col, val);
+    const int m = sym_row<CPLX>(G, keys, stab, dim, r, col, val);
     if (!fill) {
       rowptr[r] = m;
     } else {
       const int64_t o = rowptr[r];
       for (int i = 0; i < m; ++i) {
         colo[o + i] = col[i];
-        valo[o + i] = val[i];
+        valo[W * (o + i)] = val[W * i];
+        if (CPLX) valo[W * (o + i) + 1] = val[W * i + 1];
       }
     }
   }
@@ -289,28 +316,52 @@ __device__ void sym_finish_last(const double* partial, double* out, int mode, un
 constexpr int kSymRowLanes = 8;
 constexpr int kSymRowsPerBlock = kSymThreads / kSymRowLanes;
 
+template <bool CPLX>
 __global__ void __launch_bounds__(kSymThreads) k_sym_spmv(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                                          const double* __restrict__ val, int64_t dim,
                                                          const double* __restrict__ x, double* __restrict__ y,
                                                          const double* __restrict__ xprev, const double* __restrict__ beta,
                                                          double* __restrict__ partial, unsigned* ticket, double* out) {
+  // CPLX: val, x, y, xprev hold interleaved (real, imaginary) pairs; the partial is Re <x, y>
   __shared__ double s_part[kSymRowsPerBlock];
   const int sub = threadIdx.x & (kSymRowLanes - 1), grp = threadIdx.x / kSymRowLanes;
   const double b = (xprev && beta) ? *beta : 0.0;
   double dot = 0.0;
   for (int64_t r0 = (int64_t)blockIdx.x * kSymRowsPerBlock; r0 < dim; r0 += (int64_t)gridDim.x * kSymRowsPerBlock) {
     const int64_t r = r0 + grp;
-    double s = 0.0;
+    double sr = 0.0, si = 0.0;
     if (r < dim) {
       const int64_t e = rowptr[r + 1];
-      for (int64_t k = rowptr[r] + sub; k < e; k += kSymRowLanes) s += val[k] * __ldg(x + col[k]);
+      for (int64_t k = rowptr[r] + sub; k < e; k += kSymRowLanes) {
+        if constexpr (CPLX) {
+          const double2 v = reinterpret_cast<const double2*>(val)[k];
+          const double2 xv = __ldg(reinterpret_cast<const double2*>(x) + col[k]);
+          sr += v.x * xv.x - v.y * xv.y;
+          si += v.x * xv.y + v.y * xv.x;
+        } else {
+          sr += val[k] * __ldg(x + col[k]);
+        }
+      }
     }
 #pragma unroll
-    for (int o = kSymRowLanes / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    for (int o = kSymRowLanes / 2; o > 0; o >>= 1) {
+      sr += __shfl_xor_sync(0xffffffffu, sr, o);
+      if (CPLX) si += __shfl_xor_sync(0xffffffffu, si, o);
+    }
     if (r < dim && sub == 0) {
-      if (xprev) s -= b * xprev[r];
-      y[r] = s;
-      dot += s * x[r];
+      if constexpr (CPLX) {
+        if (xprev) {
+          sr -= b * xprev[2 * r];
+          si -= b * xprev[2 * r + 1];
+        }
+        y[2 * r] = sr;
+        y[2 * r + 1] = si;
+        dot += sr * x[2 * r] + si * x[2 * r + 1];
+      } else {
+        if (xprev) sr -= b * xprev[r];
+        y[r] = sr;
+        dot += sr * x[r];
+      }
     }
   }
   if (sub == 0) s_part[grp] = dot;
@@ -417,13 +468,61 @@ __global__ void __launch_bounds__(128) k_sym_apply(const SymDev* __restrict__ Gs
       const uint32_t nb = bs ^ (1u << a);
       const int before = spin ? __popc(bu) + __popc(bd & ((1u << a) - 1u)) : __popc(bu & ((1u << a) - 1u));
       uint64_t rk;
-      int f;
-      sym_rep(G, spin ? bu : nb, spin ? nb : bd, &rk, &f);
+      double f, fi;
+      sym_rep(G, spin ? bu : nb, spin ? nb : bd, &rk, &f, &fi);  // +-1 characters here: fi = 0
       const int64_t c = sym_find(src_keys, src_dim, rk);
       if (c < 0) continue;
-      acc += w * ((before & 1) ? -1.0 : 1.0) * (double)f * sqrt((double)src_stab[c] / st) * omega[c];
+      acc += w * ((before & 1) ? -1.0 : 1.0) * f * sqrt((double)src_stab[c] / st) * omega[c];
     }
     out[r] = acc;
+  }
+}
+
+// The same with complex weights and characters (any Abelian group): phi = O Omega for
+// O = sum_a w[a] c+_a (create) or sum_a w[a] c_a, w interleaved (real, imaginary) over the L
+// orbitals; the target irrep's vector is complex (interleaved), Omega is complex when SRC_CPLX.
+// <b| psi_S(r)> = phi_g(b) chi_S(g) (|S_r| / |G|)^(1/2) for g b = r, so every term carries the
+// conjugate of the factor phi_g(b) chi_S(g)^* that sym_rep returns:
+//   phi[r'] = sum_a w[a] sign_a phi_g(b) chi_S(g) sqrt(|S_r| / |S_r'|) Omega[r].
+template <bool SRC_CPLX>
+__global__ void __launch_bounds__(128) k_sym_apply_c(const SymDev* __restrict__ Gsrc, const uint64_t* __restrict__ src_keys,
+                                                     const uint8_t* __restrict__ src_stab, int64_t src_dim,
+                                                     const double* __restrict__ omega, const uint64_t* __restrict__ tgt_keys,
+                                                     const uint8_t* __restrict__ tgt_stab, int64_t tgt_dim,
+                                                     const double* __restrict__ w, int create, int spin,
+                                                     double* __restrict__ out) {
+  __shared__ SymDev G;
+  for (int i = threadIdx.x; i < (int)(sizeof(SymDev) / 4); i += blockDim.x)
+    reinterpret_cast<int*>(&G)[i] = reinterpret_cast<const int*>(Gsrc)[i];
+  __syncthreads();
+  const uint64_t lmask = (G.L == 32) ? 0xFFFFFFFFull : ((1ull << G.L) - 1ull);
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < tgt_dim; r += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = tgt_keys[r];
+    const uint32_t bu = (uint32_t)(k >> G.L), bd = (uint32_t)(k & lmask);
+    const double st = (double)tgt_stab[r];
+    double ar = 0.0, ai = 0.0;
+    for (int a = 0; a < G.L; ++a) {
+      const double wr = w[2 * a], wi = w[2 * a + 1];
+      if (wr == 0.0 && wi == 0.0) continue;
+      const uint32_t bs = spin ? bd : bu;
+      const bool occ = (bs >> a) & 1u;
+      if (create ? !occ : occ) continue;
+      const uint32_t nb = bs ^ (1u << a);
+      const int before = spin ? __popc(bu) + __popc(bd & ((1u << a) - 1u)) : __popc(bu & ((1u << a) - 1u));
+      uint64_t rk;
+      double fr, fi;
+      sym_rep(G, spin ? bu : nb, spin ? nb : bd, &rk, &fr, &fi);
+      const int64_t c = sym_find(src_keys, src_dim, rk);
+      if (c < 0) continue;
+      const double amp = ((before & 1) ? -1.0 : 1.0) * sqrt((double)src_stab[c] / st);
+      // t = w[a] * conj(f) * amp
+      const double tr = amp * (wr * fr + wi * fi), ti = amp * (wi * fr - wr * fi);
+      const double orr = SRC_CPLX ? omega[2 * c] : omega[c], oi = SRC_CPLX ? omega[2 * c + 1] : 0.0;
+      ar += tr * orr - ti * oi;
+      ai += tr * oi + ti * orr;
+    }
+    out[2 * r] = ar;
+    out[2 * r + 1] = ai;
   }
 }
 
@@ -454,7 +553,10 @@ struct ed_sym {
   ed_cluster* c = nullptr;
   int n_gen = 0;
   int n_up = 0, n_dn = 0;     // the sector
-  std::vector<int> signs;
+  std::vector<int> orders;   // order n_k of every generator
+  std::vector<int> irrep;    // exponents m_k: chi(g_a) = exp(2 pi i sum m_k a_k / n_k)
+  bool cplx = false;         // some character is complex, or force_cplx: complex matrix and vectors
+  bool force_cplx = false;   // complex storage even with real characters (targets of a complex G)
   std::vector<int> perm;     // n_gen x L generator images
   ed::SymDev host;           // host copy of the group (characters of this irrep)
   ed::DevBuf<ed::SymDev> G;
@@ -484,16 +586,20 @@ static void sym_build(ed_sym& S, const int* perm, cudaStream_t s) {
   SymDev h;
   std::memset(&h, 0, sizeof(h));
   h.L = L;
-  h.ng = 1 << k;
+  h.ng = 1;
+  for (int j = 0; j < k; ++j) h.ng *= S.orders[j];
+  S.cplx = S.force_cplx;
   for (int g = 0; g < h.ng; ++g) {
+    // element g_a = prod_j g_j^{a_j}, a the mixed-radix digits of g (first generator fastest)
     std::vector<int> p(L);
     std::iota(p.begin(), p.end(), 0);
-    int chi = 1;
-    for (int j = 0; j < k; ++j)
-      if (g >> j & 1) {
+    double phase = 0.0;  // sum_j m_j a_j / n_j
+    for (int j = 0, rest = g; j < k; rest /= S.orders[j], ++j) {
+      const int aj = rest % S.orders[j];
+      for (int t = 0; t < aj; ++t)
         for (int i = 0; i < L; ++i) p[i] = perm[j * L + p[i]];
-        chi *= S.signs[j];
-      }
+      phase += (double)S.irrep[j] * aj / S.orders[j];
+    }
     for (int i = 0; i < L; ++i) {
       h.perm[g][i] = (uint8_t)p[i];
       uint32_t inv = 0;
@@ -501,7 +607,17 @@ static void sym_build(ed_sym& S, const int* perm, cudaStream_t s) {
         if (p[jj] < p[i]) inv |= 1u << jj;
       h.inv[g][i] = inv;
     }
-    h.chi[g] = chi;
+    // exact values on the real axis (the +-1 characters of involutions stay exact)
+    const double f = phase - std::floor(phase);
+    if (f == 0.0) {
+      h.chr[g] = 1.0, h.chi[g] = 0.0;
+    } else if (f == 0.5) {
+      h.chr[g] = -1.0, h.chi[g] = 0.0;
+    } else {
+      h.chr[g] = std::cos(2.0 * M_PI * f);
+      h.chi[g] = std::sin(2.0 * M_PI * f);
+      S.cplx = true;
+    }
   }
   for (int a = 0; a < L; ++a) {
     h.hdiag[a] = m.h[(size_t)a * L + a];
@@ -542,7 +658,10 @@ static void sym_build(ed_sym& S, const int* perm, cudaStream_t s) {
     S.nnz = 0;
     return;
   }
-  k_sym_rows<<<sym_grid(tot, 128), 128, 0, s>>>(S.G.p, S.keys.p, S.stab.p, tot, S.rowptr.p, nullptr, nullptr, 0);
+  if (S.cplx)
+    k_sym_rows<true><<<sym_grid(tot, 128), 128, 0, s>>>(S.G.p, S.keys.p, S.stab.p, tot, S.rowptr.p, nullptr, nullptr, 0);
+  else
+    k_sym_rows<false><<<sym_grid(tot, 128), 128, 0, s>>>(S.G.p, S.keys.p, S.stab.p, tot, S.rowptr.p, nullptr, nullptr, 0);
   ED_CHECK_LAUNCH();
   std::vector<int64_t> rp(tot + 1);
   ED_CUDA(cudaMemcpyAsync(rp.data(), S.rowptr.p, tot * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -557,36 +676,46 @@ static void sym_build(ed_sym& S, const int* perm, cudaStream_t s) {
   S.nnz = acc;
   ED_CUDA(cudaMemcpyAsync(S.rowptr.p, rp.data(), (tot + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   S.col.alloc(std::max<int64_t>(acc, 1));
-  S.val.alloc(std::max<int64_t>(acc, 1));
-  k_sym_rows<<<sym_grid(tot, 128), 128, 0, s>>>(S.G.p, S.keys.p, S.stab.p, tot, S.rowptr.p, S.col.p, S.val.p, 1);
+  S.val.alloc(std::max<int64_t>(acc, 1) * (S.cplx ? 2 : 1));
+  if (S.cplx)
+    k_sym_rows<true><<<sym_grid(tot, 128), 128, 0, s>>>(S.G.p, S.keys.p, S.stab.p, tot, S.rowptr.p, S.col.p, S.val.p, 1);
+  else
+    k_sym_rows<false><<<sym_grid(tot, 128), 128, 0, s>>>(S.G.p, S.keys.p, S.stab.p, tot, S.rowptr.p, S.col.p, S.val.p, 1);
   ED_CHECK_LAUNCH();
   ED_CUDA(cudaStreamSynchronize(s));
 }
 
-// y = H x in the symmetrized basis (device vectors of S.dim doubles)
+// y = H x in the symmetrized basis (device vectors of S.dim values: doubles, or interleaved
+// complex pairs when a character is complex)
 static void sym_spmv(ed_sym& S, const double* x, double* y, const double* xprev, const double* beta, double* partial,
                      int nblk, cudaStream_t s, unsigned* ticket = nullptr, double* out = nullptr) {
-  ProfScope ps_(K_HPSI, s, (double)S.nnz * 12.0 + (double)S.dim * 16.0);
-  k_sym_spmv<<<nblk, kSymThreads, 0, s>>>(S.rowptr.p, S.col.p, S.val.p, S.dim, x, y, xprev, beta, partial, ticket, out);
+  const double w = S.cplx ? 2.0 : 1.0;
+  ProfScope ps_(K_HPSI, s, (double)S.nnz * (4.0 + 8.0 * w) + (double)S.dim * 16.0 * w);
+  if (S.cplx)
+    k_sym_spmv<true><<<nblk, kSymThreads, 0, s>>>(S.rowptr.p, S.col.p, S.val.p, S.dim, x, y, xprev, beta, partial, ticket,
+                                                  out);
+  else
+    k_sym_spmv<false><<<nblk, kSymThreads, 0, s>>>(S.rowptr.p, S.col.p, S.val.p, S.dim, x, y, xprev, beta, partial, ticket,
+                                                   out);
   ED_CHECK_LAUNCH();
 }
 
 // FP64 Lanczos ground state of the symmetrized sector (see the header).
 static void sym_ground_state(ed_sym& S, double tol, int max_iter, uint64_t seed) {
   cudaStream_t s = S.c->stream;
-  const int64_t dim = S.dim;
-  if (dim == 0) throw Error(ED_ERR_INVALID, "the irrep has no state in this sector");
+  const int64_t dim = S.dim, vlen = S.cplx ? 2 * dim : dim;  // vectors: doubles, or interleaved complex
+  if (vlen == 0) throw Error(ED_ERR_INVALID, "the irrep has no state in this sector");
   const int M = std::max(2, (int)std::min<int64_t>(max_iter > 0 ? max_iter : 600, dim));
-  const int nb = sym_grid(dim, kSymRowsPerBlock), nv = sym_grid(dim, kSymThreads * 4);
+  const int nb = sym_grid(dim, kSymRowsPerBlock), nv = sym_grid(vlen, kSymThreads * 4);
   const int np = std::max(nb, nv);
-  DevBuf<double> V0(dim), V1(dim), W(dim), start(dim), alpha(M + 1), beta(M + 2), evals(3), svec(M + 1), part(np),
+  DevBuf<double> V0(vlen), V1(vlen), W(vlen), start(vlen), alpha(M + 1), beta(M + 2), evals(3), svec(M + 1), part(np),
       part2(np);
   DevBuf<unsigned> tk(2);
   ED_CUDA(cudaMemsetAsync(tk.p, 0, 2 * sizeof(unsigned), s));
-  S.omega.alloc(dim);
+  S.omega.alloc(vlen);
   const double tol_ritz = std::max(tol, 1e-14);
   ED_CUDA(cudaMemsetAsync(beta.p, 0, (M + 2) * sizeof(double), s));
-  k_sym_start<<<nv, kSymThreads, 0, s>>>(start.p, dim, seed);
+  k_sym_start<<<nv, kSymThreads, 0, s>>>(start.p, vlen, seed);
   ED_CHECK_LAUNCH();
   double host[3] = {0, 0, 0};
   std::vector<double> hb(M + 2);
@@ -594,9 +723,9 @@ static void sym_ground_state(ed_sym& S, double tol, int max_iter, uint64_t seed)
   S.iters = 0;
   for (int round = 0; round < kSymRounds; ++round) {
     // normalize the start vector into V0
-    k_sym_axpy_norm<<<nv, kSymThreads, 0, s>>>(start.p, nullptr, nullptr, dim, part.p);
+    k_sym_axpy_norm<<<nv, kSymThreads, 0, s>>>(start.p, nullptr, nullptr, vlen, part.p);
     k_sym_finish<<<1, kSymThreads, 0, s>>>(part.p, nv, beta.p, 1);
-    k_sym_scale<<<nv, kSymThreads, 0, s>>>(V0.p, start.p, beta.p, dim, nullptr, nullptr);
+    k_sym_scale<<<nv, kSymThreads, 0, s>>>(V0.p, start.p, beta.p, vlen, nullptr, nullptr);
     ED_CHECK_LAUNCH();
     ED_CUDA(cudaMemsetAsync(beta.p, 0, sizeof(double), s));
     int m = 0;
@@ -604,19 +733,19 @@ static void sym_ground_state(ed_sym& S, double tol, int max_iter, uint64_t seed)
       double* v = V0.p;
       double* vp = V1.p;
       if (pass == 1) {
-        k_sym_axpy_norm<<<nv, kSymThreads, 0, s>>>(start.p, nullptr, nullptr, dim, part.p);
+        k_sym_axpy_norm<<<nv, kSymThreads, 0, s>>>(start.p, nullptr, nullptr, vlen, part.p);
         k_sym_finish<<<1, kSymThreads, 0, s>>>(part.p, nv, W.p, 1);
-        ED_CUDA(cudaMemsetAsync(S.omega.p, 0, dim * sizeof(double), s));
-        k_sym_scale<<<nv, kSymThreads, 0, s>>>(V0.p, start.p, W.p, dim, S.omega.p, svec.p);
+        ED_CUDA(cudaMemsetAsync(S.omega.p, 0, vlen * sizeof(double), s));
+        k_sym_scale<<<nv, kSymThreads, 0, s>>>(V0.p, start.p, W.p, vlen, S.omega.p, svec.p);
         ED_CHECK_LAUNCH();
       }
-      ED_CUDA(cudaMemsetAsync(vp, 0, dim * sizeof(double), s));
+      ED_CUDA(cudaMemsetAsync(vp, 0, vlen * sizeof(double), s));
       const int nmax = pass == 0 ? M : m - 1;
       for (int n = 0; n < nmax; ++n) {
         // W = H v - b_n v_prev, alpha_n = <v, W>; W -= alpha_n v, b_{n+1} = |W|; v_prev = W / b_{n+1}
         sym_spmv(S, v, W.p, vp, beta.p + n, part.p, nb, s, tk.p, alpha.p + n);
-        k_sym_axpy_norm<<<nv, kSymThreads, 0, s>>>(W.p, v, alpha.p + n, dim, part2.p, tk.p + 1, beta.p + n + 1);
-        k_sym_scale<<<nv, kSymThreads, 0, s>>>(vp, W.p, beta.p + n + 1, dim, pass == 1 ? S.omega.p : nullptr, svec.p + n + 1);
+        k_sym_axpy_norm<<<nv, kSymThreads, 0, s>>>(W.p, v, alpha.p + n, vlen, part2.p, tk.p + 1, beta.p + n + 1);
+        k_sym_scale<<<nv, kSymThreads, 0, s>>>(vp, W.p, beta.p + n + 1, vlen, pass == 1 ? S.omega.p : nullptr, svec.p + n + 1);
         ED_CHECK_LAUNCH();
         std::swap(v, vp);
         if (pass == 0 && ((n + 1) % kSymCheck == 0 || n + 1 == M)) {
@@ -640,14 +769,14 @@ static void sym_ground_state(ed_sym& S, double tol, int max_iter, uint64_t seed)
     }
     S.iters += m;
     // residual of the rebuilt vector: normalize, E = <w, H w>, r = |H w - E w|
-    k_sym_axpy_norm<<<nv, kSymThreads, 0, s>>>(S.omega.p, nullptr, nullptr, dim, part.p);
+    k_sym_axpy_norm<<<nv, kSymThreads, 0, s>>>(S.omega.p, nullptr, nullptr, vlen, part.p);
     k_sym_finish<<<1, kSymThreads, 0, s>>>(part.p, nv, W.p + 0, 1);
-    k_sym_scale<<<nv, kSymThreads, 0, s>>>(start.p, S.omega.p, W.p, dim, nullptr, nullptr);
+    k_sym_scale<<<nv, kSymThreads, 0, s>>>(start.p, S.omega.p, W.p, vlen, nullptr, nullptr);
     ED_CHECK_LAUNCH();
-    ED_CUDA(cudaMemcpyAsync(S.omega.p, start.p, dim * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    ED_CUDA(cudaMemcpyAsync(S.omega.p, start.p, vlen * sizeof(double), cudaMemcpyDeviceToDevice, s));
     sym_spmv(S, S.omega.p, W.p, nullptr, nullptr, part.p, nb, s);
     k_sym_finish<<<1, kSymThreads, 0, s>>>(part.p, nb, evals.p, 0);
-    k_sym_axpy_norm<<<nv, kSymThreads, 0, s>>>(W.p, S.omega.p, evals.p, dim, part.p);
+    k_sym_axpy_norm<<<nv, kSymThreads, 0, s>>>(W.p, S.omega.p, evals.p, vlen, part.p);
     k_sym_finish<<<1, kSymThreads, 0, s>>>(part.p, nv, evals.p + 1, 1);
     ED_CHECK_LAUNCH();
     ED_CUDA(cudaMemcpyAsync(host, evals.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -663,15 +792,17 @@ static void sym_ground_state(ed_sym& S, double tol, int max_iter, uint64_t seed)
   }
 }
 
-// The sector of the same group for another particle number and irrep.
-static std::unique_ptr<ed_sym> sym_sibling(const ed_sym& S, int n_up, int n_dn, const std::vector<int>& signs,
-                                           cudaStream_t s) {
+// The sector of the same group for another particle number and irrep (exponents m_k).
+static std::unique_ptr<ed_sym> sym_sibling(const ed_sym& S, int n_up, int n_dn, const std::vector<int>& irrep,
+                                           bool force_cplx, cudaStream_t s) {
   auto T = std::make_unique<ed_sym>();
+  T->force_cplx = force_cplx;
   T->c = S.c;
   T->n_gen = S.n_gen;
   T->n_up = n_up;
   T->n_dn = n_dn;
-  T->signs = signs;
+  T->orders = S.orders;
+  T->irrep = irrep;
   T->perm = S.perm;
   sym_build(*T, T->perm.data(), s);
   return T;
@@ -686,22 +817,22 @@ constexpr int kSymCfMax = 20000;     // preset maximum of a continued fraction
 // Returns the number of levels.
 static int sym_cf(ed_sym& T, const double* phi, double E0, double s_eh, const DevBuf<double>& zr,
                   const DevBuf<double>& zi, int nz, double tol, double coef, double2* out, cudaStream_t s) {
-  const int64_t dim = T.dim;
-  const int nb = sym_grid(dim, kSymRowsPerBlock), nv = sym_grid(dim, kSymThreads * 4);
+  const int64_t dim = T.dim, vlen = T.cplx ? 2 * dim : dim;  // vectors: doubles, or interleaved complex
+  const int nb = sym_grid(dim, kSymRowsPerBlock), nv = sym_grid(vlen, kSymThreads * 4);
   const int maxn = (int)std::min<int64_t>(kSymCfMax, 2 * dim + 16);
-  DevBuf<double> V0(dim), V1(dim), W(dim), alpha(maxn + 1), beta(maxn + 2), part(std::max(nb, nv)),
+  DevBuf<double> V0(vlen), V1(vlen), W(vlen), alpha(maxn + 1), beta(maxn + 2), part(std::max(nb, nv)),
       part2(std::max(nb, nv)), nrm(1);
   DevBuf<unsigned> tk(2);
   ED_CUDA(cudaMemsetAsync(tk.p, 0, 2 * sizeof(unsigned), s));
   DevBuf<double2> g0(nz), g1(nz);
   ED_CUDA(cudaMemsetAsync(beta.p, 0, (maxn + 2) * sizeof(double), s));
-  k_sym_axpy_norm<<<nv, kSymThreads, 0, s>>>(const_cast<double*>(phi), nullptr, nullptr, dim, part.p);
+  k_sym_axpy_norm<<<nv, kSymThreads, 0, s>>>(const_cast<double*>(phi), nullptr, nullptr, vlen, part.p);
   k_sym_finish<<<1, kSymThreads, 0, s>>>(part.p, nv, nrm.p, 1);
-  k_sym_scale<<<nv, kSymThreads, 0, s>>>(V0.p, phi, nrm.p, dim, nullptr, nullptr);
+  k_sym_scale<<<nv, kSymThreads, 0, s>>>(V0.p, phi, nrm.p, vlen, nullptr, nullptr);
   ED_CHECK_LAUNCH();
   double b0 = 0.0;
   ED_CUDA(cudaMemcpyAsync(&b0, nrm.p, sizeof(double), cudaMemcpyDeviceToHost, s));
-  ED_CUDA(cudaMemsetAsync(V1.p, 0, dim * sizeof(double), s));
+  ED_CUDA(cudaMemsetAsync(V1.p, 0, vlen * sizeof(double), s));
   ED_CUDA(cudaStreamSynchronize(s));
   if (!(b0 > 0.0)) return 0;
   const double b0sq = b0 * b0;
@@ -713,8 +844,8 @@ static int sym_cf(ed_sym& T, const double* phi, double E0, double s_eh, const De
   bool have_prev = false;
   for (int n = 0; n < maxn; ++n) {
     sym_spmv(T, v, W.p, vp, beta.p + n, part.p, nb, s, tk.p, alpha.p + n);
-    k_sym_axpy_norm<<<nv, kSymThreads, 0, s>>>(W.p, v, alpha.p + n, dim, part2.p, tk.p + 1, beta.p + n + 1);
-    k_sym_scale<<<nv, kSymThreads, 0, s>>>(vp, W.p, beta.p + n + 1, dim, nullptr, nullptr);
+    k_sym_axpy_norm<<<nv, kSymThreads, 0, s>>>(W.p, v, alpha.p + n, vlen, part2.p, tk.p + 1, beta.p + n + 1);
+    k_sym_scale<<<nv, kSymThreads, 0, s>>>(vp, W.p, beta.p + n + 1, vlen, nullptr, nullptr);
     ED_CHECK_LAUNCH();
     std::swap(v, vp);
     levels = n + 1;
@@ -756,6 +887,66 @@ __global__ void k_sym_add(const double* __restrict__ x, const double* __restrict
     z[i] = x[i] + y[i];
 }
 
+// z = x + y (mode 0) or x + i y (mode 1) on n interleaved complex values
+__global__ void k_sym_combine(const double2* __restrict__ x, const double2* __restrict__ y, int64_t n, int mode,
+                              double2* __restrict__ z) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 a = x[i], b = y[i];
+    z[i] = mode ? make_double2(a.x - b.y, a.y + b.x) : make_double2(a.x + b.x, a.y + b.y);
+  }
+}
+
+// <phi_x| R |phi_y> of one part from its continued fractions: D (diagonal), and for the pair
+// rho < sigma (slot k) Pp = <phi_rho + phi_sigma| R |phi_rho + phi_sigma>, Pi the same with
+// phi_rho + i phi_sigma.  With X = Pp - D_rho - D_sigma, Y = Pi - D_rho - D_sigma:
+// <phi_rho|R|phi_sigma> = (X - i Y) / 2 and <phi_sigma|R|phi_rho> = (X + i Y) / 2.
+__device__ __forceinline__ double2 sym_pair_value(int x, int y, int nz, int iz, int nrow, const int* __restrict__ pidx,
+                                                  const double2* __restrict__ D, const double2* __restrict__ Pp,
+                                                  const double2* __restrict__ Pi) {
+  if (x == y) return D[(int64_t)x * nz + iz];
+  const int k = pidx[x * nrow + y];
+  if (k < 0) return make_double2(0.0, 0.0);
+  const double2 dx = D[(int64_t)x * nz + iz], dy = D[(int64_t)y * nz + iz];
+  const double2 p = Pp[(int64_t)k * nz + iz], q = Pi[(int64_t)k * nz + iz];
+  const double Xr = p.x - dx.x - dy.x, Xi = p.y - dx.y - dy.y;
+  const double Yr = q.x - dx.x - dy.x, Yi = q.y - dx.y - dy.y;
+  const double sg = x < y ? 1.0 : -1.0;  // x < y: (X - i Y) / 2, else (X + i Y) / 2
+  return make_double2(0.5 * (Xr + sg * Yi), 0.5 * (Xi - sg * Yr));
+}
+
+// Complex recombination (unitary M, rows c+_rho = sum_a M_rho,a c+_a):
+//   G_ab = sum_rho,sigma M_rho,a conj(M_sigma,b) (<phi^e_rho| R_e |phi^e_sigma> + <phi^h_sigma| R_h |phi^h_rho>)
+// with phi^e_rho = c+_rho Omega and phi^h_rho = c_rho Omega.  M: [nrow][ns] complex; D, Pp, Pi of
+// the electron part first, then of the hole part (offsets nrow nz and npair nz).
+__global__ void k_sym_assemble_c(int nz, int ns, int nrow, int npair, const double2* __restrict__ M,
+                                 const int* __restrict__ pidx, const double2* __restrict__ D,
+                                 const double2* __restrict__ Pp, const double2* __restrict__ Pi,
+                                 double2* __restrict__ G) {
+  const int64_t total = (int64_t)nz * ns * ns;
+  const int64_t dso = (int64_t)nrow * nz, pso = (int64_t)npair * nz;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int iz = (int)(t / (ns * ns)), a = (int)((t / ns) % ns), b = (int)(t % ns);
+    double gr = 0.0, gi = 0.0;
+    for (int r = 0; r < nrow; ++r) {
+      const double2 ma = M[r * ns + a];
+      if (ma.x == 0.0 && ma.y == 0.0) continue;
+      for (int q = 0; q < nrow; ++q) {
+        const double2 mb = M[q * ns + b];
+        if (mb.x == 0.0 && mb.y == 0.0) continue;
+        if (q != r && pidx[r * nrow + q] < 0) continue;
+        // w = M_ra conj(M_qb)
+        const double wr = ma.x * mb.x + ma.y * mb.y, wi = ma.y * mb.x - ma.x * mb.y;
+        const double2 ke = sym_pair_value(r, q, nz, iz, nrow, pidx, D, Pp, Pi);
+        const double2 kh = sym_pair_value(q, r, nz, iz, nrow, pidx, D + dso, Pp + pso, Pi + pso);
+        const double kr = ke.x + kh.x, ki = ke.y + kh.y;
+        gr += wr * kr - wi * ki;
+        gi += wr * ki + wi * kr;
+      }
+    }
+    G[t] = make_double2(gr, gi);
+  }
+}
+
 // G_ab(z) = sum over rows rho, sigma of the same irrep of M_rho,a M_sigma,b G_rho,sigma(z), with
 // G_rho,rho = D_rho and G_rho,sigma = (P_rho,sigma - D_rho - D_sigma) / 2 (the pair combination
 // of Sec. 4.3 for a real Hamiltonian).  M: [nrow][ns] (orthonormal rows); pidx[rho][sigma]: the
@@ -789,6 +980,140 @@ __global__ void k_sym_assemble(int nz, int ns, int nrow, const double* __restric
   }
 }
 
+// Green function with symmetrized operators for any Abelian group (complex characters).  Rows:
+// for every irrep beta and site orbit, c+_rho = sum_a M_rho,a c+_a with M_rho proportional to sum_g
+// chi_beta(g)^* e_{g(a)}, normalized, so that U_h c+_rho U_h^-1 = chi_beta(h) c+_rho; M is unitary.
+// c+_rho Omega lies in the irrep alpha + beta of N + 1 and c_rho Omega in alpha - beta of N - 1
+// (exponents modulo the orders); every target sector is kept in complex storage.  The diagonal
+// <phi_rho|R|phi_rho> and, for two rows of the same beta, the fractions of phi_rho + phi_sigma and
+// phi_rho + i phi_sigma give <phi_rho|R|phi_sigma> (R is not symmetric when H is complex).
+static void sym_green_general(ed_sym& S, const double* omega, int nz, double eta, int axis, int spin, double* G_out) {
+  ed_cluster& c = *S.c;
+  cudaStream_t s = c.stream;
+  const int L = c.model.L, ns = c.model.ns, ng = S.host.ng, k = S.n_gen;
+  auto digits = [&](int g) {
+    std::vector<int> a(k);
+    for (int j = 0, rest = g; j < k; rest /= S.orders[j], ++j) a[j] = rest % S.orders[j];
+    return a;
+  };
+  std::vector<std::vector<int>> gdig(ng);
+  for (int g = 0; g < ng; ++g) gdig[g] = digits(g);
+  // rows: the projection of every site orbit onto every irrep beta (element order as in sym_build)
+  std::vector<std::vector<int>> row_beta;
+  std::vector<std::vector<std::complex<double>>> row_m;
+  for (int bm = 0; bm < ng; ++bm) {
+    const std::vector<int> beta = digits(bm);
+    std::vector<char> seen(ns, 0);
+    for (int a = 0; a < ns; ++a) {
+      if (seen[a]) continue;
+      std::vector<std::complex<double>> v(L, 0.0);
+      for (int g = 0; g < ng; ++g) {
+        double ph = 0.0;
+        for (int j = 0; j < k; ++j) ph += (double)beta[j] * gdig[g][j] / S.orders[j];
+        ph -= std::floor(ph);
+        v[S.host.perm[g][a]] += std::polar(1.0, -2.0 * M_PI * ph) / (double)ng;
+        seen[S.host.perm[g][a]] = 1;
+      }
+      double nn = 0.0;
+      for (auto& x : v) nn += std::norm(x);
+      if (nn < 1e-20) continue;
+      for (auto& x : v) x /= std::sqrt(nn);
+      row_beta.push_back(beta);
+      row_m.push_back(v);
+    }
+  }
+  const int nrow = (int)row_m.size();
+  if (nrow != ns) throw Error(ED_ERR_INVALID, "symmetrized site operators do not span the sites");
+  std::vector<double> zr_h(nz), zi_h(nz);
+  for (int i = 0; i < nz; ++i) {
+    zr_h[i] = axis == ED_AXIS_MATSUBARA ? 0.0 : omega[i];
+    zi_h[i] = axis == ED_AXIS_MATSUBARA ? omega[i] : eta;
+  }
+  DevBuf<double> zr(nz), zi(nz), Wd(2 * L);
+  ED_CUDA(cudaMemcpyAsync(zr.p, zr_h.data(), nz * sizeof(double), cudaMemcpyHostToDevice, s));
+  ED_CUDA(cudaMemcpyAsync(zi.p, zi_h.data(), nz * sizeof(double), cudaMemcpyHostToDevice, s));
+  std::vector<int> pidx(nrow * nrow, -1);
+  int npair = 0;
+  for (int r = 0; r < nrow; ++r)
+    for (int q = r + 1; q < nrow; ++q)
+      if (row_beta[r] == row_beta[q]) pidx[r * nrow + q] = pidx[q * nrow + r] = npair++;
+  // electron part first, then hole part
+  DevBuf<double2> D((size_t)2 * nrow * nz), Pp((size_t)2 * std::max(1, npair) * nz),
+      Pi((size_t)2 * std::max(1, npair) * nz);
+  ED_CUDA(cudaMemsetAsync(D.p, 0, D.n * sizeof(double2), s));
+  ED_CUDA(cudaMemsetAsync(Pp.p, 0, Pp.n * sizeof(double2), s));
+  ED_CUDA(cudaMemsetAsync(Pi.p, 0, Pi.n * sizeof(double2), s));
+  const double tol = c.gf_tol > 0.0 ? c.gf_tol : 1e-12;
+  const double E0 = S.E0;
+  const int nu = S.n_up, nd = S.n_dn;
+  for (int part = 0; part < 2; ++part) {  // 0: electron (c+ Omega, N + 1), 1: hole (c Omega, N - 1)
+    const int du = spin == 0 ? (part == 0 ? 1 : -1) : 0, dd = spin == 1 ? (part == 0 ? 1 : -1) : 0;
+    if (nu + du < 0 || nu + du > L || nd + dd < 0 || nd + dd > L) continue;
+    const double s_eh = part == 0 ? 1.0 : -1.0;
+    double2* Dp = D.p + (size_t)part * nrow * nz;
+    double2* Ppp = Pp.p + (size_t)part * std::max(1, npair) * nz;
+    double2* Pip = Pi.p + (size_t)part * std::max(1, npair) * nz;
+    std::map<std::vector<int>, std::unique_ptr<ed_sym>> sectors;
+    std::vector<DevBuf<double>> phi(nrow);
+    std::vector<ed_sym*> tgt(nrow, nullptr);
+    for (int r = 0; r < nrow; ++r) {
+      std::vector<int> mt(k);  // alpha + beta (electron) or alpha - beta (hole), modulo the orders
+      for (int j = 0; j < k; ++j)
+        mt[j] = ((S.irrep[j] + (part == 0 ? row_beta[r][j] : -row_beta[r][j])) % S.orders[j] + S.orders[j]) % S.orders[j];
+      auto& T = sectors[mt];
+      if (!T) T = sym_sibling(S, nu + du, nd + dd, mt, true, s);
+      tgt[r] = T.get();
+      if (T->dim == 0) continue;
+      phi[r].alloc(2 * T->dim);
+      // weights of O: M_rho (c+_rho) or conj(M_rho) (c_rho)
+      std::vector<double> wh(2 * L);
+      for (int a = 0; a < L; ++a) {
+        wh[2 * a] = row_m[r][a].real();
+        wh[2 * a + 1] = part == 0 ? row_m[r][a].imag() : -row_m[r][a].imag();
+      }
+      ED_CUDA(cudaMemcpyAsync(Wd.p, wh.data(), 2 * L * sizeof(double), cudaMemcpyHostToDevice, s));
+      if (S.cplx)
+        k_sym_apply_c<true><<<sym_grid(T->dim, 128), 128, 0, s>>>(S.G.p, S.keys.p, S.stab.p, S.dim, S.omega.p, T->keys.p,
+                                                                  T->stab.p, T->dim, Wd.p, part == 0 ? 1 : 0, spin,
+                                                                  phi[r].p);
+      else
+        k_sym_apply_c<false><<<sym_grid(T->dim, 128), 128, 0, s>>>(S.G.p, S.keys.p, S.stab.p, S.dim, S.omega.p, T->keys.p,
+                                                                   T->stab.p, T->dim, Wd.p, part == 0 ? 1 : 0, spin,
+                                                                   phi[r].p);
+      ED_CHECK_LAUNCH();
+      ED_CUDA(cudaStreamSynchronize(s));  // Wd is rewritten for the next row
+      sym_cf(*T, phi[r].p, E0, s_eh, zr, zi, nz, tol, 1.0, Dp + (size_t)r * nz, s);
+    }
+    for (int r = 0; r < nrow; ++r)
+      for (int q = r + 1; q < nrow; ++q) {
+        const int kp = pidx[r * nrow + q];
+        if (kp < 0 || tgt[r]->dim == 0) continue;
+        const int64_t n = tgt[r]->dim;
+        DevBuf<double> sum(2 * n);
+        for (int mode = 0; mode < 2; ++mode) {
+          k_sym_combine<<<sym_grid(n, kSymThreads * 4), kSymThreads, 0, s>>>(
+              reinterpret_cast<const double2*>(phi[r].p), reinterpret_cast<const double2*>(phi[q].p), n, mode,
+              reinterpret_cast<double2*>(sum.p));
+          ED_CHECK_LAUNCH();
+          sym_cf(*tgt[r], sum.p, E0, s_eh, zr, zi, nz, tol, 1.0, (mode ? Pip : Ppp) + (size_t)kp * nz, s);
+        }
+      }
+  }
+  std::vector<double2> Mh((size_t)nrow * ns);
+  for (int r = 0; r < nrow; ++r)
+    for (int a = 0; a < ns; ++a) Mh[(size_t)r * ns + a] = make_double2(row_m[r][a].real(), row_m[r][a].imag());
+  DevBuf<double2> Mdev(Mh.size());
+  DevBuf<int> Pd(pidx.size());
+  DevBuf<double2> G((size_t)nz * ns * ns);
+  ED_CUDA(cudaMemcpyAsync(Mdev.p, Mh.data(), Mh.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
+  ED_CUDA(cudaMemcpyAsync(Pd.p, pidx.data(), pidx.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  k_sym_assemble_c<<<sym_grid((int64_t)nz * ns * ns, 256), 256, 0, s>>>(nz, ns, nrow, std::max(1, npair), Mdev.p, Pd.p,
+                                                                         D.p, Pp.p, Pi.p, G.p);
+  ED_CHECK_LAUNCH();
+  ED_CUDA(cudaMemcpyAsync(G_out, G.p, (size_t)nz * ns * ns * sizeof(double2), cudaMemcpyDeviceToHost, s));
+  ED_CUDA(cudaStreamSynchronize(s));
+}
+
 // Green function of the cluster's physical sites for one spin from the irrep ground state of S
 // (Sec. 4.6): symmetrized site operators of every irrep beta, continued fractions in the N +- 1
 // sectors of the product irrep alpha beta, recombined with the orthogonal matrix M of the
@@ -797,10 +1122,15 @@ static void sym_green(ed_sym& S, const double* omega, int nz, double eta, int ax
   ed_cluster& c = *S.c;
   cudaStream_t s = c.stream;
   if (!S.have_gs) throw Error(ED_ERR_STATE, "no ground state of this irrep yet (ed_sym_ground_state)");
+  for (int g = 0; g < S.host.ng; ++g)
+    for (int a = 0; a < c.model.ns; ++a)
+      if (S.host.perm[g][a] >= c.model.ns) throw Error(ED_ERR_INVALID, "the group maps a cluster site to a bath orbital");
+  for (int o : S.orders)
+    if (o != 2) {
+      sym_green_general(S, omega, nz, eta, axis, spin, G_out);
+      return;
+    }
   const int L = c.model.L, ns = c.model.ns, ng = 1 << S.n_gen;
-  for (int g = 0; g < ng; ++g)
-    for (int a = 0; a < ns; ++a)
-      if (S.host.perm[g][a] >= ns) throw Error(ED_ERR_INVALID, "the group maps a cluster site to a bath orbital");
   // rows: the projection of each site orbit onto each irrep beta (generator signs), normalized
   std::vector<std::vector<int>> row_sig;
   std::vector<std::vector<double>> row_m;
@@ -855,10 +1185,10 @@ static void sym_green(ed_sym& S, const double* omega, int nz, double eta, int ax
     std::vector<DevBuf<double>> phi(nrow);
     std::vector<ed_sym*> tgt(nrow, nullptr);
     for (int r = 0; r < nrow; ++r) {
-      std::vector<int> sig(S.n_gen);
-      for (int j = 0; j < S.n_gen; ++j) sig[j] = S.signs[j] * row_sig[r][j];
-      auto& T = sectors[sig];
-      if (!T) T = sym_sibling(S, nu + du, nd + dd, sig, s);
+      std::vector<int> mt(S.n_gen);  // the product irrep alpha beta (exponents modulo 2)
+      for (int j = 0; j < S.n_gen; ++j) mt[j] = (S.irrep[j] + (row_sig[r][j] < 0 ? 1 : 0)) & 1;
+      auto& T = sectors[mt];
+      if (!T) T = sym_sibling(S, nu + du, nd + dd, mt, false, s);
       tgt[r] = T.get();
       if (T->dim == 0) continue;
       phi[r].alloc(T->dim);
@@ -893,34 +1223,44 @@ static void sym_green(ed_sym& S, const double* omega, int nz, double eta, int ax
   ED_CUDA(cudaStreamSynchronize(s));
 }
 
-static void sym_validate(const ed_cluster* c, int n_gen, const int* perm, const int* signs) {
+static void sym_validate(const ed_cluster* c, int n_gen, const int* perm, const int* orders, const int* irrep) {
   if (!c) throw Error(ED_ERR_INVALID, "cluster is NULL");
   if (n_gen < 1 || n_gen > kSymMaxGen) throw Error(ED_ERR_INVALID, "need 1 to 5 generators");
-  if (!perm || !signs) throw Error(ED_ERR_INVALID, "perm and signs must not be NULL");
+  if (!perm || !orders || !irrep) throw Error(ED_ERR_INVALID, "perm, orders and the irrep must not be NULL");
   const ModelHost& m = c->model;
   const int L = m.L;
+  int64_t ng = 1;
   for (int j = 0; j < n_gen; ++j) {
-    if (signs[j] != 1 && signs[j] != -1) throw Error(ED_ERR_INVALID, "irrep signs must be +1 or -1");
+    if (orders[j] < 2) throw Error(ED_ERR_INVALID, "generator orders must be at least 2");
+    ng *= orders[j];
+    if (ng > (1 << kSymMaxGen)) throw Error(ED_ERR_INVALID, "the group has more than 32 elements");
+    if (irrep[j] < 0 || irrep[j] >= orders[j]) throw Error(ED_ERR_INVALID, "irrep exponents must lie in [0, n_k)");
     std::vector<int> seen(L, 0);
     for (int i = 0; i < L; ++i) {
       const int pi = perm[j * L + i];
       if (pi < 0 || pi >= L || seen[pi]++) throw Error(ED_ERR_INVALID, "a generator is not a permutation of the orbitals");
     }
+    // g^{n} = identity
+    std::vector<int> q(L);
+    std::iota(q.begin(), q.end(), 0);
+    for (int t = 0; t < orders[j]; ++t)
+      for (int i = 0; i < L; ++i) q[i] = perm[j * L + q[i]];
     for (int i = 0; i < L; ++i)
-      if (perm[j * L + perm[j * L + i]] != i) throw Error(ED_ERR_INVALID, "a generator is not an involution");
+      if (q[i] != i)
+        throw Error(ED_ERR_INVALID, orders[j] == 2 ? "a generator is not an involution" : "a generator's order does not divide its n");
   }
   for (int j = 0; j < n_gen; ++j)
     for (int k = j + 1; k < n_gen; ++k)
       for (int i = 0; i < L; ++i)
         if (perm[j * L + perm[k * L + i]] != perm[k * L + perm[j * L + i]])
           throw Error(ED_ERR_INVALID, "generators do not commute");
-  // independence: the 2^n_gen products are distinct
+  // independence: the prod n_k products are distinct
   std::vector<std::vector<int>> els;
-  for (int g = 0; g < (1 << n_gen); ++g) {
+  for (int g = 0; g < (int)ng; ++g) {
     std::vector<int> p(L);
     std::iota(p.begin(), p.end(), 0);
-    for (int j = 0; j < n_gen; ++j)
-      if (g >> j & 1)
+    for (int j = 0, rest = g; j < n_gen; rest /= orders[j], ++j)
+      for (int t = 0; t < rest % orders[j]; ++t)
         for (int i = 0; i < L; ++i) p[i] = perm[j * L + p[i]];
     for (auto& q : els)
       if (q == p) throw Error(ED_ERR_INVALID, "generators are not independent");
@@ -969,22 +1309,47 @@ static void sym_require_device(const ed_cluster* c) {
 
 extern "C" {
 
+static ed_status sym_create(ed_cluster* c, int n_gen, const int* perm, const int* orders, const int* irrep, ed_sym** out) {
+  if (!out) throw Error(ED_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  sym_validate(c, n_gen, perm, orders, irrep);
+  sym_require_device(c);
+  auto S = std::make_unique<ed_sym>();
+  S->c = c;
+  S->n_gen = n_gen;
+  S->n_up = c->desc.n_up;
+  S->n_dn = c->desc.n_dn;
+  S->orders.assign(orders, orders + n_gen);
+  S->irrep.assign(irrep, irrep + n_gen);
+  S->perm.assign(perm, perm + n_gen * c->model.L);
+  AllocStreamScope as_(c->stream);
+  sym_build(*S, perm, c->stream);
+  *out = S.release();
+  return ED_OK;
+}
+
 ed_status ed_sym_create(ed_cluster* c, int n_gen, const int* perm, const int* signs, ed_sym** out) {
   return sym_guard([&]() -> ed_status {
-    if (!out) throw Error(ED_ERR_INVALID, "out is NULL");
-    *out = nullptr;
-    sym_validate(c, n_gen, perm, signs);
-    sym_require_device(c);
-    auto S = std::make_unique<ed_sym>();
-    S->c = c;
-    S->n_gen = n_gen;
-    S->n_up = c->desc.n_up;
-    S->n_dn = c->desc.n_dn;
-    S->signs.assign(signs, signs + n_gen);
-    S->perm.assign(perm, perm + n_gen * c->model.L);
-    AllocStreamScope as_(c->stream);
-    sym_build(*S, perm, c->stream);
-    *out = S.release();
+    if (!signs) throw Error(ED_ERR_INVALID, "signs must not be NULL");
+    if (n_gen < 1 || n_gen > kSymMaxGen) throw Error(ED_ERR_INVALID, "need 1 to 5 generators");
+    std::vector<int> orders(n_gen, 2), m(n_gen);
+    for (int j = 0; j < n_gen; ++j) {
+      if (signs[j] != 1 && signs[j] != -1) throw Error(ED_ERR_INVALID, "irrep signs must be +1 or -1");
+      m[j] = signs[j] < 0 ? 1 : 0;
+    }
+    return sym_create(c, n_gen, perm, orders.data(), m.data(), out);
+  });
+}
+
+ed_status ed_sym_create_abelian(ed_cluster* c, int n_gen, const int* perm, const int* orders, const int* irrep,
+                                ed_sym** out) {
+  return sym_guard([&]() -> ed_status { return sym_create(c, n_gen, perm, orders, irrep, out); });
+}
+
+ed_status ed_sym_is_complex(const ed_sym* S, int* is_complex) {
+  return sym_guard([&]() -> ed_status {
+    if (!S || !is_complex) throw Error(ED_ERR_INVALID, "handle and is_complex must not be NULL");
+    *is_complex = S->cplx ? 1 : 0;
     return ED_OK;
   });
 }
@@ -1017,7 +1382,8 @@ ed_status ed_sym_matrix(const ed_sym* S, int64_t* rowptr, int32_t* col, double* 
     cudaStream_t s = S->c->stream;
     if (rowptr) ED_CUDA(cudaMemcpyAsync(rowptr, S->rowptr.p, (S->dim + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     if (col && S->nnz) ED_CUDA(cudaMemcpyAsync(col, S->col.p, S->nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    if (val && S->nnz) ED_CUDA(cudaMemcpyAsync(val, S->val.p, S->nnz * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (val && S->nnz)
+      ED_CUDA(cudaMemcpyAsync(val, S->val.p, S->nnz * (S->cplx ? 2 : 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
     ED_CUDA(cudaStreamSynchronize(s));
     return ED_OK;
   });
@@ -1052,7 +1418,8 @@ ed_status ed_sym_ground_vector(const ed_sym* S, double* out) {
     if (!S || !out) throw Error(ED_ERR_INVALID, "handle and out must not be NULL");
     if (S->omega.n == 0) throw Error(ED_ERR_STATE, "no ground state yet");
     sym_require_device(S->c);
-    ED_CUDA(cudaMemcpyAsync(out, S->omega.p, S->dim * sizeof(double), cudaMemcpyDeviceToHost, S->c->stream));
+    ED_CUDA(cudaMemcpyAsync(out, S->omega.p, S->dim * (S->cplx ? 2 : 1) * sizeof(double), cudaMemcpyDeviceToHost,
+                            S->c->stream));
     ED_CUDA(cudaStreamSynchronize(S->c->stream));
     return ED_OK;
   });

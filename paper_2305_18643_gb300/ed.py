@@ -617,6 +617,8 @@ def ed_cdmft_fit(theta, eps, z, weights, A, theta_free=None, gtol=0.0, max_iter=
 _ip = C.POINTER(C.c_int)
 _sym_sigs = {
     "ed_sym_create": (C.c_int, [C.c_void_p, C.c_int, _ip, _ip, C.POINTER(C.c_void_p)]),
+    "ed_sym_create_abelian": (C.c_int, [C.c_void_p, C.c_int, _ip, _ip, _ip, C.POINTER(C.c_void_p)]),
+    "ed_sym_is_complex": (C.c_int, [C.c_void_p, _ip]),
     "ed_sym_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "ed_sym_basis": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "ed_sym_matrix": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -636,6 +638,24 @@ def ed_sym_create(h, perms, signs):
     out = C.c_void_p()
     _check(lib().ed_sym_create(h, int(len(sg)), P.ctypes.data_as(_ip), sg.ctypes.data_as(_ip), C.byref(out)))
     return out
+
+
+def ed_sym_create_abelian(h, perms, orders, irrep):
+    """Handle of the irrep with exponents `irrep` (0 <= m_k < orders[k]) of the Abelian group
+    generated by the orbital permutations `perms` of the given orders."""
+    P = np.ascontiguousarray(np.asarray(perms, dtype=np.int32).reshape(len(orders), -1))
+    od = np.ascontiguousarray(np.asarray(orders, dtype=np.int32))
+    ir = np.ascontiguousarray(np.asarray(irrep, dtype=np.int32))
+    out = C.c_void_p()
+    _check(lib().ed_sym_create_abelian(h, int(len(od)), P.ctypes.data_as(_ip), od.ctypes.data_as(_ip),
+                                       ir.ctypes.data_as(_ip), C.byref(out)))
+    return out
+
+
+def ed_sym_is_complex(s):
+    v = C.c_int()
+    _check(lib().ed_sym_is_complex(s, C.byref(v)))
+    return bool(v.value)
 
 
 def ed_sym_info(s):
@@ -659,7 +679,7 @@ def ed_sym_matrix(s):
     d, z = ed_sym_info(s)
     rp = np.zeros(d + 1, dtype=np.int64)
     col = np.zeros(z, dtype=np.int32)
-    val = np.zeros(z, dtype=np.float64)
+    val = np.zeros(z, dtype=np.complex128 if ed_sym_is_complex(s) else np.float64)
     _check(lib().ed_sym_matrix(s, rp.ctypes.data, col.ctypes.data, val.ctypes.data))
     return rp, col, val
 
@@ -678,7 +698,7 @@ def ed_sym_ground_state(s):
 
 def ed_sym_ground_vector(s):
     d, _ = ed_sym_info(s)
-    v = np.zeros(d)
+    v = np.zeros(d, dtype=np.complex128 if ed_sym_is_complex(s) else np.float64)
     _check(lib().ed_sym_ground_vector(s, v.ctypes.data_as(_dp)))
     return v
 

@@ -1,7 +1,8 @@
 """Symmetrized sectors (Sec. 4.5) on the GPU against the symmetry oracle: the representatives and
 their stabilizers bit for bit, the stored matrix entry by entry, H.psi, and the ground energy of
 every irrep; Table 1's counts straight from the device matrix; invalid groups are refused; the
-Green function with symmetrized operators (Sec. 4.6) against the exact Lehmann sum."""
+Green function with symmetrized operators (Sec. 4.6) against the exact Lehmann sum; the same for
+Abelian groups with complex characters (rotations of order 4, ring translations)."""
 
 import json
 import os
@@ -294,6 +295,207 @@ def test_symmetrized_green_function_3x4_matches_the_unsymmetrized_path():
         try:
             G = ed.ed_sym_green(s, om, 12, axis=ed.ED_AXIS_MATSUBARA)
             assert np.max(np.abs(G - G_full)) <= 1e-8, np.max(np.abs(G - G_full))
+        finally:
+            ed.ed_sym_destroy(s)
+    finally:
+        ed.ed_cluster_destroy(hc)
+
+
+# ---- Abelian groups with complex characters (Sec. 4.5): rotations of order 4, ring translations
+
+
+def _ring(L, t1=-1.0, t2=0.0):
+    t = np.zeros((L, L))
+    for i in range(L):
+        t[i, (i + 1) % L] = t[(i + 1) % L, i] = t1
+        if t2:
+            t[i, (i + 2) % L] = t[(i + 2) % L, i] = t2
+    return t
+
+
+def _abelian_cases():
+    """(name, (t, U, mu, n_up, n_dn[, eps, theta]), generators, orders)."""
+    out = []
+    t = _ring(4)
+    tr4 = [(i + 1) % 4 for i in range(4)]
+    out.append(("ring4 C4", (t, 5.0, 2.5, 2, 2), [tr4], (4,)))
+    out.append(("ring4 C4 odd filling", (t, 5.0, 2.5, 1, 2), [tr4], (4,)))
+    out.append(("ring6 C6 t'", (_ring(6, -1.0, 0.3), 4.0, 2.0, 3, 2), [[(i + 1) % 6 for i in range(6)]], (6,)))
+    h, _, _ = rect(2, 2)
+    h[0, 3] = h[3, 0] = h[1, 2] = h[2, 1] = 0.3
+    rot = [1, 3, 0, 2]  # (x, y) -> (1 - y, x) on s = x + 2 y
+    out.append(("plaquette + bath C4", (h, 8.0, 4.0, 3, 3, np.full(4, -1.0), 0.5 * np.eye(4)),
+                [rot + [4 + v for v in rot]], (4,)))
+    t = np.zeros((8, 8))
+    for x in range(4):
+        t[x, (x + 1) % 4] = t[(x + 1) % 4, x] = -1.0
+        t[4 + x, 4 + (x + 1) % 4] = t[4 + (x + 1) % 4, 4 + x] = -1.0
+        t[x, 4 + x] = t[4 + x, x] = -0.5
+    tr = [(s + 1) % 4 + 4 * (s // 4) for s in range(8)]
+    leg = [(s + 4) % 8 for s in range(8)]
+    out.append(("ladder 2x4 Z4 x Z2", (t, 3.0, 1.5, 3, 3), [tr, leg], (4, 2)))
+    # 12-site periodic ring, the twelve momenta: sectors of about 20,000 states
+    out.append(("ring12 C12", (_ring(12, -1.0, 0.2), 4.0, 2.0, 4, 4), [[(i + 1) % 12 for i in range(12)]], (12,)))
+    return out
+
+
+def _check_abelian_irrep(hc, m, nu, nd, gens, orders, ir):
+    L = m.L
+    s = ed.ed_sym_create_abelian(hc, np.array(gens), orders, ir)
+    try:
+        bu, bd, st = S.symmetric_basis(L, nu, nd, gens, ir, orders)
+        keys, stab = ed.ed_sym_basis(s)
+        okey = (bu.astype(np.uint64) << np.uint64(L)) | bd.astype(np.uint64)
+        assert np.array_equal(keys, okey)
+        assert np.array_equal(stab.astype(np.int64), st)
+        if len(keys) == 0:
+            return None
+        Ho, _ = S.symmetric_hamiltonian(m, nu, nd, gens, ir, orders)
+        cplx = ed.ed_sym_is_complex(s)
+        assert cplx == np.iscomplexobj(Ho.data)
+        Hg = _device_csr(s)
+        assert np.array_equal(Hg.indptr, Ho.indptr) and np.array_equal(Hg.indices, Ho.indices)
+        assert np.max(np.abs(Hg.data - Ho.data)) <= 1e-14 * max(1.0, np.max(np.abs(Ho.data)))
+        rng = np.random.default_rng(len(keys))
+        x = rng.standard_normal(len(keys)) + (1j * rng.standard_normal(len(keys)) if cplx else 0.0)
+        xd = torch.tensor(x, device="cuda")
+        yd = torch.empty_like(xd)
+        ed.ed_sym_hpsi(s, xd.data_ptr(), yd.data_ptr())
+        ref = Ho @ x
+        assert np.max(np.abs(yd.cpu().numpy() - ref)) <= 1e-13 * max(1.0, np.max(np.abs(ref)))
+        E, res, it, st_ = ed.ed_sym_ground_state(s)
+        Eo = S.irrep_ground_energy(m, nu, nd, gens, ir, orders=orders)
+        assert abs(E - Eo) <= 1e-10 * max(1.0, abs(Eo)), (E, Eo)
+        assert res <= 1e-12 * max(1.0, abs(E))
+        w = ed.ed_sym_ground_vector(s)
+        assert np.iscomplexobj(w) == cplx
+        assert abs(np.linalg.norm(w) - 1.0) < 1e-12
+        assert np.linalg.norm(Ho @ w - E * w) <= 1e-11 * max(1.0, abs(E))
+        return E
+    finally:
+        ed.ed_sym_destroy(s)
+
+
+@pytest.mark.parametrize("case", _abelian_cases(), ids=lambda c: c[0])
+def test_abelian_sector_matches_oracle(case):
+    """Every irrep of a group with complex characters: representatives and stabilizers bit for
+    bit, the complex Hermitian matrix entry by entry, H.psi on complex device vectors, the irrep's
+    ground energy and vector; the lowest irrep energy is the sector's ground energy."""
+    name, params, gens, orders = case
+    t, U, mu, nu, nd = params[:5]
+    eps, theta = (params[5], params[6]) if len(params) > 5 else (None, None)
+    hc, m = _cluster(t, U, mu, nu, nd, eps, theta)
+    try:
+        Es = [e for ir in S.all_irreps(len(gens), orders)
+              if (e := _check_abelian_irrep(hc, m, nu, nd, gens, orders, ir)) is not None]
+        E0, _, _ = ground_state(sector_hamiltonian(m, nu, nd))
+        assert abs(min(Es) - E0) <= 1e-10 * max(1.0, abs(E0))
+    finally:
+        ed.ed_cluster_destroy(hc)
+
+
+def test_abelian_handle_with_sign_irreps_equals_the_involution_handle():
+    """Orders 2 and exponents m_j = (1 - sign_j) / 2 name the same irrep as the signs."""
+    h, mx, my = rect(3, 2)
+    hc, m = _cluster(h, 4.0, 2.0, 3, 3)
+    try:
+        for signs in S.all_irreps(2):
+            a = ed.ed_sym_create(hc, np.array([mx, my]), signs)
+            b = ed.ed_sym_create_abelian(hc, np.array([mx, my]), (2, 2), [(1 - v) // 2 for v in signs])
+            try:
+                assert not ed.ed_sym_is_complex(a) and not ed.ed_sym_is_complex(b)
+                for x, y in zip(ed.ed_sym_matrix(a), ed.ed_sym_matrix(b)):
+                    assert np.array_equal(x, y)
+            finally:
+                ed.ed_sym_destroy(a)
+                ed.ed_sym_destroy(b)
+    finally:
+        ed.ed_cluster_destroy(hc)
+
+
+def test_invalid_abelian_groups_are_refused():
+    t = _ring(6)
+    hc, m = _cluster(t, 4.0, 2.0, 3, 3)
+    tr = [(i + 1) % 6 for i in range(6)]
+    inv = [(-i) % 6 for i in range(6)]
+    try:
+        bad = [
+            ([tr], (4,), [0]),            # g^4 is not the identity
+            ([tr], (6,), [6]),            # exponent out of range
+            ([tr], (6,), [-1]),           # exponent out of range
+            ([tr], (1,), [0]),            # order below 2
+            ([tr, inv], (6, 2), [0, 0]),  # the reflection does not commute with the translation
+            ([tr, [(i + 3) % 6 for i in range(6)]], (6, 2), [0, 0]),  # dependent: t^3
+            ([tr, tr, tr], (6, 6, 6), [0, 0, 0]),  # more than 32 elements
+        ]
+        for perms, orders, ir in bad:
+            with pytest.raises(ed.EDError) as e:
+                ed.ed_sym_create_abelian(hc, np.array(perms), orders, ir)
+            assert e.value.status == ed.ED_ERR_INVALID, (perms, orders, ir)
+    finally:
+        ed.ed_cluster_destroy(hc)
+
+
+def _ground_irrep_abelian(hc, gens, orders):
+    """The irrep holding the sector's ground state: (exponents, handle with its ground state, E)."""
+    best = None
+    for ir in S.all_irreps(len(gens), orders):
+        s = ed.ed_sym_create_abelian(hc, np.array(gens), orders, ir)
+        d, _ = ed.ed_sym_info(s)
+        if d == 0:
+            ed.ed_sym_destroy(s)
+            continue
+        E = ed.ed_sym_ground_state(s)[0]
+        if best is None or E < best[2] - 1e-9:
+            if best is not None:
+                ed.ed_sym_destroy(best[1])
+            best = (ir, s, E)
+        else:
+            ed.ed_sym_destroy(s)
+    return best
+
+
+def _abelian_gf_cases():
+    """Clusters of _abelian_cases whose sector ground state is not degenerate, and a half-filled
+    ladder; G is unique there."""
+    keep = {"ring4 C4", "plaquette + bath C4", "ladder 2x4 Z4 x Z2"}
+    out = [c for c in _abelian_cases() if c[0] in keep]
+    t = _ring(6, -1.0, 0.3)
+    out.append(("ring6 C6 t' 3/3", (t, 4.0, 2.0, 3, 3), [[(i + 1) % 6 for i in range(6)]], (6,)))
+    lad = [c for c in _abelian_cases() if c[0] == "ladder 2x4 Z4 x Z2"][0]
+    out.append(("ladder 2x4 Z4 x Z2 half filling", (lad[1][0], 3.0, 1.5, 4, 4), lad[2], lad[3]))
+    # translations alone: two site orbits (the legs), so every irrep beta has two rows and the
+    # off-diagonal fractions (phi_rho + phi_sigma, phi_rho + i phi_sigma) are needed
+    out.append(("ladder 2x4 Z4 only", (lad[1][0], 3.0, 1.5, 3, 3), lad[2][:1], lad[3][:1]))
+    out.append(("ladder 2x4 Z4 only half filling", (lad[1][0], 3.0, 1.5, 4, 4), lad[2][:1], lad[3][:1]))
+    return out
+
+
+@pytest.mark.parametrize("case", _abelian_gf_cases(), ids=lambda c: c[0])
+def test_abelian_green_function_matches_oracle(case):
+    """Sec. 4.6 with complex characters: G of the ground state from symmetrized operators of
+    every irrep (complex unitary M), continued fractions in the complex N +- 1 irrep sectors
+    (alpha + beta for c+, alpha - beta for c), off-diagonal terms from the fractions of
+    phi_rho + phi_sigma and phi_rho + i phi_sigma, against the exact Lehmann sum of the
+    unsymmetrized sectors (real axis, eta = 0.1, and Matsubara axis, beta = 50), both spins."""
+    name, params, gens, orders = case
+    t, U, mu, nu, nd = params[:5]
+    eps, theta = (params[5], params[6]) if len(params) > 5 else (None, None)
+    hc, m = _cluster(t, U, mu, nu, nd, eps, theta)
+    try:
+        ir, s, E = _ground_irrep_abelian(hc, gens, orders)
+        try:
+            om_r = np.linspace(-8.0, 8.0, 48)
+            om_m = (2 * np.arange(24) + 1) * np.pi / 50.0
+            for spin in (0, 1):
+                Gr, _, _, E0o, gap = O_green_exact(m, nu, nd, om_r + 0.1j, spin)
+                assert gap > 1e-6, "the cases are chosen with a non-degenerate ground state"
+                assert abs(E - E0o) <= 1e-10 * max(1.0, abs(E0o))
+                G = ed.ed_sym_green(s, om_r, m.ns, eta=0.1, axis=ed.ED_AXIS_REAL, spin=spin)
+                assert np.max(np.abs(G - Gr)) <= 1e-8, np.max(np.abs(G - Gr))
+                Gm = O_green_exact(m, nu, nd, 1j * om_m, spin)[0]
+                G = ed.ed_sym_green(s, om_m, m.ns, axis=ed.ED_AXIS_MATSUBARA, spin=spin)
+                assert np.max(np.abs(G - Gm)) <= 1e-8, np.max(np.abs(G - Gm))
         finally:
             ed.ed_sym_destroy(s)
     finally:
