@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+import oracle_memo as OM
 from paper_2305_18643_gb300 import build, ed
 from paper_2305_18643_gb300 import workloads as W
 
@@ -81,7 +82,8 @@ def test_low_states_match_oracle(name, c, k):
     to 1e-10 relative, residuals to 1e-12; the 12-orbital sector takes the two-pass H.psi when
     forced (ED_OPT_TWO_PASS_MIN_BYTES = 0)."""
     m = _model(c)
-    Eref, V = O.low_states(O.sector_hamiltonian(m, c["n_up"], c["n_dn"]), k)
+    with OM.dense_blas_threads():
+        Eref, V = O.low_states(O.sector_hamiltonian(m, c["n_up"], c["n_dn"]), k)
     with ed.Cluster(c) as cl:
         if name == "2x2+bath":
             ed.ed_set_option(cl.h, ed.ED_OPT_TWO_PASS_MIN_BYTES, 0)

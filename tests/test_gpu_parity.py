@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+import oracle_memo as OM
 from paper_2305_18643_gb300 import build, ed
 from paper_2305_18643_gb300 import workloads as W
 
@@ -120,7 +121,7 @@ def test_hpsi_full_size_sampled(padded):
     vectors, used by the benchmark) the two-pass kernels run; contiguous rows take the one-pass
     kernel.  d_up = 12,870 is ragged for the 4-row groups and the 64-row blocks."""
     c = W.periodic_4x4()
-    op = O.sector_hamiltonian(_model(c), 8, 8)
+    op = OM.sector_hamiltonian(_model(c), 8, 8)
     du, dd = op.shape2
     ld = (dd + 127) // 128 * 128 if padded else dd
     rng = np.random.default_rng(5)
@@ -171,7 +172,7 @@ def test_ground_state_full_size_properties():
 def test_ground_state_2x4():
     c = W.plain_2x4()
     m = _model(c)
-    E0, Om, gap = O.ground_state(O.sector_hamiltonian(m, 4, 4))
+    E0, Om, gap = OM.ground_state(m, 4, 4)
     with ed.Cluster(c) as cl:
         st, E, res, it = cl.ground_state()
         assert st == ed.ED_OK
@@ -201,7 +202,7 @@ def test_ground_state_free_fermions():
 def test_ground_state_cdmft_impurity(precision):
     """2x2 plaquette + 8 bath orbitals, d = 853,776: FP64 and FP32-storage forms, E0 to 1e-10."""
     c = W.cdmft_2x2_bath()
-    E0, _, _ = O.ground_state(O.sector_hamiltonian(_model(c), 6, 6))
+    E0, _, _ = OM.ground_state(_model(c), 6, 6)
     with ed.Cluster(c, precision=precision) as cl:
         st, E, res, it = cl.ground_state()
     assert st in (ed.ED_OK, ed.ED_WARN_DEGENERATE)
@@ -214,7 +215,7 @@ def test_green_2x4_continued_fraction():
     c = W.plain_2x4()
     om = W.real_grid(1000)
     z = om + 0.05j
-    Gref = O.green_exact(_model(c), 4, 4, z)[0]
+    Gref = OM.green_exact(_model(c), 4, 4, z)[0]
     with ed.Cluster(c) as cl:
         st, G = ed.ed_green(cl.h, om, 0.05, 8)
     assert np.max(np.abs(G - Gref)) <= 1e-8
@@ -237,7 +238,7 @@ def test_green_matches_exact(name, c, spin, axis):
     else:
         om = W.matsubara_grid(256, 50.0)
         z = 1j * om
-    Gref, Q, w, E0, gap = O.green_exact(m, c["n_up"], c["n_dn"], z, spin=spin)
+    Gref, Q, w, E0, gap = OM.green_exact(m, c["n_up"], c["n_dn"], z, spin=spin)
     with ed.Cluster(c) as cl:
         st, G = ed.ed_green(cl.h, om, 0.05, m.ns, axis=axis, spin=spin)
     assert np.max(np.abs(G - Gref)) <= 1e-8
@@ -249,7 +250,7 @@ def test_green_band_matches_exact(name, c, spin):
     """Band Lanczos run until the block Krylov space is exhausted equals the exact Lehmann sum."""
     m = _model(c)
     om = W.real_grid(301)
-    Gref = O.green_exact(m, c["n_up"], c["n_dn"], om + 0.05j, spin=spin)[0]
+    Gref = OM.green_exact(m, c["n_up"], c["n_dn"], om + 0.05j, spin=spin)[0]
     with ed.Cluster(c, gf_method=ed.ED_GF_BAND) as cl:
         st, G = ed.ed_green(cl.h, om, 0.05, m.ns, spin=spin)
     assert st in (ed.ED_OK, ed.ED_WARN_DEGENERATE)
@@ -259,7 +260,7 @@ def test_green_band_matches_exact(name, c, spin):
 def test_green_band_2x4():
     c = W.plain_2x4()
     om = W.real_grid(1000)
-    Gref = O.green_exact(_model(c), 4, 4, om + 0.05j)[0]
+    Gref = OM.green_exact(_model(c), 4, 4, om + 0.05j)[0]
     with ed.Cluster(c, gf_method=ed.ED_GF_BAND) as cl:
         st, G = ed.ed_green(cl.h, om, 0.05, 8)
     assert np.max(np.abs(G - Gref)) <= 1e-8
@@ -316,12 +317,12 @@ def test_batch_matches_oracle(precision):
     E0, res, st, it, G = ed.ed_batch_solve(fam, precision=precision, omega=om, eta=0.05, cf_max_levels=20000)
     for k, c in enumerate(fam):
         m = _model(c)
-        Gu, _, _, Eref, gap = O.green_exact(m, c["n_up"], c["n_dn"], om + 0.05j, spin=0)
+        Gu, _, _, Eref, gap = OM.green_exact(m, c["n_up"], c["n_dn"], om + 0.05j, spin=0)
         assert abs(E0[k] - Eref) <= 1e-10 * max(1.0, abs(Eref)), (k, c["name"])
         if gap < 1e-6:
             continue  # degenerate ground state: G is not unique (Sec. 4.2)
         if precision == ed.ED_FP64:
-            Gd = O.green_exact(m, c["n_up"], c["n_dn"], om + 0.05j, spin=1)[0]
+            Gd = OM.green_exact(m, c["n_up"], c["n_dn"], om + 0.05j, spin=1)[0]
             assert np.max(np.abs(G[k][0] - Gu)) <= 1e-8, (k, c["name"])
             assert np.max(np.abs(G[k][1] - Gd)) <= 1e-8, (k, c["name"])
 

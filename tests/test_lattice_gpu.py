@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+import oracle_memo as OM
 from oracle import lattice_oracle as LO
 from paper_2305_18643_gb300 import build, ed
 from paper_2305_18643_gb300 import workloads as W
@@ -47,7 +48,7 @@ def plaquette_gc():
     m = O.Model(c["t"], c["U"], c["mu"], c["eps"], c["theta"])
     om = W.matsubara_grid(96, 50.0)
     z = 1j * om
-    Gc, Q, w, E0, gap = O.green_exact(m, 4, 4, z)
+    Gc, Q, w, E0, gap = OM.green_exact(m, 4, 4, z)
     return c, m, om, z, Gc
 
 
@@ -189,7 +190,7 @@ def test_cdmft_iteration_through_the_solver():
         st, Gc = ed.ed_green(cl.h, om, 0.0, 2, axis=ed.ED_AXIS_MATSUBARA)
     Gam = ed.ed_hybridization(theta, eps, z)
     A = ed.ed_cdmft_target(lat, Gc, kt, Gamma=Gam)
-    Gc_o = O.green_exact(m, 3, 3, z)[0]
+    Gc_o = OM.green_exact(m, 3, 3, z)[0]
     A_o = LO.cdmft_target(Gc_o, z, m.h[:2, :2], LO.hybridization(theta, eps, z),
                           LO.inter_cluster(lat["bonds"], 2, lat["E"], kt))
     assert np.max(np.abs(A - A_o)) <= 1e-7 * max(1.0, np.max(np.abs(A_o)))

@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+import oracle_memo as OM
 from paper_2305_18643_gb300 import build, ed
 from paper_2305_18643_gb300 import workloads as W
 
@@ -83,7 +84,7 @@ def test_served_results_match_the_oracle():
     for (r, G), c in zip(out, clusters):
         m = _model(c)
         for spin in (0, 1):
-            Gx, _, _, E0, gap = O.green_exact(m, c["n_up"], c["n_dn"], om + 0.05j, spin=spin)
+            Gx, _, _, E0, gap = OM.green_exact(m, c["n_up"], c["n_dn"], om + 0.05j, spin=spin)
             assert abs(r["E0"] - E0) <= 1e-10 * max(1.0, abs(E0))
             if gap > 1e-6:
                 assert np.max(np.abs(G[spin] - Gx)) <= 1e-8
@@ -152,7 +153,7 @@ def test_wait_timeout_cancel_and_host_failure():
     assert rf["status"] == ed.ED_ERR_CUDA
     assert st["failed"] == 1 and st["cancelled"] == 1 and st["completed"] == 2
     m = _model(small)
-    Gx, _, _, E0, _ = O.green_exact(m, 4, 4, om + 0.05j, spin=0)
+    Gx, _, _, E0, _ = OM.green_exact(m, 4, 4, om + 0.05j, spin=0)
     assert abs(ro["E0"] - E0) <= 1e-10 * abs(E0)
     assert np.max(np.abs(Go[0] - Gx)) <= 1e-8
 

@@ -12,6 +12,7 @@ import pytest
 import scipy.sparse as sp
 
 import oracle.symmetry_oracle as S
+import oracle_memo as OM
 from oracle.ed_oracle import Model, ground_state, sector_hamiltonian
 from paper_2305_18643_gb300 import build, ed
 
@@ -114,7 +115,8 @@ def _check_irrep(hc, m, L, nu, nd, gens, ir):
         y = yd.cpu().numpy()
         assert np.max(np.abs(y - Ho @ x)) <= 1e-13 * max(1.0, np.max(np.abs(Ho @ x)))
         E, res, it, st_ = ed.ed_sym_ground_state(s)
-        Eo = S.irrep_ground_energy(m, nu, nd, gens, ir)
+        with OM.dense_blas_threads():
+            Eo = S.irrep_ground_energy(m, nu, nd, gens, ir)
         assert abs(E - Eo) <= 1e-10 * max(1.0, abs(Eo)), (E, Eo)
         assert res <= 1e-12 * max(1.0, abs(E))
         w = ed.ed_sym_ground_vector(s)
@@ -132,7 +134,7 @@ def test_symmetrized_sector_matches_oracle(case):
     try:
         Es = [e for ir in S.all_irreps(len(gens)) if (e := _check_irrep(hc, m, m.L, nu, nd, gens, ir)) is not None]
         # the lowest irrep energy is the sector's ground energy
-        E0, _, _ = ground_state(sector_hamiltonian(m, nu, nd))
+        E0, _, _ = OM.ground_state(m, nu, nd)
         assert abs(min(Es) - E0) <= 1e-10 * max(1.0, abs(E0))
     finally:
         ed.ed_cluster_destroy(hc)
@@ -185,8 +187,9 @@ def test_3x4_ground_energy_in_a1_matches_the_full_sector():
             assert np.array_equal(Hg.indices, Ho.indices)
             assert np.max(np.abs(Hg.data - Ho.data)) <= 1e-13
             E, res, it, st = ed.ed_sym_ground_state(s)
-            E0, _, _ = ground_state(sector_hamiltonian(m, 6, 6))
-            Ea1 = S.irrep_ground_energy(m, 6, 6, [mx, my], (1, 1))
+            E0, _, _ = OM.ground_state(m, 6, 6)
+            with OM.dense_blas_threads():
+                Ea1 = S.irrep_ground_energy(m, 6, 6, [mx, my], (1, 1))
             assert abs(E - Ea1) <= 1e-10 * abs(Ea1)
             assert E >= E0 - 1e-10 * abs(E0)
             assert res <= 1e-12 * max(1.0, abs(E))
@@ -275,9 +278,7 @@ def test_symmetrized_green_function_matches_oracle(case):
 
 
 def O_green_exact(m, nu, nd, z, spin):
-    from oracle.ed_oracle import green_exact
-
-    return green_exact(m, nu, nd, np.asarray(z), spin=spin)
+    return OM.green_exact(m, nu, nd, np.asarray(z), spin=spin)
 
 
 def test_symmetrized_green_function_3x4_matches_the_unsymmetrized_path():
@@ -364,7 +365,8 @@ def _check_abelian_irrep(hc, m, nu, nd, gens, orders, ir):
         ref = Ho @ x
         assert np.max(np.abs(yd.cpu().numpy() - ref)) <= 1e-13 * max(1.0, np.max(np.abs(ref)))
         E, res, it, st_ = ed.ed_sym_ground_state(s)
-        Eo = S.irrep_ground_energy(m, nu, nd, gens, ir, orders=orders)
+        with OM.dense_blas_threads():
+            Eo = S.irrep_ground_energy(m, nu, nd, gens, ir, orders=orders)
         assert abs(E - Eo) <= 1e-10 * max(1.0, abs(Eo)), (E, Eo)
         assert res <= 1e-12 * max(1.0, abs(E))
         w = ed.ed_sym_ground_vector(s)
@@ -388,7 +390,7 @@ def test_abelian_sector_matches_oracle(case):
     try:
         Es = [e for ir in S.all_irreps(len(gens), orders)
               if (e := _check_abelian_irrep(hc, m, nu, nd, gens, orders, ir)) is not None]
-        E0, _, _ = ground_state(sector_hamiltonian(m, nu, nd))
+        E0, _, _ = OM.ground_state(m, nu, nd)
         assert abs(min(Es) - E0) <= 1e-10 * max(1.0, abs(E0))
     finally:
         ed.ed_cluster_destroy(hc)
