@@ -20,6 +20,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+import oracle_memo as OM
 from paper_2305_18643_gb300 import build, ed
 from paper_2305_18643_gb300 import workloads as W
 
@@ -57,10 +58,25 @@ def _force_two_pass(cl):
     ed.ed_set_option(cl.h, ed.ED_OPT_TWO_PASS_MIN_BYTES, 0)
 
 
+def _three_magnitude_chain():
+    """A 6-site ring with bond values -1, -0.5, +0.7: three magnitudes, so the row pass selects
+    among the signed values (the 2x4 cluster and the 3x3 lattice below use the two-magnitude
+    form, the random clusters the table of values in shared memory)."""
+    T = np.zeros((6, 6))
+    for i, v in enumerate([-1.0, -0.5, 0.7, -1.0, -0.5, 0.7]):
+        j = (i + 1) % 6
+        T[i, j] = T[j, i] = v
+    return W._cluster("6-ring, three magnitudes", T, 4.0, 2.0, 3, 2)
+
+
 SMALL = [("2x4", W.plain_2x4()),
          ("rand-bath", W.random_cluster(np.random.default_rng(3), 3, 3, 2, 4)),
          ("chain5", W.random_cluster(np.random.default_rng(4), 5, 0, 1, 4)),
-         ("2x2+bath", W.cdmft_2x2_bath())]
+         ("2x2+bath", W.cdmft_2x2_bath()),
+         # t = -1 and t' = +-0.3 with seeded signs: two magnitudes, values of both signs
+         ("3x3-tp-signs", W._cluster("3x3 open, t' of seeded sign", W.lattice_hopping(
+             3, 3, tp=0.3, rng=np.random.default_rng(7), seeded_tp_sign=True), 8.0, 4.0, 5, 4)),
+         ("ring6-3mag", _three_magnitude_chain())]
 
 
 # ------------------------------------------------------------------ H.psi, element by element
@@ -69,7 +85,8 @@ SMALL = [("2x4", W.plain_2x4()),
 def test_two_pass_hpsi_matches_oracle(name, c, shift):
     """Rows padded to a multiple of 128 elements (the solver's own layout) and the option at 0:
     ed_hpsi runs the two-pass kernels.  d_up values of 70, 35, 10 and 924 leave ragged 4-row
-    groups and 64-row blocks; every padding element must stay zero."""
+    groups and 64-row blocks (also 126 and 20 for the last two clusters); every padding element
+    must stay zero.  The clusters cover the three ways the row pass finds a hop's value."""
     m = _model(c)
     nu, nd = c["n_up"] + shift[0], c["n_dn"] + shift[1]
     if not (0 <= nu <= m.L and 0 <= nd <= m.L):
@@ -116,7 +133,7 @@ def test_two_pass_option_changes_the_kernels():
 @pytest.mark.parametrize("precision", [ed.ED_FP64, ed.ED_FP32], ids=["fp64", "fp32"])
 def test_two_pass_ground_state_2x4(precision):
     c = W.plain_2x4()
-    E0, Om, gap = O.ground_state(O.sector_hamiltonian(_model(c), 4, 4))
+    E0, Om, gap = OM.ground_state(_model(c), 4, 4)
     with ed.Cluster(c, precision=precision) as cl:
         _force_two_pass(cl)
         st, E, res, it = cl.ground_state()
@@ -133,7 +150,7 @@ def test_two_pass_green_2x4(method):
     against the exact Lehmann sum (Eq. spectral1), with the two-pass kernels in every run."""
     c = W.plain_2x4()
     om = W.real_grid(1000)
-    Gref = O.green_exact(_model(c), 4, 4, om + 0.05j)[0]
+    Gref = OM.green_exact(_model(c), 4, 4, om + 0.05j)[0]
     with ed.Cluster(c, gf_method=method) as cl:
         _force_two_pass(cl)
         st, G = ed.ed_green(cl.h, om, 0.05, 8)
@@ -157,7 +174,7 @@ def test_two_pass_green_matches_exact(name, c, spin, method, axis):
     else:
         om = W.matsubara_grid(256, 50.0)
         z = 1j * om
-    Gref = O.green_exact(m, c["n_up"], c["n_dn"], z, spin=spin)[0]
+    Gref = OM.green_exact(m, c["n_up"], c["n_dn"], z, spin=spin)[0]
     with ed.Cluster(c, gf_method=method) as cl:
         _force_two_pass(cl)
         st, G = ed.ed_green(cl.h, om, 0.05, m.ns, axis=axis, spin=spin)
@@ -246,7 +263,7 @@ def test_fp32_green_within_stated_bound(name, c, spin, method, axis):
     else:
         om = W.matsubara_grid(256, 50.0)
         z, tol = 1j * om, FP32_G_TOL_MATSUBARA
-    Gref, Q, w, E0, gap = O.green_exact(m, c["n_up"], c["n_dn"], z, spin=spin)
+    Gref, Q, w, E0, gap = OM.green_exact(m, c["n_up"], c["n_dn"], z, spin=spin)
     with ed.Cluster(c, precision=ed.ED_FP32, gf_method=method) as cl:
         st, E, res, it = cl.ground_state()
         stg, G = ed.ed_green(cl.h, om, 0.05, m.ns, axis=axis, spin=spin)
