@@ -129,22 +129,7 @@ void build_model(const ed_cluster_desc* desc, ModelHost& m, HopParams& hp) {
       m.pair_b.push_back(b);
       m.pair_vidx.push_back(idx);
     }
-  std::vector<double> mags;
-  for (double v : m.vals) {
-    const double a = std::fabs(v);
-    if (std::find(mags.begin(), mags.end(), a) == mags.end()) mags.push_back(a);
-  }
-  m.nmag = (!m.vals.empty() && mags.size() <= 2) ? (int)mags.size() : 0;
-  std::memset(&m.mm, 0, sizeof(m.mm));
-  for (size_t k = 0; m.nmag && k < m.vals.size(); ++k) {
-    m.mm.mag[k] = (uint8_t)(std::fabs(m.vals[k]) == mags[0] ? 0 : 1);
-    m.mm.neg[k] = (uint8_t)(m.vals[k] < 0.0 ? 1 : 0);
-  }
   std::memset(&hp, 0, sizeof(hp));
-  for (int k = 0; k < m.nmag; ++k) {
-    hp.mag[k] = mags[k];
-    hp.magf[k] = (float)mags[k];
-  }
   for (size_t k = 0; k < m.vals.size(); ++k) {
     hp.val[k] = m.vals[k];
     hp.valf[k] = (float)m.vals[k];
@@ -215,9 +200,6 @@ SectorView ed_cluster::view(int n_up, int n_dn, int64_t ld) {
   v.ptr_dn = d.ptr.p;
   v.ent_dn = d.ent.p;
   v.ell_dn = d.ell.p;
-  v.ell_up = u.ell.p;
-  v.ell_mag = d.ell_mag ? 1 : 0;
-  v.up_slots = u.zmax + kEllPad;
   v.e_up = u.ediag.p;
   v.e_dn = d.ediag.p;
   v.e_up32 = u.ediag32.p;

@@ -30,27 +30,9 @@ __host__ __device__ inline uint32_t ent_vidx(uint32_t e) { return e & 127u; }
 __host__ __device__ inline uint32_t row_ell_pack(uint32_t e) {
   return (ent_col(e) << 14) | (((ent_vidx(e) << 1) | ent_neg(e)) << 2);
 }
-// Magnitude form of the row kernel's entries, used when the off-diagonal values take at most two
-// distinct magnitudes (a nearest-neighbour t and a second-neighbour t' of either sign, the
-// lattices of Secs. 2-6): bit 31 = sign of the term (fermionic sign times the sign of the value),
-// bit 30 = which magnitude, bits 4..21 = byte offset col * 16 of the column's 16-byte group in
-// shared memory.  The kernel then needs one select and one sign flip per hop.  col < 2^18.
-struct MagMap {
-  uint8_t mag[kMaxVals];  // value index -> magnitude index (0 or 1)
-  uint8_t neg[kMaxVals];  // value index -> 1 if the value is negative
-};
-__host__ __device__ inline uint32_t row_ell_pack_mag(uint32_t e, const MagMap& mm) {
-  const uint32_t v = ent_vidx(e);
-  return ((ent_neg(e) ^ (uint32_t)mm.neg[v]) << 31) | ((uint32_t)mm.mag[v] << 30) | (ent_col(e) << 4);
-}
-constexpr uint32_t kMagAddrMask = 0x003FFFF0u;
-
 // Slots of zeros after the last slot of the row kernel's table, so that it may load ahead
-// without bounds checks (the row kernel loads this many slots ahead of their use).
-#ifndef ED_ELL_PAD
-#define ED_ELL_PAD 8
-#endif
-constexpr int kEllPad = ED_ELL_PAD;
+// without bounds checks.
+constexpr int kEllPad = 8;
 
 struct Error : public std::runtime_error {
   ed_status code;
@@ -175,8 +157,6 @@ struct ModelHost {
   std::vector<double> U;        // L (0 on bath)
   std::vector<double> vals;     // distinct off-diagonal h values
   std::vector<int> pair_a, pair_b, pair_vidx;  // ordered pairs with h[a][b] != 0, a != b
-  int nmag = 0;                 // 1 or 2: distinct |values| (row tables in magnitude form); 0: more
-  MagMap mm{};
 };
 
 // Parameters passed to kernels by value.
@@ -190,8 +170,6 @@ struct HopParams {
   int uniform_u;    // 1: every orbital of umask has the same U (u0), so sum_i U_i n_i n_i = u0 popc(...)
   double u0;
   float u0f;
-  double mag[2];    // the magnitudes of the magnitude form (ModelHost::nmag > 0)
-  float magf[2];
 };
 
 // One spin's sector with N particles: basis, two-level rank tables, hopping table, diagonal.
@@ -205,7 +183,6 @@ struct SpinTables {
   DevBuf<uint32_t> ent;        // [nnz]
   int zmax = 0;                // longest row of the table
   DevBuf<uint32_t> ell;        // [zmax][dim] slot-major copy: ell[k * dim + r] = k-th entry of row r
-  bool ell_mag = false;        // ell entries in the magnitude form (row_ell_pack_mag)
   DevBuf<double> ediag;        // [dim] sum_a h_aa n_a
   DevBuf<float> ediag32;       // [dim]
 };
@@ -220,9 +197,6 @@ struct SectorView {
   const int32_t* ptr_dn;
   const uint32_t* ent_dn;
   const uint32_t* ell_dn;   // slot-major down-spin table (coalesced across a warp's columns)
-  const uint32_t* ell_up;   // slot-major up-spin table (the column pass reads one row's slots)
-  int ell_mag;              // ell_dn and ell_up hold magnitude-form entries
-  int up_slots;             // slots of ell_up (its longest row + kEllPad)
   const double* e_up;
   const double* e_dn;
   const float* e_up32;

@@ -132,27 +132,7 @@ struct Vec<double> {
   }
 };
 
-// Column kernel: 16-byte operand loads in flight per lane, and the blocks per SM its registers
-// are sized for.
-#ifndef ED_COL_UNROLL
-#define ED_COL_UNROLL 8
-#endif
-#ifndef ED_COL_MINB
-#define ED_COL_MINB 3
-#endif
-constexpr int kColUnroll = ED_COL_UNROLL;
-constexpr int kColMinBlocks = ED_COL_MINB;
-
-// Threads of the row kernel (one block per SM: the staged rows take most of shared memory).
-#ifndef ED_ROW_THREADS
-#define ED_ROW_THREADS 1024
-#endif
-constexpr int kRowThreads = ED_ROW_THREADS;
-#if ED_ROW_THREADS == 1024
-#define ED_ROW_BOUNDS __launch_bounds__(1024)
-#else
-#define ED_ROW_BOUNDS __launch_bounds__(ED_ROW_THREADS, 1)
-#endif
+constexpr int kRowThreads = 1024;
 
 // Per-thread partial sums of <x,w>, <w,w>, <x,x>: FP64 for FP64 vectors; compensated (Kahan)
 // FP32 for FP32 vectors, so that no per-element FP64 arithmetic is needed (FP64 runs at a
@@ -267,18 +247,14 @@ struct Acc16<double> {
 
 // Row pass: O[u][:] = (D + K_dn) X[u][:] - b O[u][:] for R interleaved rows per step.  The rows
 // are staged in shared memory as 16-byte groups (one per column); each thread owns columns d and
-// gathers the groups sx[col] of its hops.  The slot-major entries carry the byte offset of the
-// group, so a hop costs one table load, one shared gather, the choice of its value and the FMAs.
-// The value comes, by MODE:
-//   0  from a table of signed values in shared memory (entry bits 2..9 = its byte offset);
-//   1  from registers when the cluster has at most four distinct values (entry bits 3..4 = which,
-//      bit 2 = the fermionic sign);
-//   2  from registers in the magnitude form (row_ell_pack_mag): one select between two
-//      magnitudes and a sign flip taken from the entry's top bit.
-// Table loads run one chunk of kPre slots ahead of their use, alternating between two register
-// chunks (the table has kEllPad zero slots at its end, so the look-ahead needs no bounds check).
-template <typename T, int MODE>
-__global__ void ED_ROW_BOUNDS k_down_rows(SectorView sv, HopParams hp, const T* __restrict__ X0,
+// gathers the groups sx[col] of its hops.  The slot-major entries (row_ell_pack) carry the byte
+// offsets of the group and of the signed hop value, so a hop costs one table load, two shared
+// loads and the FMAs (one shared load when the cluster has at most four distinct hop values,
+// REG: the value is then selected in registers).  Table loads run one chunk of kPre slots ahead
+// of their use (the table has kEllPad zero slots at its end, so the look-ahead needs no bounds
+// check).
+template <typename T, bool REG>
+__global__ void __launch_bounds__(kRowThreads) k_down_rows(SectorView sv, HopParams hp, const T* __restrict__ X0,
                                                    T* __restrict__ O0, int64_t vstride, const double* __restrict__ beta,
                                                    int beta_stride, int n_step, const int* __restrict__ active) {
   constexpr int R = Vec<T>::n;
@@ -303,36 +279,20 @@ __global__ void ED_ROW_BOUNDS k_down_rows(SectorView sv, HopParams hp, const T* 
   const T* eup = Prec<T>::e_up(sv);
   const T* edn = Prec<T>::e_dn(sv);
   const unsigned char* ssvb = reinterpret_cast<const unsigned char*>(ssv);
-  T v0, v1, v2, v3;
-  if constexpr (MODE == 2) {
-    v0 = sizeof(T) == 8 ? (T)hp.mag[0] : (T)hp.magf[0];
-    v1 = sizeof(T) == 8 ? (T)hp.mag[1] : (T)hp.magf[1];
-    v2 = v3 = T(0);
-  } else {
-    v0 = Prec<T>::val(hp, 0), v1 = Prec<T>::val(hp, 1), v2 = Prec<T>::val(hp, 2), v3 = Prec<T>::val(hp, 3);
-  }
-  auto flip = [](T v, uint32_t sbit31) -> T {  // v with its sign bit xor-ed by bit 31 of sbit31
-    if constexpr (sizeof(T) == 4)
-      return __int_as_float(__float_as_int(v) ^ (int)sbit31);
-    else
-      return __longlong_as_double(__double_as_longlong(v) ^ ((long long)sbit31 << 32));
-  };
+  const T v0 = Prec<T>::val(hp, 0), v1 = Prec<T>::val(hp, 1), v2 = Prec<T>::val(hp, 2), v3 = Prec<T>::val(hp, 3);
   auto hop = [&](Acc16<T>& acc, uint32_t e) {
     T v;
-    uint32_t off;
-    if constexpr (MODE == 2) {
-      v = flip((e & 0x40000000u) ? v1 : v0, e & 0x80000000u);
-      off = e & kMagAddrMask;
-    } else if constexpr (MODE == 1) {
+    if constexpr (REG) {  // at most four distinct values: select in registers, sign bit from the entry
       const uint32_t i = (e >> 3) & 3u;
       v = (i & 2u) ? ((i & 1u) ? v3 : v2) : ((i & 1u) ? v1 : v0);
-      v = flip(v, (e & 4u) << 29);
-      off = e >> 10;
+      if constexpr (sizeof(T) == 4)
+        v = __int_as_float(__float_as_int(v) ^ (int)((e & 4u) << 29));
+      else
+        v = __longlong_as_double(__double_as_longlong(v) ^ ((long long)(e & 4u) << 61));
     } else {
       v = *reinterpret_cast<const T*>(ssvb + (e & 0x3FCu) * (sizeof(T) / 4));
-      off = e >> 10;
     }
-    acc.fma(v, *reinterpret_cast<const ulonglong2*>(sxb + off));
+    acc.fma(v, *reinterpret_cast<const ulonglong2*>(sxb + (e >> 10)));
   };
   for (int64_t u0r = (int64_t)blockIdx.x * R; u0r < du; u0r += (int64_t)gridDim.x * R) {
     __syncthreads();
@@ -354,9 +314,9 @@ __global__ void ED_ROW_BOUNDS k_down_rows(SectorView sv, HopParams hp, const T* 
     for (int64_t d = threadIdx.x; d < dd; d += blockDim.x) {
       const int32_t nz = sv.ptr_dn[d + 1] - sv.ptr_dn[d];
       const uint32_t* p = sv.ell_dn + d;
-      uint32_t ea[kPre], eb[kPre];
+      uint32_t e[kPre];
 #pragma unroll
-      for (int i = 0; i < kPre; ++i) ea[i] = __ldg(p + i * dd);
+      for (int i = 0; i < kPre; ++i) e[i] = __ldg(p + i * dd);
       p += kPre * dd;
       const uint32_t bd = sv.B_dn[d];
       const T ed = edn[d];
@@ -380,35 +340,21 @@ __global__ void ED_ROW_BOUNDS k_down_rows(SectorView sv, HopParams hp, const T* 
         }
         acc.set(a);
       }
-      // chunks alternate between ea and eb: while one chunk's hops run, the next one loads
-      // (slots k + kPre .. k + 2 kPre - 1 <= zmax + kEllPad - 1 whenever k + kPre <= nz)
       int32_t k = 0;
-      for (;;) {
-        if (k + kPre > nz) {
+      for (; k + kPre <= nz; k += kPre) {
+        uint32_t f[kPre];
 #pragma unroll
-          for (int i = 0; i < kPre; ++i)
-            if (k + i < nz) hop(acc, ea[i]);
-          break;
+        for (int i = 0; i < kPre; ++i) {
+          f[i] = e[i];
+          e[i] = __ldg(p + i * dd);  // slots k + kPre + i <= zmax + kEllPad - 1
         }
-#pragma unroll
-        for (int i = 0; i < kPre; ++i) eb[i] = __ldg(p + i * dd);
         p += kPre * dd;
 #pragma unroll
-        for (int i = 0; i < kPre; ++i) hop(acc, ea[i]);
-        k += kPre;
-        if (k + kPre > nz) {
-#pragma unroll
-          for (int i = 0; i < kPre; ++i)
-            if (k + i < nz) hop(acc, eb[i]);
-          break;
-        }
-#pragma unroll
-        for (int i = 0; i < kPre; ++i) ea[i] = __ldg(p + i * dd);
-        p += kPre * dd;
-#pragma unroll
-        for (int i = 0; i < kPre; ++i) hop(acc, eb[i]);
-        k += kPre;
+        for (int i = 0; i < kPre; ++i) hop(acc, f[i]);
       }
+#pragma unroll
+      for (int i = 0; i < kPre; ++i)
+        if (k + i < nz) hop(acc, e[i]);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         if (u0r + r >= du) continue;
@@ -421,98 +367,57 @@ __global__ void ED_ROW_BOUNDS k_down_rows(SectorView sv, HopParams hp, const T* 
   }
 }
 
-// Column pass: each warp owns one row u at a time and the 32 NV columns of the block's chunk.
-// The row's hops come from the slot-major table (slot k of row u at ell[k * d_up + u]), whose
-// address does not depend on the row pointer, so the entries of the warp's next row load while
-// the current one runs; each lane decodes the entries of its own slots (column, signed value)
-// and the warp broadcasts them with shuffles.  Operand rows are gathered in predicated groups of
-// kColUnroll 16-byte loads per lane, all in flight together.
-template <typename T, bool FUSED, bool MAG>
-__global__ void __launch_bounds__(kThreads, FUSED ? 2 : kColMinBlocks) k_up_cols(SectorView sv, HopParams hp, const T* __restrict__ X0,
-                                                                   T* __restrict__ O0, int64_t vstride, int rows_per_cta,
-                                                                   int n, LanczosScalars ls) {
+template <typename T, bool FUSED>
+__global__ void __launch_bounds__(kThreads, 4) k_up_cols(SectorView sv, HopParams hp, const T* __restrict__ X0,
+                                                      T* __restrict__ O0, int64_t vstride, int rows_per_cta, int n,
+                                                      LanczosScalars ls) {
   using RV = typename Vec<T>::t;
   constexpr int NV = Vec<T>::n;
-  constexpr int U = sizeof(T) == 8 ? 4 : kColUnroll;  // FP64 products are bound by FP64 arithmetic
-  __shared__ T ssv[256];  // signed values, index (vidx << 1) | neg
+  __shared__ T sval[kMaxVals];
   __shared__ bool s_last;
   const int run = blockIdx.z;
   if (FUSED && !ls.active[run]) return;
-  for (int i = threadIdx.x; i < 256; i += blockDim.x) {
-    const T v = Prec<T>::val(hp, i >> 1);
-    ssv[i] = (i & 1) ? -v : v;
-  }
+  for (int i = threadIdx.x; i < kMaxVals; i += blockDim.x) sval[i] = Prec<T>::val(hp, i);
   __syncthreads();
   const T* X = X0 + run * vstride;
   T* O = O0 + run * vstride;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  const int64_t ld = sv.ld, du = sv.d_up;
+  const int64_t ld = sv.ld;
   const int64_t c0 = (int64_t)blockIdx.y * (32 * NV) + lane * NV;
   const T* Xc = X + c0;
   const int64_t ub = (int64_t)blockIdx.x * rows_per_cta;
-  const int64_t ue = ub + rows_per_cta < du ? ub + rows_per_cta : du;
-  const int slots = sv.up_slots;
-  const T m0 = sizeof(T) == 8 ? (T)hp.mag[0] : (T)hp.magf[0];
-  const T m1 = sizeof(T) == 8 ? (T)hp.mag[1] : (T)hp.magf[1];
-  // entry of slot k of row u -> (column, signed value); slots past the table are empty
-  auto fetch = [&](int64_t u, int k) -> uint32_t { return k < slots ? __ldg(sv.ell_up + (int64_t)k * du + u) : 0u; };
-  auto decode = [&](uint32_t e, uint32_t& col, T& v) {
-    if constexpr (MAG) {
-      col = (e & kMagAddrMask) >> 4;
-      const T mv = (e & 0x40000000u) ? m1 : m0;
-      v = (e & 0x80000000u) ? -mv : mv;
-    } else {
-      col = e >> 14;
-      v = ssv[(e >> 2) & 255u];
-    }
-  };
+  const int64_t ue = ub + rows_per_cta < sv.d_up ? ub + rows_per_cta : sv.d_up;
   Partial3<T> part3;
-  int64_t u = ub + warp;
-  uint32_t f0 = 0u, f1 = 0u;  // slots lane and lane + 32 of the next row
-  int32_t q0 = 0, q1 = 0;
-  if (u < ue) {
-    q0 = sv.ptr_up[u];
-    q1 = sv.ptr_up[u + 1];
-    f0 = fetch(u, lane);
-    f1 = fetch(u, lane + 32);
-  }
-  for (; u < ue; u += nwarp) {
-    const int nz = q1 - q0;
-    uint32_t col0, col1;
-    T v0, v1;
-    decode(f0, col0, v0);
-    decode(f1, col1, v1);
-    const int64_t un = u + nwarp;
-    if (un < ue) {  // the next row's entries load while this row runs
-      q0 = sv.ptr_up[un];
-      q1 = sv.ptr_up[un + 1];
-      f0 = fetch(un, lane);
-      f1 = fetch(un, lane + 32);
-    }
+  for (int64_t u = ub + warp; u < ue; u += nwarp) {
     RV* op = reinterpret_cast<RV*>(O + u * ld + c0);
     RV acc = *op;
+    const int32_t p0 = sv.ptr_up[u], p1 = sv.ptr_up[u + 1];
     Acc16<T> a16;
     a16.set_vec(acc);
-    for (int w0 = 0; w0 < nz; w0 += 64) {
-      if (w0 > 0) {  // rows of more than 64 hops: the next window of slots
-        decode(fetch(u, w0 + lane), col0, v0);
-        decode(fetch(u, w0 + 32 + lane), col1, v1);
+    for (int32_t base = p0; base < p1; base += 32) {
+      // the warp's next 32 entries: lane j holds entry base + j (column and signed value)
+      const int cnt = p1 - base < 32 ? p1 - base : 32;
+      const uint32_t me = lane < cnt ? __ldg(sv.ent_up + base + lane) : 0u;
+      const uint32_t mcol = ent_col(me);
+      T mv = sval[ent_vidx(me)];
+      mv = ent_neg(me) ? -mv : mv;
+      int j = 0;
+      for (; j + 4 <= cnt; j += 4) {
+        ulonglong2 xv[4];
+        T v[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const uint32_t col = __shfl_sync(0xffffffffu, mcol, j + i);
+          v[i] = __shfl_sync(0xffffffffu, mv, j + i);
+          xv[i] = __ldg(reinterpret_cast<const ulonglong2*>(Xc + (int64_t)col * ld));
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a16.fma(v[i], xv[i]);
       }
-      const int cnt = nz - w0 < 64 ? nz - w0 : 64;
-      for (int j = 0; j < cnt; j += U) {
-        ulonglong2 xv[U];
-#pragma unroll
-        for (int i = 0; i < U; ++i) {  // all loads of the group first ...
-          const int jj = j + i;
-          const uint32_t col = __shfl_sync(0xffffffffu, jj < 32 ? col0 : col1, jj & 31);
-          xv[i] = jj < cnt ? __ldg(reinterpret_cast<const ulonglong2*>(Xc + (int64_t)col * ld)) : make_ulonglong2(0ull, 0ull);
-        }
-#pragma unroll
-        for (int i = 0; i < U; ++i) {  // ... then their products (empty slots add 0 x 0)
-          const int jj = j + i;
-          const T v = __shfl_sync(0xffffffffu, jj < 32 ? v0 : v1, jj & 31);
-          a16.fma(jj < cnt ? v : T(0), xv[i]);
-        }
+      for (; j < cnt; ++j) {
+        const uint32_t col = __shfl_sync(0xffffffffu, mcol, j);
+        const T v = __shfl_sync(0xffffffffu, mv, j);
+        a16.fma(v, __ldg(reinterpret_cast<const ulonglong2*>(Xc + (int64_t)col * ld)));
       }
     }
     acc = a16.vec();
@@ -594,34 +499,25 @@ static void launch_two_pass(const SectorView& sv, const HopParams& hp, const T* 
   const double es = sizeof(T);
   const double dim = (double)sv.d_up * sv.d_dn;
   const size_t smem = down_rows_smem(sv, sizeof(T) == 8 ? ED_FP64 : ED_FP32);
-  const int mode = sv.ell_mag ? 2 : hp.nvals <= 4 ? 1 : 0;
-  allow_max_dynamic_smem(k_down_rows<T, 0>);
-  allow_max_dynamic_smem(k_down_rows<T, 1>);
-  allow_max_dynamic_smem(k_down_rows<T, 2>);
+  const bool reg = hp.nvals <= 4;
+  allow_max_dynamic_smem(k_down_rows<T, true>);
+  allow_max_dynamic_smem(k_down_rows<T, false>);
   const int64_t groups = (sv.d_up + Vec<T>::n - 1) / Vec<T>::n;
   dim3 g1((unsigned)std::min<int64_t>(groups, 152), runs);
   dim3 g2((unsigned)((sv.d_up + kRowsPerCta - 1) / kRowsPerCta), (unsigned)((sv.d_dn + 32 * Vec<T>::n - 1) / (32 * Vec<T>::n)),
           runs);
   // one timed unit per step: both passes (the second launch is counted separately)
   ProfScope ps_(ls ? K_LANCZOS_STEP : K_HPSI, s, (beta ? 3.0 : 2.0) * es * dim * runs);
-  const int* act = ls ? ls->active : nullptr;
-  if (mode == 2)
-    k_down_rows<T, 2><<<g1, kRowThreads, smem, s>>>(sv, hp, X, O, vstride, beta, beta_stride, n, act);
-  else if (mode == 1)
-    k_down_rows<T, 1><<<g1, kRowThreads, smem, s>>>(sv, hp, X, O, vstride, beta, beta_stride, n, act);
+  if (reg)
+    k_down_rows<T, true><<<g1, kRowThreads, smem, s>>>(sv, hp, X, O, vstride, beta, beta_stride, n, ls ? ls->active : nullptr);
   else
-    k_down_rows<T, 0><<<g1, kRowThreads, smem, s>>>(sv, hp, X, O, vstride, beta, beta_stride, n, act);
+    k_down_rows<T, false><<<g1, kRowThreads, smem, s>>>(sv, hp, X, O, vstride, beta, beta_stride, n, ls ? ls->active : nullptr);
   ED_CHECK_LAUNCH();
   note_launch();
-  const LanczosScalars none{};
-  if (ls && sv.ell_mag)
-    k_up_cols<T, true, true><<<g2, kThreads, 0, s>>>(sv, hp, X, O, vstride, kRowsPerCta, n, *ls);
-  else if (ls)
-    k_up_cols<T, true, false><<<g2, kThreads, 0, s>>>(sv, hp, X, O, vstride, kRowsPerCta, n, *ls);
-  else if (sv.ell_mag)
-    k_up_cols<T, false, true><<<g2, kThreads, 0, s>>>(sv, hp, X, O, vstride, kRowsPerCta, n, none);
+  if (ls)
+    k_up_cols<T, true><<<g2, kThreads, 0, s>>>(sv, hp, X, O, vstride, kRowsPerCta, n, *ls);
   else
-    k_up_cols<T, false, false><<<g2, kThreads, 0, s>>>(sv, hp, X, O, vstride, kRowsPerCta, n, none);
+    k_up_cols<T, false><<<g2, kThreads, 0, s>>>(sv, hp, X, O, vstride, kRowsPerCta, n, LanczosScalars{});
   ED_CHECK_LAUNCH();
 }
 

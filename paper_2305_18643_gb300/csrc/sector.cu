@@ -123,14 +123,13 @@ __global__ void k_max_int(const int32_t* __restrict__ v, int64_t n, int* __restr
 }
 
 // Slot-major copy of the CSR table for the row kernel: ell[k * dim + r] = k-th entry of row r
-// in row_ell_pack form, or row_ell_pack_mag form when mag is set (0 past its end).
+// in row_ell_pack form (0 past its end).
 __global__ void k_ell_fill(int64_t dim, const int32_t* __restrict__ ptr, const uint32_t* __restrict__ ent, int zmax,
-                           uint32_t* __restrict__ ell, int mag, MagMap mm) {
+                           uint32_t* __restrict__ ell) {
   int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (r >= dim) return;
   const int32_t p0 = ptr[r], n = ptr[r + 1] - p0;
-  for (int k = 0; k < zmax; ++k)
-    ell[(int64_t)k * dim + r] = k < n ? (mag ? row_ell_pack_mag(ent[p0 + k], mm) : row_ell_pack(ent[p0 + k])) : 0u;
+  for (int k = 0; k < zmax; ++k) ell[(int64_t)k * dim + r] = k < n ? row_ell_pack(ent[p0 + k]) : 0u;
 }
 
 // Exclusive scan of cnt[0..n) into ptr[0..n] by one block (one-time table construction).
@@ -214,7 +213,7 @@ struct BankMatch {
 }  // namespace
 
 static void ell_bank_order(const std::vector<int32_t>& ptr, const std::vector<uint32_t>& ent, int64_t dim, int zmax,
-                           const MagMap* mm, std::vector<uint32_t>& ell) {
+                           std::vector<uint32_t>& ell) {
   ell.assign((size_t)zmax * dim, 0u);
   std::vector<uint32_t> rem[8];
   BankMatch bm;
@@ -252,7 +251,7 @@ static void ell_bank_order(const std::vector<int32_t>& ptr, const std::vector<ui
               pick = j;
               break;
             }
-        ell[(size_t)k * dim + r0 + i] = mm ? row_ell_pack_mag(v[pick], *mm) : row_ell_pack(v[pick]);
+        ell[(size_t)k * dim + r0 + i] = row_ell_pack(v[pick]);
         v.erase(v.begin() + (ptrdiff_t)pick);
       }
     }
@@ -320,7 +319,6 @@ std::unique_ptr<SpinTables> build_spin_tables(const ModelHost& m, int N, cudaStr
     }
     ED_CUDA(cudaMemcpyAsync(&t->zmax, dz.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     ED_CUDA(cudaStreamSynchronize(s));
-    t->ell_mag = m.nmag > 0;
     t->ell.alloc(std::max<int64_t>((int64_t)(t->zmax + kEllPad) * dim, 1));
     ED_CUDA(cudaMemsetAsync(t->ell.p, 0, (size_t)(t->zmax + kEllPad) * dim * sizeof(uint32_t), s));
     if (dim >= kEllOrderMinDim && t->zmax > 0) {
@@ -331,11 +329,11 @@ std::unique_ptr<SpinTables> build_spin_tables(const ModelHost& m, int N, cudaStr
       ED_CUDA(cudaMemcpyAsync(hent.data(), t->ent.p, std::max<int64_t>(nnz, 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
       ED_CUDA(cudaStreamSynchronize(s));
       std::vector<uint32_t> hell;
-      ell_bank_order(hptr, hent, dim, t->zmax, t->ell_mag ? &m.mm : nullptr, hell);
+      ell_bank_order(hptr, hent, dim, t->zmax, hell);
       ED_CUDA(cudaMemcpyAsync(t->ell.p, hell.data(), hell.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
       ED_CUDA(cudaStreamSynchronize(s));
     } else if (dim > 0 && t->zmax > 0) {
-      { ProfScope ps_(K_TABLES, s, 0.0); k_ell_fill<<<nblocks(dim, bs), bs, 0, s>>>(dim, t->ptr.p, t->ent.p, t->zmax, t->ell.p, t->ell_mag ? 1 : 0, m.mm); }
+      { ProfScope ps_(K_TABLES, s, 0.0); k_ell_fill<<<nblocks(dim, bs), bs, 0, s>>>(dim, t->ptr.p, t->ent.p, t->zmax, t->ell.p); }
       ED_CHECK_LAUNCH();
     }
   }
