@@ -13,7 +13,7 @@ import scipy.sparse as sp
 
 import oracle.symmetry_oracle as S
 import oracle_memo as OM
-from oracle.ed_oracle import Model, ground_state, sector_hamiltonian
+from oracle.ed_oracle import Model
 from paper_2305_18643_gb300 import build, ed
 
 pytestmark = pytest.mark.gpu
