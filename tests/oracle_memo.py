@@ -106,3 +106,18 @@ def sector_hamiltonian(m, n_up, n_dn):
     if k not in _ops:
         _ops[k] = O.sector_hamiltonian(m, n_up, n_dn)
     return _ops[k]
+
+
+def irrep_ground_energy(H, m, n_up, n_dn, gens, irrep, orders=None):
+    """The symmetry oracle's irrep_ground_energy, given the irrep matrix H that the caller has
+    already built with symmetric_hamiltonian for the same arguments: the oracle's own function
+    and eigensolver run, without building H a second time."""
+    import oracle.symmetry_oracle as S
+
+    build = S.symmetric_hamiltonian
+    S.symmetric_hamiltonian = lambda *a, **k: (H, None)
+    try:
+        with dense_blas_threads():
+            return S.irrep_ground_energy(m, n_up, n_dn, gens, irrep, orders=orders)
+    finally:
+        S.symmetric_hamiltonian = build
